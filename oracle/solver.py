@@ -1,0 +1,128 @@
+"""FP64 regularised least squares: the finite-difference prior and CG.
+
+Test infrastructure: see ``oracle/__init__.py``.
+
+The criterion is Eq. criterion of the paper (Section 2.2),
+
+    J(x) = ||y - A x||^2 + lambda ||B x||^2 ,
+    x_hat = (A^T A + lambda B^T B)^{-1} A^T y ,
+
+with A = M P (the masked projector: masked pixels are not projected, Section
+4) and B = D, "a finite-difference operator along each axis of the maps"
+(Section 3.3.1).  Reading of D where the paper is silent: forward
+differences ``x[i+1] - x[i]`` along x, y and z, without wrap-around (N - 1
+differences per line), the same lambda on every axis (as in Table hypers).
+
+The solver is the textbook (Hestenes-Stiefel) conjugate-gradient method on
+the normal equations, started from x0 (zero unless given), run for a fixed
+number of iterations (the paper uses CG throughout, Sections 3.1 and 5.1; it
+tried no preconditioner, Section 5.2).
+"""
+
+import numpy as np
+
+from . import siddon
+
+
+def D(x):
+    """Forward differences along x, y, z of a ``[nz][ny][nx]`` map; returns
+    the three difference arrays (axis order x, y, z)."""
+    x = np.asarray(x, dtype=np.float64)
+    return [np.diff(x, axis=2), np.diff(x, axis=1), np.diff(x, axis=0)]
+
+
+def Dt(dx, dy, dz):
+    """Transpose of :func:`D`: sum over axes of the adjoint of one forward
+    difference, which maps a difference array g to -g[i] + g[i-1] padded with
+    zeros at the ends."""
+    def adj(g, axis):
+        n = g.shape[axis] + 1
+        shape = list(g.shape)
+        shape[axis] = n
+        out = np.zeros(shape)
+        sl_lo = [slice(None)] * 3
+        sl_hi = [slice(None)] * 3
+        sl_lo[axis] = slice(0, n - 1)
+        sl_hi[axis] = slice(1, n)
+        out[tuple(sl_lo)] -= g
+        out[tuple(sl_hi)] += g
+        return out
+    return adj(dx, 2) + adj(dy, 1) + adj(dz, 0)
+
+
+def DtD(x):
+    return Dt(*D(x))
+
+
+def prior_energy(x):
+    """||D x||^2."""
+    return float(sum(np.sum(g * g) for g in D(x)))
+
+
+class Problem:
+    """One static reconstruction: cube geometry, pointing, mask, data, lambda."""
+
+    def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0):
+        self.geom, self.pointing = geom, np.asarray(pointing, np.float64)
+        self.nu, self.nv = int(nu), int(nv)
+        self.mask = mask
+        self.y = np.asarray(y, dtype=np.float64)
+        self.lam = float(lam)
+        self.shape = (geom["nz"], geom["ny"], geom["nx"])
+
+    def P(self, x):
+        return siddon.project(self.geom, x, self.pointing, self.nu, self.nv,
+                              self.mask)
+
+    def Pt(self, y):
+        return siddon.backproject(self.geom, y, self.pointing, self.nu,
+                                  self.nv, self.mask)
+
+    def masked(self, y):
+        if self.mask is None:
+            return y
+        return np.where(self.mask == 0, y, 0.0)
+
+    def rhs(self):
+        """b = P^T M y."""
+        return self.Pt(self.masked(self.y))
+
+    def normal(self, v):
+        """(P^T M P + lambda D^T D) v."""
+        return self.Pt(self.P(v)) + self.lam * DtD(v)
+
+    def J(self, x):
+        """Eq. criterion: ||M (y - P x)||^2 + lambda ||D x||^2."""
+        r = self.masked(self.y - self.P(x))
+        return float(np.sum(r * r)) + self.lam * prior_energy(x)
+
+
+def cg(problem, n_iter, x0=None, track_J=True):
+    """Conjugate gradients on the normal equations.
+
+    Returns ``(x, report)`` where ``report`` holds, per iterate k = 0..n_iter,
+    ``J`` (Eq. criterion, evaluated directly) and ``rr`` (squared norm of the
+    recursively updated residual).
+    """
+    b = problem.rhs()
+    x = np.zeros(problem.shape) if x0 is None else np.array(x0, np.float64)
+    r = b - problem.normal(x) if x0 is not None else b.copy()
+    p = r.copy()
+    rr = float(np.sum(r * r))
+    Js = [problem.J(x)] if track_J else []
+    rrs = [rr]
+    for _ in range(n_iter):
+        if rr == 0.0:  # exact solution reached: CG stops
+            break
+        q = problem.normal(p)
+        alpha = rr / float(np.sum(p * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        rr_new = float(np.sum(r * r))
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+        rrs.append(rr)
+        if track_J:
+            Js.append(problem.J(x))
+    return x, {"J": np.array(Js), "rr": np.array(rrs)}

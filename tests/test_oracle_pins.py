@@ -1,0 +1,468 @@
+"""Pins of the FP64 oracle against geometry, closed forms and brute force.
+
+None of these checks re-types the oracle's own formulas: each compares it
+with something the geometry or the mathematics fixes independently, chosen so
+that a dropped term, a wrong sign or index, or a transposed operand fails at
+least one of them.
+"""
+
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import checks, siddon, solver
+
+
+def _geom(n, lo, d):
+    nx, ny, nz = n
+    return {"nx": nx, "ny": ny, "nz": nz, "x0": lo[0], "y0": lo[1],
+            "z0": lo[2], "dx": d[0], "dy": d[1], "dz": d[2]}
+
+
+def _dense(geom, o, u):
+    idx, ln, _, _ = siddon.segments(geom, o, u)
+    out = np.zeros(geom["nx"] * geom["ny"] * geom["nz"])
+    np.add.at(out, idx, ln)
+    return out
+
+
+# --------------------------------------------------------------- hand cases
+
+def test_hand_derived_cases(golden_dir):
+    """Hand-derived integrals through a 2x2x2 cube, incl. the half-open tie
+    rule, a corner-to-corner diagonal and an observer inside the cube."""
+    g = _geom((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    k, j, i = np.meshgrid(np.arange(2), np.arange(2), np.arange(2),
+                          indexing="ij")
+    cube = (1 + i + 2 * j + 4 * k).astype(np.float64).reshape(-1)
+    rows = [ln.split() for ln in open(os.path.join(golden_dir,
+                                                   "siddon_hand_cases.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 8
+    for name, *vals in rows:
+        ox, oy, oz, ux, uy, uz, want = map(float, vals)
+        idx, ln, _, _ = siddon.segments(g, [ox, oy, oz], [ux, uy, uz])
+        got = float(np.sum(ln * cube[idx]))
+        assert got == pytest.approx(want, rel=1e-14, abs=1e-14), name
+
+
+# ------------------------------------------------------ exact rational pins
+
+def _exact_lengths(n, o, u):
+    """Parameter length (in units of |u|) of o + a u, a >= 0, inside every
+    half-open unit voxel of [0, n)^3, in exact rational arithmetic."""
+    out = {}
+    for kk in range(n):
+        for jj in range(n):
+            for ii in range(n):
+                b0 = (ii, jj, kk)
+                t_in, t_out = Fraction(0), None
+                ok = True
+                for a in range(3):
+                    if u[a] == 0:
+                        if not (b0[a] <= o[a] < b0[a] + 1):
+                            ok = False
+                        continue
+                    ta = (Fraction(b0[a]) - o[a]) / u[a]
+                    tb = (Fraction(b0[a] + 1) - o[a]) / u[a]
+                    lo_, hi_ = min(ta, tb), max(ta, tb)
+                    t_in = max(t_in, lo_)
+                    t_out = hi_ if t_out is None else min(t_out, hi_)
+                if ok and t_out is not None and t_out > t_in:
+                    out[(kk * n + jj) * n + ii] = t_out - t_in
+    return out
+
+
+@pytest.mark.parametrize("o,u", [
+    ((Fraction(-1), Fraction(-1), Fraction(-1)), (1, 1, 1)),          # corners
+    ((Fraction(-1), Fraction(1, 2), Fraction(-2)), (2, 0, 3)),        # edges
+    ((Fraction(5), Fraction(3, 7), Fraction(9, 4)), (-3, 1, -1)),
+    ((Fraction(-2), Fraction(-3), Fraction(1)), (1, 2, 0)),           # face z=1
+    ((Fraction(1, 3), Fraction(4, 3), Fraction(7, 5)), (1, -1, 2)),   # inside
+    ((Fraction(-1), Fraction(2), Fraction(2)), (1, -1, -1)),          # edges
+])
+def test_exact_rational_brute_force(o, u):
+    """Every per-voxel length equals the exact rational slab clip, including
+    rays through voxel corners, along edges and lying in faces."""
+    n = 3
+    g = _geom((n, n, n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0))
+    exact = _exact_lengths(n, o, u)
+    un = math.sqrt(sum(c * c for c in u))
+    want = np.zeros(n ** 3)
+    for j, v in exact.items():
+        want[j] = float(v) * un
+    got = _dense(g, [float(c) for c in o], [float(c) for c in u])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------ brute force O2
+
+def test_brute_force_random_rays():
+    """Merge-form Siddon equals the per-voxel slab clip on small anisotropic
+    cubes for random rays (random origins inside and outside the cube)."""
+    rng = np.random.default_rng(7)
+    g = _geom((5, 4, 6), (-0.7, 0.2, -1.1), (0.3, 0.45, 0.25))
+    for _ in range(60):
+        o = rng.uniform(-3, 3, 3)
+        u = rng.standard_normal(3)
+        np.testing.assert_allclose(_dense(g, o, u),
+                                   checks.brute_force_ray(g, o, u),
+                                   rtol=0, atol=1e-12)
+
+
+def test_brute_force_wcs_rays():
+    """Same pin on rays built from pointing records (far observer)."""
+    g = synth.cube_geom(6, 1.5)
+    ptg = synth.pointing_table([17.0, 133.0], [3.0, -11.0], 215.0, 9, 7, 3.2,
+                               roll_deg=[0.0, 25.0][1])
+    for n in range(2):
+        for iu, iv in [(0, 0), (4, 3), (8, 6), (2, 5)]:
+            o, u = siddon.ray(ptg[n], iu, iv)
+            np.testing.assert_allclose(_dense(g, o, u),
+                                       checks.brute_force_ray(g, o, u),
+                                       rtol=0, atol=1e-11)
+
+
+# ------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("seed", range(5))
+def test_chord_through_centre_closed_form(seed):
+    """A line through the centre of a cube of half-width h along unit u has
+    chord 2 h / max|u_a|; a uniform cube c integrates to c times the chord,
+    and the segment lengths sum to the chord."""
+    rng = np.random.default_rng(seed)
+    h = 1.3
+    n = int(rng.integers(3, 12))
+    g = synth.cube_geom(n, h)
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    o = -200.0 * u  # far observer, line through the centre
+    idx, ln, a0, a1 = siddon.segments(g, o, u)
+    chord = 2 * h / np.max(np.abs(u))
+    assert np.sum(ln) == pytest.approx(chord, rel=1e-12)
+    cube = np.full(n ** 3, 2.5)
+    assert np.sum(ln * cube[idx]) == pytest.approx(2.5 * chord, rel=1e-12)
+
+
+def test_axis_aligned_column_sums():
+    """Axis-aligned rays through voxel centres return dx times the exact
+    column sums, along x, y and z and in both directions."""
+    rng = np.random.default_rng(3)
+    g = _geom((7, 5, 4), (-1.0, -0.5, 0.25), (0.2, 0.3, 0.4))
+    x = rng.random((4, 5, 7))
+    flat = x.reshape(-1)
+    for (k, j) in [(0, 0), (3, 4), (2, 1)]:
+        yc = g["y0"] + (j + 0.5) * g["dy"]
+        zc = g["z0"] + (k + 0.5) * g["dz"]
+        for sgn in (1, -1):
+            o = [-5.0 * sgn, yc, zc]
+            idx, ln, _, _ = siddon.segments(g, o, [sgn * 1.0, 0, 0])
+            assert np.sum(ln * flat[idx]) == pytest.approx(
+                g["dx"] * x[k, j, :].sum(), rel=1e-13)
+    for (k, i) in [(1, 6), (0, 0)]:
+        xc = g["x0"] + (i + 0.5) * g["dx"]
+        zc = g["z0"] + (k + 0.5) * g["dz"]
+        idx, ln, _, _ = siddon.segments(g, [xc, 9.0, zc], [0, -2.0, 0])
+        assert np.sum(ln * flat[idx]) == pytest.approx(
+            g["dy"] * x[k, :, i].sum(), rel=1e-13)
+    for (j, i) in [(2, 3), (4, 6)]:
+        xc = g["x0"] + (i + 0.5) * g["dx"]
+        yc = g["y0"] + (j + 0.5) * g["dy"]
+        idx, ln, _, _ = siddon.segments(g, [xc, yc, -3.0], [0, 0, 0.5])
+        assert np.sum(ln * flat[idx]) == pytest.approx(
+            g["dz"] * x[:, j, i].sum(), rel=1e-13)
+
+
+def test_fine_sampling_converges():
+    """Midpoint sampling with step h stays within (S + 2) h max|x| of the
+    Siddon integral (S = number of segments), and the error shrinks with h."""
+    rng = np.random.default_rng(11)
+    g = synth.cube_geom(8, 1.0)
+    x = rng.random((8, 8, 8))
+    flat = x.reshape(-1)
+    for _ in range(4):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        o = rng.uniform(-0.3, 0.3, 3) - 5.0 * u
+        idx, ln, _, _ = siddon.segments(g, o, u)
+        exact = float(np.sum(ln * flat[idx]))
+        errs = []
+        for h in (1e-2, 1e-3, 1e-4):
+            approx = checks.sampled_ray(g, x, o, u, h, 5.0 + 2 * np.sqrt(3))
+            err = abs(approx - exact)
+            assert err <= (len(idx) + 2) * h * x.max()
+            errs.append(err)
+        assert errs[-1] < 1e-2 * (len(idx) + 2) * x.max() * 1e-2 + 1e-12
+
+
+# --------------------------------------------------------- WCS ray reading
+
+def test_wcs_reference_pixel_hits_sun_centre():
+    """With crval = 0 the reference pixel looks at Sun centre: the impact
+    parameter |o x u| is 0 and u = -o/|o|."""
+    ptg = synth.pointing_table([0.0, 57.0, 211.0], [0.0, 12.0, -30.0], 215.0,
+                               5, 9, 3.2, roll_deg=17.0)
+    for n in range(3):
+        o, u = siddon.ray(ptg[n], 2, 4)  # crpix = (2, 4)
+        assert np.linalg.norm(np.cross(o, u)) < 1e-12
+        np.testing.assert_allclose(u, -o / np.linalg.norm(o), atol=1e-15)
+        lon, lat = np.deg2rad([0.0, 57.0, 211.0][n]), np.deg2rad(
+            [0.0, 12.0, -30.0][n])
+        np.testing.assert_allclose(
+            o, 215.0 * np.array([np.cos(lat) * np.cos(lon),
+                                 np.cos(lat) * np.sin(lon), np.sin(lat)]),
+            atol=1e-12)
+
+
+def test_wcs_gnomonic_angles_and_impact_parameter():
+    """Gnomonic pixels: the angle between a pixel's ray and the boresight
+    satisfies tan^2 = tan^2(theta_u) + tan^2(theta_v), and its impact
+    parameter is d sin(theta)."""
+    nu, nv = 11, 7
+    ptg = synth.pointing_table([33.0], [5.0], 215.0, nu, nv, 40.0,
+                               roll_deg=12.0)
+    ptg[0, 8] = 1e-3   # crval_u
+    ptg[0, 9] = -2e-3  # crval_v
+    p = ptg[0]
+    _, w = siddon.ray(np.concatenate([p[:8], [0.0, 0.0], p[10:]]), 5, 3)
+    for iu, iv in [(0, 0), (10, 6), (3, 5), (7, 1)]:
+        o, u = siddon.ray(p, iu, iv)
+        tu = math.tan((iu - p[6]) * p[4] + p[8])
+        tv = math.tan((iv - p[7]) * p[5] + p[9])
+        theta = math.atan(math.hypot(tu, tv))
+        assert math.acos(np.clip(np.dot(u, w), -1, 1)) == pytest.approx(
+            theta, rel=1e-9)
+        assert np.linalg.norm(np.cross(o, u)) == pytest.approx(
+            215.0 * math.sin(theta), rel=1e-9)
+
+
+def test_wcs_orientation_and_roll():
+    """At lon = lat = roll = 0 the u axis points to +y and the v axis to +z
+    (solar north up); a 90-degree roll turns +u into +v."""
+    p = synth.pointing_table([0.0], [0.0], 215.0, 3, 3, 3.2)[0]
+    o, u_c = siddon.ray(p, 1, 1)
+    _, u_r = siddon.ray(p, 2, 1)  # one pixel along +u
+    _, u_t = siddon.ray(p, 1, 2)  # one pixel along +v
+    d_r, d_t = u_r - u_c, u_t - u_c
+    assert d_r[1] > 0 and abs(d_r[2]) < 1e-15
+    assert d_t[2] > 0 and abs(d_t[1]) < 1e-15
+    q = synth.pointing_table([0.0], [0.0], 215.0, 3, 3, 3.2, roll_deg=90.0)[0]
+    _, ur = siddon.ray(q, 2, 1)
+    np.testing.assert_allclose(ur, u_t, atol=1e-14)
+
+
+def test_wcs_pole_rejected():
+    p = synth.pointing_table([0.0], [90.0], 215.0, 3, 3, 3.2)[0]
+    with pytest.raises(ValueError):
+        siddon.ray(p, 0, 0)
+
+
+def test_mask_recipe_matches_ray_impact_parameter():
+    """The occulter recipe (an image-plane disk) masks exactly the pixels
+    whose ray passes within r_occ of Sun centre."""
+    ptg = synth.pointing_table([10.0, 200.0], [4.0, -6.0], 215.0, 16, 12, 4.0)
+    m = synth.occulter_mask(ptg, 16, 12, r_occ=1.0, r_edge=1.8)
+    for n in range(2):
+        for iv in range(12):
+            for iu in range(16):
+                o, u = siddon.ray(ptg[n], iu, iv)
+                rho = np.linalg.norm(np.cross(o, u))
+                assert bool(m[n, iv, iu]) == (rho < 1.0 or rho > 1.8)
+
+
+# --------------------------------------------------- operator-level pins
+
+def _small_scene(T=1):
+    g = synth.cube_geom(9, 1.5, ny=7, nz=8)
+    rng = np.random.default_rng(5)
+    ptg = synth.pointing_table(rng.uniform(0, 360, 5), rng.uniform(-20, 20, 5),
+                               215.0, 10, 6, 3.4, roll_deg=8.0,
+                               gain=rng.uniform(0.5, 2.0, 5),
+                               time=rng.uniform(0, max(T - 1, 0), 5))
+    mask = (rng.random((5, 6, 10)) < 0.2).astype(np.uint8)
+    return g, ptg, mask, rng
+
+
+@pytest.mark.parametrize("T", [1, 3])
+def test_adjoint_identity_fp64(T):
+    """<P x, y> = <x, P^T y> to 1e-12 (with mask, gains and, for T = 3,
+    time interpolation between frames)."""
+    g, ptg, mask, rng = _small_scene(T)
+    shape = ((T,) if T > 1 else ()) + (g["nz"], g["ny"], g["nx"])
+    x = rng.standard_normal(shape)
+    y = rng.standard_normal((5, 6, 10))
+    Px = siddon.project(g, x, ptg, 10, 6, mask, n_frames=T)
+    Pty = siddon.backproject(g, y, ptg, 10, 6, mask, n_frames=T)
+    lhs, rhs = np.sum(Px * y), np.sum(x * Pty)
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert np.all(Px[mask != 0] == 0.0)
+
+
+def test_dense_matrix_equals_brute_force():
+    """Rows of P (projecting unit vectors) equal the brute-force clip of each
+    pixel's ray, times the gain."""
+    g, ptg, _, _ = _small_scene()
+    nvox = g["nx"] * g["ny"] * g["nz"]
+    Pm = np.zeros((5 * 6 * 10, nvox))
+    eye = np.zeros(nvox)
+    for j in range(nvox):
+        eye[:] = 0.0
+        eye[j] = 1.0
+        Pm[:, j] = siddon.project(g, eye.reshape(8, 7, 9), ptg, 10, 6).reshape(-1)
+    for r in [0, 17, 123, 299]:
+        n, iv, iu = r // 60, (r // 10) % 6, r % 10
+        o, u = siddon.ray(ptg[n], iu, iv)
+        np.testing.assert_allclose(Pm[r], ptg[n, 10] * checks.brute_force_ray(g, o, u),
+                                   atol=1e-12)
+
+
+def test_gain_scales_projection():
+    g, ptg, mask, rng = _small_scene()
+    x = rng.random((8, 7, 9))
+    y1 = siddon.project(g, x, ptg, 10, 6, mask)
+    p2 = ptg.copy()
+    p2[:, 10] *= 3.0
+    y3 = siddon.project(g, x, p2, 10, 6, mask)
+    np.testing.assert_allclose(y3, 3.0 * y1, rtol=1e-14)
+
+
+def test_time_interpolation_special_cases():
+    """Integer time stamps select one frame; tau = T-1 selects the last
+    frame; a stamp halfway between frames gives the mean of the two
+    projections; a stamp outside [0, T-1] is rejected."""
+    g, ptg, _, rng = _small_scene()
+    T = 4
+    X = rng.random((T, 8, 7, 9))
+    per_frame = [siddon.project(g, X[t], ptg, 10, 6) for t in range(T)]
+    for tau, want in [(0.0, per_frame[0]), (2.0, per_frame[2]),
+                      (3.0, per_frame[3]),
+                      (1.5, 0.5 * (per_frame[1] + per_frame[2]))]:
+        p = ptg.copy()
+        p[:, 11] = tau
+        got = siddon.project(g, X, p, 10, 6, n_frames=T)
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-15)
+    p = ptg.copy()
+    p[0, 11] = 3.5
+    with pytest.raises(ValueError):
+        siddon.project(g, X, p, 10, 6, n_frames=T)
+
+
+def test_fd_gradient_of_data_term():
+    """Central finite differences of f(x) = 0.5 ||P x - y||^2 (exact for a
+    quadratic up to rounding) equal P^T (P x - y)."""
+    g, ptg, mask, rng = _small_scene()
+    x = rng.random((8, 7, 9))
+    y = rng.random((5, 6, 10))
+    r = siddon.project(g, x, ptg, 10, 6, mask) - np.where(mask == 0, y, 0.0)
+    grad = siddon.backproject(g, r, ptg, 10, 6, mask)
+
+    def f(v):
+        rr = siddon.project(g, v, ptg, 10, 6, mask) - np.where(mask == 0, y, 0)
+        return 0.5 * np.sum(rr * rr)
+    h = 1e-3
+    for j in rng.choice(x.size, 12, replace=False):
+        e = np.zeros(x.size)
+        e[j] = h
+        e = e.reshape(x.shape)
+        fd = (f(x + e) - f(x - e)) / (2 * h)
+        assert fd == pytest.approx(grad.reshape(-1)[j], rel=1e-7, abs=1e-10)
+
+
+# ---------------------------------------------------------- prior D
+
+def test_DtD_cosine_eigenmodes():
+    """Forward differences without wrap make D^T D the path-graph Laplacian
+    on each line; its eigenvectors are cos(pi m (i + 1/2) / n) with
+    eigenvalues 2 - 2 cos(pi m / n)."""
+    nz, ny, nx = 5, 6, 7
+    for axis, n in ((2, nx), (1, ny), (0, nz)):
+        for m in range(n):
+            c = np.cos(np.pi * m * (np.arange(n) + 0.5) / n)
+            shape = [1, 1, 1]
+            shape[axis] = n
+            x = np.broadcast_to(c.reshape(shape), (nz, ny, nx)).copy()
+            lam = 2 - 2 * np.cos(np.pi * m / n)
+            np.testing.assert_allclose(solver.DtD(x), lam * x, atol=1e-12)
+
+
+def test_D_adjoint_and_ramp():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((4, 5, 6))
+    gs = [rng.standard_normal(d.shape) for d in solver.D(x)]
+    lhs = sum(np.sum(a * b) for a, b in zip(solver.D(x), gs))
+    assert lhs == pytest.approx(np.sum(x * solver.Dt(*gs)), rel=1e-12)
+    # ramp 2 i + 3 j - k: differences are 2, 3, -1 on every line
+    k, j, i = np.meshgrid(np.arange(4), np.arange(5), np.arange(6),
+                          indexing="ij")
+    ramp = 2.0 * i + 3.0 * j - 1.0 * k
+    want = 4 * 4 * 5 * 5 + 9 * 4 * 4 * 6 + 1 * 3 * 5 * 6
+    assert solver.prior_energy(ramp) == pytest.approx(want, rel=1e-14)
+
+
+# ---------------------------------------------------------------- CG
+
+def _dense_problem():
+    g = synth.cube_geom(5, 1.5, ny=4, nz=4)
+    rng = np.random.default_rng(9)
+    ptg = synth.pointing_table(rng.uniform(0, 360, 6), rng.uniform(-30, 30, 6),
+                               215.0, 8, 8, 3.4)
+    mask = (rng.random((6, 8, 8)) < 0.15).astype(np.uint8)
+    x_true = rng.random((4, 4, 5))
+    y = siddon.project(g, x_true, ptg, 8, 8, mask) + 0.01 * rng.standard_normal(
+        (6, 8, 8))
+    return solver.Problem(g, ptg, 8, 8, y, mask, lam=0.3)
+
+
+def test_cg_matches_direct_solve():
+    """CG on the normal equations reaches the direct solution of
+    (A^T A + lambda B^T B) x = A^T y (Eq. criterion) built from dense
+    brute-force rows and dense difference matrices."""
+    pb = _dense_problem()
+    g = pb.geom
+    nvox = 80
+    A = np.zeros((6 * 64, nvox))
+    for r in range(6 * 64):
+        n, iv, iu = r // 64, (r // 8) % 8, r % 8
+        if pb.mask.reshape(-1)[r]:
+            continue
+        o, u = siddon.ray(pb.pointing[n], iu, iv)
+        A[r] = checks.brute_force_ray(g, o, u)
+    # dense forward-difference matrices, built from index arithmetic
+    rows = []
+    for (dk, dj, di) in ((0, 0, 1), (0, 1, 0), (1, 0, 0)):
+        for k in range(4 - dk):
+            for j in range(4 - dj):
+                for i in range(5 - di):
+                    row = np.zeros(nvox)
+                    row[((k + dk) * 4 + j + dj) * 5 + i + di] += 1
+                    row[(k * 4 + j) * 5 + i] -= 1
+                    rows.append(row)
+    B = np.array(rows)
+    ym = np.where(pb.mask == 0, pb.y, 0.0).reshape(-1)
+    x_direct = np.linalg.solve(A.T @ A + pb.lam * B.T @ B, A.T @ ym)
+    x_cg, rep = solver.cg(pb, 400)
+    np.testing.assert_allclose(x_cg.reshape(-1), x_direct, rtol=0,
+                               atol=1e-9 * np.abs(x_direct).max())
+    J = rep["J"]
+    assert np.all(np.diff(J) <= 1e-12 * J[0])  # non-increasing
+    Jmin = float(np.sum((ym - A @ x_direct) ** 2) + pb.lam * np.sum((B @ x_direct) ** 2))
+    assert J[-1] == pytest.approx(Jmin, rel=1e-10)
+
+
+def test_cg_warm_start_and_J_identity():
+    """CG from a warm start continues the same minimisation; and
+    J(x) = y^T M y - x^T (r + b) holds for every iterate (the identity the
+    device solver reports J through)."""
+    pb = _dense_problem()
+    x5, rep5 = solver.cg(pb, 5)
+    b = pb.rhs()
+    r = b - pb.normal(x5)
+    ym = pb.masked(pb.y)
+    assert pb.J(x5) == pytest.approx(float(np.sum(ym * ym) - np.sum(x5 * (r + b))),
+                                     rel=1e-10)
+    x_more, rep_more = solver.cg(pb, 30, x0=x5)
+    assert rep_more["J"][-1] <= rep5["J"][-1]
