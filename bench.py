@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Throughput of the Siddon projector, its transpose and the CG solver.
+
+One step = one ``tomo_solve`` call on the 256^3 workload: FP64 ray setup,
+b = P^T M y, then ``--iters`` CG iterations (each one P, one D^T D, one P^T
+and the vector updates), all through the C ABI.  The reported value is
+voxel-intersections (Siddon segments) per second over P and P^T:
+segments per projection x (2 iters + 1) per step.
+
+Default workload ``cg256``: cube 256^3 float32 over [-1.5, 1.5]^3 R_sun,
+240 images 512 x 512 from two observer groups 40 degrees apart (1.5 degree
+steps, 215 R_sun, FOV 3.2 R_sun), occulter mask r < 1 R_sun, data = P x +
+Gaussian noise at SNR 50, lambda 1e-2, 3-axis finite-difference prior.
+
+``--impl reference`` times the FP64 CPU oracle instead (P and P^T over a
+seeded ray sample of the same workload) on the host cores.
+
+Multi-GPU: the path has no exchange step that this benchmark needs; with
+``--gpus N`` under torchrun every rank runs an independent replica of the
+workload (weak scaling), and the value counts the work of all ranks over the
+slowest rank's time.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("Siddon voxel-intersections/s (P and P^T) and CG s/iter at 256^3, "
+          "vs FP64 oracle")
+UNIT = "voxel-intersections/s"
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOAD_TEXT = {
+    "cg256": ("cg256: cube 256^3 f32 over [-1.5,1.5]^3 R_sun; 240 images "
+              "512x512 from two observer groups 40 deg apart (1.5 deg steps, "
+              "215 R_sun, FOV 3.2 R_sun); occulter mask r<1 R_sun; y = Px + "
+              "noise at SNR 50; lambda 1e-2, 3-axis finite-difference prior"),
+    "single": ("single: cube 128^3 f32; 60 images 256x256, lon 0-177 deg, "
+               "lat jitter +-7 deg; 6 streamers; occulter r<1; SNR 50; "
+               "lambda 1e-2"),
+}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="cg256", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--iters", type=int, default=20,
+                    help="CG iterations per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------- distributed
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def aggregate(units, seconds, world):
+    """Whole-job throughput: units of all ranks over the slowest rank's
+    time.  Returns (total_units, max_seconds)."""
+    if world <= 1:
+        return float(units), float(seconds)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    s = torch.tensor([float(seconds)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(s.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+             "sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        self.index = vis.split(",")[local_rank] if vis else str(local_rank)
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv",
+                                               delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-i", self.index,
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.out.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- workload
+
+def make_workload(name):
+    import synth
+    return synth.make_config(name)
+
+
+def algorithmic_bytes(n_rays, n_live, segments, kind):
+    """Bytes a launch must move if nothing is cached (gather model):
+    4 B per segment (voxel gather, or atomic payload for the transpose),
+    the 32-byte ray record of every live ray, 1 mask byte per pixel, and
+    the 4-byte pixel (written by P for every pixel, read by P^T per live
+    ray)."""
+    per_pixel = 4 * n_rays if kind == "forward" else 4 * n_live
+    return 4.0 * segments + 32.0 * n_live + 1.0 * n_rays + per_pixel
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` recorded in profiles/, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------- oracle legs
+
+def oracle_sample(c, seconds, seed=0):
+    """Time the FP64 oracle (P then P^T) on a seeded ray sample sized to
+    take about `seconds`.  Returns (segments/s, threads, description)."""
+    from oracle import siddon
+    g, ptg, nu, nv, mask = c["geom"], c["pointing"], c["nu"], c["nv"], c["mask"]
+    n_all = ptg.shape[0] * nu * nv
+    live = np.flatnonzero(mask.reshape(-1) == 0) if mask is not None else \
+        np.arange(n_all)
+    cube = c["cube"].astype(np.float64)
+    rng = np.random.default_rng(seed)
+    images = np.zeros(n_all)
+
+    def run(frac):
+        ids = np.sort(rng.choice(live, max(1, int(frac * live.size)),
+                                 replace=False))
+        segs = siddon.count_segments(g, ptg, nu, nv, None, ray_ids=ids)
+        t0 = time.perf_counter()
+        vals = siddon.project(g, cube, ptg, nu, nv, None, ray_ids=ids)
+        images[ids] = vals
+        siddon.backproject(g, images, ptg, nu, nv, None, ray_ids=ids)
+        dt = time.perf_counter() - t0
+        images[ids] = 0.0
+        return ids.size, segs, dt
+
+    n, segs, dt = run(2e-4)  # calibrate
+    rate = 2 * segs / max(dt, 1e-6)
+    frac = min(1.0, 2e-4 * seconds / max(dt, 1e-6))
+    n, segs, dt = run(frac)
+    desc = ("FP64 oracle P then P^T over a seeded sample of %d unmasked rays "
+            "(%.3f %% of %s, %d segments each way)"
+            % (n, 100.0 * n / live.size, c["name"], segs))
+    return 2 * segs / dt, siddon.get_threads(), desc, 2 * segs, dt
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, on the host cores."""
+    if rank != 0:
+        return 0
+    c = make_workload(args.workload)
+    per_step = max(0.5, min(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(c, per_step, seed=1)
+    rates, times, units, descs, cores = [], [], [], [], 1
+    for k in range(args.steps):
+        rate, cores, desc, segs, dt = oracle_sample(c, per_step, seed=100 + k)
+        units.append(segs)
+        times.append(dt)
+        descs.append(desc)
+    value = float(sum(units) / sum(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT[args.workload]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": descs[0]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank, local_rank, world):
+    import torch
+    import synth
+    import paper_1103_5904_gb300 as T
+    from paper_1103_5904_gb300 import build as lib_build
+
+    lib_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    c = make_workload(args.workload)
+    g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
+    n_img = ptg.shape[0]
+    ctx = T.Context(local_rank)
+    mask_h = c["mask"]
+    mask = torch.from_numpy(mask_h).to(dev) if mask_h is not None else None
+    x_true = torch.from_numpy(c["cube"]).to(dev)
+    # data: P x + Gaussian noise (seeded draws, SNR of the workload)
+    y0 = T.tomo_project(x_true, g, ptg, nu, nv, mask=mask, ctx=ctx)
+    keep = (mask == 0) if mask is not None else torch.ones_like(y0, dtype=bool)
+    rms = torch.sqrt(torch.mean(y0[keep].double() ** 2)).item()
+    z = torch.from_numpy(synth.noise_draw(c["noise_seed"] or 0, y0.shape)).to(dev)
+    y = (y0.double() + (rms / (c["snr"] or 50.0)) * z).float()
+    if mask is not None:
+        y[mask != 0] = 0.0
+    del z, y0
+    n_rays = n_img * nu * nv
+    n_live = int(keep.sum().item())
+    segments = T.tomo_count_segments(g, ptg, nu, nv, mask=mask, ctx=ctx)
+    units_per_step = segments * (2 * args.iters + 1)
+    x = torch.empty_like(x_true)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.clear_cache()  # every step redoes the FP64 ray setup
+        T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"], max_iter=args.iters,
+                     out=x, report=False, ctx=ctx)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    _, info = T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"],
+                           max_iter=args.iters, out=x, ctx=ctx)
+    ctx.set_option(T.tomo.TOMO_OPT_PROFILE, 1)
+    ctx.profile(reset=True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between steps (outside the step events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = ctx.profile(reset=True)
+    ctx.set_option(T.tomo.TOMO_OPT_PROFILE, 0)
+    local_s = sum(step_ms) / 1e3
+    tot_units, max_s = aggregate(units_per_step * args.steps, local_s, world)
+    value = tot_units / max_s
+    ms_per_step = 1e3 * max_s / args.steps
+
+    # roofline of the dominant Siddon kernel (launch-averaged device time)
+    kern = {}
+    for kind in ("forward", "adjoint"):
+        launches, ms = prof[kind]
+        if launches == 0:
+            continue
+        per_launch_s = ms / 1e3 / launches
+        b = algorithmic_bytes(n_rays, n_live, segments, kind)
+        kern[kind] = {"launches": launches, "ms_per_launch": 1e3 * per_launch_s,
+                      "segments_per_s": segments / per_launch_s,
+                      "rays_per_s": n_rays / per_launch_s,
+                      "algorithmic_bytes": b,
+                      "achieved_gbs": b / per_launch_s / 1e9,
+                      "time_share": ms / sum(v[1] for v in prof.values())}
+    dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    peak, peak_src = peak_hbm()
+    kname = {"forward": "k_forward<float,false>", "adjoint": "k_adjoint<false>"}
+    roofline = {"bound": "hbm", "kernel": kname[dom],
+                "achieved": kern[dom]["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
+                "traffic": ncu_traffic(kname[dom]),
+                "peak_source": peak_src + " HBM copy bandwidth",
+                "bytes_model": "4 B/segment + 37 B/live ray + 1 B/pixel"}
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # end to end through the C ABI with host buffers: H2D of y and mask from
+    # pinned memory, solve, D2H of x, every step
+    e2e = None
+    if not args.no_e2e:
+        y_h = y.cpu().pin_memory()
+        m_h = mask.cpu().pin_memory() if mask is not None else None
+        x_h = torch.empty(x.shape, dtype=torch.float32).pin_memory()
+        y_d = torch.empty_like(y)
+        m_d = torch.empty_like(mask) if mask is not None else None
+        h2d = y_h.numel() * 4 + (m_h.numel() if m_h is not None else 0)
+        d2h = x_h.numel() * 4
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            y_d.copy_(y_h, non_blocking=True)
+            if m_h is not None:
+                m_d.copy_(m_h, non_blocking=True)
+            ctx.clear_cache()
+            T.tomo_solve(y_d, g, ptg, mask=m_d, lam=c["lam"],
+                         max_iter=args.iters, out=x, report=False, ctx=ctx)
+            x_h.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_units, e_s = aggregate(units_per_step * args.steps,
+                                 e0.elapsed_time(e1) / 1e3, world)
+        e2e = {"value": e_units / e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc, _, _ = oracle_sample(c, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOAD_TEXT[args.workload],
+                "step": ("one tomo_solve: FP64 ray setup, b = P^T M y, %d CG "
+                         "iterations" % args.iters),
+                "cg_iters_per_step": args.iters,
+                "rays": n_rays, "live_rays": n_live,
+                "segments_per_projection": segments,
+                "segments_per_step": units_per_step,
+                "l2": "flushed between steps (512 MiB write)",
+                "parallelism": "replicas" if world > 1 else "single GPU"},
+            "cg_s_per_iter": ms_per_step / 1e3 / args.iters,
+            "final_J_over_J0": float(info["J"][-1] / info["J"][0]),
+            "kernels": kern,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, local_rank, world = dist_env()
+    if world != args.gpus:
+        if world == 1 and args.gpus > 1:
+            print("run --gpus %d under torchrun (one process per GPU)"
+                  % args.gpus, file=sys.stderr)
+            return 2
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, local_rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,224 @@
+/*
+ * tomo.h — C ABI of the GB300 solar-tomography projector library (libtomo).
+ *
+ * The library implements the line-of-sight projector P of TomograPy
+ * (Barbey, Guennou & Auchere; Section 3.3.1, Eq. lo), its exact transpose
+ * P^T, and a conjugate-gradient inversion of the regularised least-squares
+ * criterion built on them (Section 2.2, Eq. criterion), on one NVIDIA GB300
+ * (sm_103a).  Every step runs in the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Cube: identical rectangular voxels (Section 3.3.1: required by Siddon),
+ *    laid out [nz][ny][nx] with x fastest; with n_frames = T > 1 the frames
+ *    are stacked as [T][nz][ny][nx].
+ *  - Images: [n_img][nv][nu] float32, u fastest; one pointing record per image.
+ *  - Pointing (Section 3.2, WCS keywords): Sun-centred frame, z = solar
+ *    rotation axis, x at longitude 0; observer o = d (cos lat cos lon,
+ *    cos lat sin lon, sin lat); boresight w = -o/|o|; e1 = unit(w x z),
+ *    e2 = e1 x w, both turned by `roll` about w; gnomonic (TAN) pixels:
+ *    theta_u = (i_u - crpix_u) cdelt_u + crval_u (likewise v), ray direction
+ *    unit(w + tan(theta_u) e1 + tan(theta_v) e2).  Angles in radians,
+ *    distances in the cube's length unit.  The paper names the keywords but
+ *    not these formulas; this is the library's reading.
+ *  - Voxels are half-open, [x0 + i dx, x0 + (i+1) dx): a ray lying exactly on
+ *    a face is charged to the voxel above it.
+ *  - Masks: uint8 [n_img][nv][nu], nonzero = excluded (Section 4: masked
+ *    pixels are not projected).  P writes 0 there, P^T ignores them.
+ *  - Gains: each image is scaled by its record's gain (Eq. two_spacecraft,
+ *    Eq. lin2space).
+ *  - Time (Section 3.3.3, a parameterised temporal evolution): with T > 1
+ *    frames an image with time stamp tau in [0, T-1] sees
+ *    (1 - w) X[k] + w X[k+1], k = min(floor(tau), T-2), w = tau - k.
+ *  - Pointers named *_dev are device pointers, *_host host pointers.  All
+ *    buffers belong to the caller; the library keeps no pointer to them
+ *    after a call returns.  The library allocates only its own workspace
+ *    (ray records, solver vectors), owned by the context.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - Errors: every entry point validates its arguments before any launch
+ *    and returns a tomo_status; it never aborts.  tomo_last_error() gives a
+ *    one-line message.  A context must not be used by two host threads at
+ *    once.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TOMO_OK = 0,
+    TOMO_ERR_ARG = -1,         /* invalid argument (pointer, size, geometry) */
+    TOMO_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    TOMO_ERR_UNSUPPORTED = -3, /* valid but not supported (e.g. no sm_103a) */
+    TOMO_ERR_OOM = -4,         /* workspace allocation failed */
+    TOMO_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    TOMO_ERR_NUMERIC = -6      /* solver breakdown (non-positive or NaN p.q) */
+} tomo_status;
+
+typedef enum {
+    TOMO_F32 = 0,  /* float32 cube */
+    TOMO_BF16 = 1  /* bfloat16 cube, widened to float32 on load */
+} tomo_dtype;
+
+/* Cube geometry: voxel counts, minimum corner (x0, y0, z0) and voxel size
+ * (dx, dy, dz > 0).  `reserved` must be 0. */
+typedef struct {
+    int32_t nx, ny, nz, reserved;
+    double x0, y0, z0;
+    double dx, dy, dz;
+} tomo_cube_geom;
+
+/* Image stack geometry: n_img images of nv rows by nu columns. */
+typedef struct {
+    int32_t n_img, nu, nv;
+} tomo_image_geom;
+
+/* One pointing record (96 bytes; the 12 doubles of one row of a float64
+ * (n_img, 12) table, in this order). */
+typedef struct {
+    double d_obs, lon, lat, roll;
+    double cdelt_u, cdelt_v, crpix_u, crpix_v, crval_u, crval_v;
+    double gain, time;
+} tomo_pointing;
+
+typedef struct tomo_ctx tomo_ctx;
+
+/* Flags */
+#define TOMO_ACCUMULATE   1u  /* backproject: add into cube_dev (else overwrite) */
+#define TOMO_SOLVE_X0     2u  /* solve: start from x_dev (else from 0) */
+#define TOMO_SOLVE_BF16   4u  /* solve: gather the CG direction from a bf16 copy */
+
+/* Options for tomo_set_option */
+#define TOMO_OPT_RAY_CACHE  1  /* 1 (default): keep ray records per geometry */
+#define TOMO_OPT_TILE_U     2  /* pixel tile width of one CTA (default 32) */
+#define TOMO_OPT_TILE_V     3  /* pixel tile height of one CTA (default 8) */
+#define TOMO_OPT_WARP_U     4  /* pixel tile width of one warp (default 8) */
+#define TOMO_OPT_PROFILE    5  /* 1: time every kernel launch with CUDA events */
+
+/* Kernel classes of tomo_profile */
+enum {
+    TOMO_K_SETUP = 0,   /* pointing -> ray records (FP64) */
+    TOMO_K_FORWARD = 1, /* Siddon gather, P */
+    TOMO_K_ADJOINT = 2, /* Siddon scatter, P^T */
+    TOMO_K_PRIOR = 3,   /* D^T D stencil */
+    TOMO_K_VECTOR = 4,  /* CG vector updates and reductions */
+    TOMO_K_COUNT = 5
+};
+
+/* Per kernel class: launches since the last reset and, with
+ * TOMO_OPT_PROFILE on, their summed device time in milliseconds (CUDA events
+ * recorded on the launching stream around each launch). */
+typedef struct {
+    int64_t launches[TOMO_K_COUNT];
+    double ms[TOMO_K_COUNT];
+} tomo_profile;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Returns TOMO_ERR_UNSUPPORTED if the device is not sm_103. */
+tomo_status tomo_create(tomo_ctx **ctx_out, int32_t device);
+
+/* Free the context and its workspace.  NULL is accepted.  The caller makes
+ * sure no work of the context is still running. */
+void tomo_destroy(tomo_ctx *ctx);
+
+/* Static text of a status code. */
+const char *tomo_status_string(tomo_status status);
+
+/* Message of the context's last error ("" if none).  Valid until the next
+ * call on the context. */
+const char *tomo_last_error(const tomo_ctx *ctx);
+
+/* Set an option (see TOMO_OPT_*).  Tile options must satisfy
+ * tile_u * tile_v <= 512, tile_u % warp_u == 0, tile_v % (32 / warp_u) == 0;
+ * they are checked at the next launch. */
+tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value);
+
+/* Drop the cached ray records (the memory stays with the context). */
+tomo_status tomo_clear_cache(tomo_ctx *ctx);
+
+/* Read the launch counts and timings gathered so far (waits for the pending
+ * timing events), then zero them if `reset` is nonzero. */
+tomo_status tomo_profile_read(tomo_ctx *ctx, tomo_profile *out, int32_t reset);
+
+/* Forward projection y = P x (Eq. lo for one image, stacked over images as in
+ * Eq. srt; gains per Eq. lin2space; time interpolation per Section 3.3.3).
+ *   cube:          geometry of one frame
+ *   n_frames:      T >= 1 frames in cube_dev
+ *   cube_dev:      [T][nz][ny][nx] of `dtype` (4- or 2-byte aligned)
+ *   img:           image stack geometry
+ *   pointing_host: n_img records (copied during the call)
+ *   mask_dev:      nullable; nonzero pixels are written as 0
+ *   images_dev:    [n_img][nv][nu] float32, overwritten
+ * Ray records are computed in FP64 by a setup kernel and cached in the
+ * context, keyed by (cube, img, pointing) contents. */
+tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                         int32_t n_frames, const void *cube_dev,
+                         tomo_dtype dtype, const tomo_image_geom *img,
+                         const tomo_pointing *pointing_host,
+                         const uint8_t *mask_dev, float *images_dev,
+                         void *stream);
+
+/* Backprojection x = P^T y: the exact transpose of tomo_project with the
+ * same arguments (same segments, lengths, mask, gains and time weights).
+ *   images_dev: [n_img][nv][nu] float32 input
+ *   cube_dev:   [T][nz][ny][nx] float32 output; overwritten unless
+ *               flags has TOMO_ACCUMULATE
+ * Results are accumulated with float32 atomics, so the summation order and
+ * the last bits vary from run to run. */
+tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                             int32_t n_frames, const tomo_image_geom *img,
+                             const tomo_pointing *pointing_host,
+                             const uint8_t *mask_dev, const float *images_dev,
+                             float *cube_dev, uint32_t flags, void *stream);
+
+/* Regularised least squares (Eq. criterion with A = M P, B = D):
+ *     x = argmin ||M (y - P x)||^2 + lambda ||D x||^2 ,
+ * D = forward differences along x, y, z without wrap (Section 3.3.1, "a
+ * finite-difference operator along each axis"), by conjugate gradients on
+ * (P^T M P + lambda D^T D) x = P^T M y, one static frame, FP32 vectors and
+ * FP64 scalars (alpha, beta, residual norms, J).
+ *   y_dev:       [n_img][nv][nu] float32 data
+ *   x_dev:       [nz][ny][nx] float32; initial guess if flags has
+ *                TOMO_SOLVE_X0 (else start from 0); receives the result
+ *   lambda:      >= 0
+ *   max_iter:    >= 0 iterations
+ *   tol:         stop once ||r_k|| <= tol ||r_0|| (0 = run max_iter)
+ *   flags:       TOMO_SOLVE_X0, TOMO_SOLVE_BF16
+ *   report_host: nullable; (max_iter + 1) x 2 doubles: for every iterate k,
+ *                J(x_k) (through J = y^T M y - x^T (r + b), b = P^T M y) and
+ *                ||r_k||^2.  Rows past the last iteration are NaN.
+ *   iters_host:  nullable; receives the number of iterations done
+ * No host synchronisation happens inside the loop.  If report_host or
+ * iters_host is given, the call synchronises `stream` before returning. */
+tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                       const tomo_image_geom *img,
+                       const tomo_pointing *pointing_host,
+                       const uint8_t *mask_dev, const float *y_dev,
+                       float *x_dev, double lambda, int32_t max_iter,
+                       double tol, uint32_t flags, double *report_host,
+                       int32_t *iters_host, void *stream);
+
+/* q = lambda D^T D x (+ q if flags has TOMO_ACCUMULATE), the gradient of the
+ * prior term lambda ||D x||^2 / 2 (Section 3.3.1); x, q: [nz][ny][nx] f32. */
+tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                             const float *x_dev, float *q_dev, double lambda,
+                             uint32_t flags, void *stream);
+
+/* Number of positive-length voxel intersections (Siddon segments) of the
+ * unmasked rays, counted on the device with the projector's own walk. */
+tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                                const tomo_image_geom *img,
+                                const tomo_pointing *pointing_host,
+                                const uint8_t *mask_dev, int64_t *count_host,
+                                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOMO_H */

@@ -1,0 +1,725 @@
+// C ABI of libtomo: argument validation, workspace, ray-record cache and the
+// orchestration of the projector and of the CG solver.  Declarations and the
+// contract of every entry point are in include/tomo.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tomo_internal.cuh"
+
+using namespace tomo;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tomo_ctx {
+    int device = 0;
+    int num_sms = 0;
+    char err[512] = { 0 };
+    bool ray_cache = true;
+    Tiling tiling = { 32, 8, 8 };
+    // geometry cache
+    bool key_valid = false;
+    uint64_t key = 0;
+    cudaEvent_t setup_done = nullptr;
+    // per-geometry buffers
+    DevBuf ptg, frames, tan_u, tan_v, params, rays;
+    // solver workspace
+    DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
+    // launch counts and optional per-launch event timing
+    bool profile = false;
+    int64_t launches[TOMO_K_COUNT] = { 0 };
+    double ms[TOMO_K_COUNT] = { 0 };
+    std::vector<cudaEvent_t> ev_start, ev_stop;  // event pool (pairs)
+    std::vector<int> ev_free;                    // free pair slots
+    std::vector<int> ev_pending_slot, ev_pending_kind;
+};
+
+namespace {
+
+tomo_status fail(tomo_ctx *ctx, tomo_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess)                                               \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation               \
+                                   ? TOMO_ERR_OOM : TOMO_ERR_CUDA,           \
+                        "%s: %s", #call, cudaGetErrorString(e_));            \
+    } while (0)
+
+// Launch a kernel through its host launcher `call`, counted and (optionally)
+// timed as class `kind` on stream `s`.
+#define LAUNCH(ctx, kind, s, call)                                           \
+    do {                                                                     \
+        Launch L_((ctx), (kind), (s));                                       \
+        CUDA_TRY((ctx), (call));                                             \
+    } while (0)
+
+// Makes the context's device current for the call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Counts one kernel launch of class `kind`; with profiling on, brackets it
+// with a pair of CUDA events on the launching stream.
+struct Launch {
+    tomo_ctx *ctx;
+    int kind;
+    cudaStream_t s;
+    int slot = -1;
+    Launch(tomo_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k), s(st)
+    {
+        ctx->launches[kind] += 1;
+        if (!ctx->profile) return;
+        if (ctx->ev_free.empty()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) {
+                cudaEventDestroy(a);
+                return;
+            }
+            ctx->ev_start.push_back(a);
+            ctx->ev_stop.push_back(b);
+            ctx->ev_free.push_back((int)ctx->ev_start.size() - 1);
+        }
+        slot = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        cudaEventRecord(ctx->ev_start[slot], s);
+    }
+    ~Launch()
+    {
+        if (slot < 0) return;
+        cudaEventRecord(ctx->ev_stop[slot], s);
+        ctx->ev_pending_slot.push_back(slot);
+        ctx->ev_pending_kind.push_back(kind);
+    }
+};
+
+tomo_status ensure(tomo_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TOMO_OK;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess)
+            return fail(ctx, TOMO_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, TOMO_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+    return TOMO_OK;
+}
+
+bool finite_all(const double *v, int n)
+{
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+tomo_status check_cube(tomo_ctx *ctx, const tomo_cube_geom *c, int32_t n_frames)
+{
+    if (!c) return fail(ctx, TOMO_ERR_ARG, "cube geometry is NULL");
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1)
+        return fail(ctx, TOMO_ERR_ARG, "cube counts must be >= 1 (got %d %d %d)",
+                    c->nx, c->ny, c->nz);
+    if (c->reserved != 0)
+        return fail(ctx, TOMO_ERR_ARG, "cube geometry: reserved must be 0");
+    const double v[6] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz };
+    if (!finite_all(v, 6) || !(c->dx > 0) || !(c->dy > 0) || !(c->dz > 0))
+        return fail(ctx, TOMO_ERR_ARG, "cube corner/voxel size must be finite, "
+                                       "voxel size > 0");
+    const int64_t nvox = (int64_t)c->nx * c->ny * c->nz;
+    if (nvox > INT32_MAX)
+        return fail(ctx, TOMO_ERR_UNSUPPORTED,
+                    "cube of %lld voxels exceeds 2^31-1 per frame",
+                    (long long)nvox);
+    if (n_frames < 1 || n_frames > 65535)
+        return fail(ctx, TOMO_ERR_ARG, "n_frames must be in [1, 65535]");
+    if (c->nz > 65535)
+        return fail(ctx, TOMO_ERR_UNSUPPORTED, "nz > 65535");
+    return TOMO_OK;
+}
+
+tomo_status check_img(tomo_ctx *ctx, const tomo_image_geom *g)
+{
+    if (!g) return fail(ctx, TOMO_ERR_ARG, "image geometry is NULL");
+    if (g->n_img < 0 || g->n_img > 65535)
+        return fail(ctx, TOMO_ERR_ARG, "n_img must be in [0, 65535]");
+    if (g->n_img > 0 && (g->nu < 1 || g->nv < 1 || g->nu > 1 << 20 ||
+                         g->nv > 1 << 19))
+        return fail(ctx, TOMO_ERR_ARG, "image size out of range (%d x %d)",
+                    g->nu, g->nv);
+    return TOMO_OK;
+}
+
+tomo_status check_pointing(tomo_ctx *ctx, const tomo_pointing *p,
+                           const tomo_image_geom *g, int32_t n_frames)
+{
+    if (g->n_img == 0) return TOMO_OK;
+    if (!p) return fail(ctx, TOMO_ERR_ARG, "pointing table is NULL");
+    const double half_pi = 1.5707963267948966;
+    for (int32_t n = 0; n < g->n_img; ++n) {
+        const tomo_pointing &q = p[n];
+        if (!finite_all(&q.d_obs, 12))
+            return fail(ctx, TOMO_ERR_ARG, "pointing %d: non-finite field", n);
+        if (!(q.d_obs > 0))
+            return fail(ctx, TOMO_ERR_ARG, "pointing %d: d_obs must be > 0", n);
+        if (!(fabs(cos(q.lat)) > 1e-9))
+            return fail(ctx, TOMO_ERR_ARG,
+                        "pointing %d: |lat| = 90 deg leaves the frame undefined", n);
+        const double th[4] = {
+            (0 - q.crpix_u) * q.cdelt_u + q.crval_u,
+            (g->nu - 1 - q.crpix_u) * q.cdelt_u + q.crval_u,
+            (0 - q.crpix_v) * q.cdelt_v + q.crval_v,
+            (g->nv - 1 - q.crpix_v) * q.cdelt_v + q.crval_v };
+        for (int i = 0; i < 4; ++i)
+            if (!(fabs(th[i]) < half_pi - 1e-6))
+                return fail(ctx, TOMO_ERR_ARG,
+                            "pointing %d: pixel angle reaches 90 deg", n);
+        if (n_frames > 1 && !(q.time >= 0.0 && q.time <= n_frames - 1))
+            return fail(ctx, TOMO_ERR_ARG,
+                        "pointing %d: time %g outside [0, %d]", n, q.time,
+                        n_frames - 1);
+    }
+    return TOMO_OK;
+}
+
+tomo_status check_tiling(tomo_ctx *ctx)
+{
+    const Tiling t = ctx->tiling;
+    const int wu = t.warp_u;
+    if (wu < 1 || wu > 32 || (wu & (wu - 1)) != 0)
+        return fail(ctx, TOMO_ERR_ARG, "warp_u must be a power of 2 in [1, 32]");
+    if (t.tile_u < 1 || t.tile_v < 1 || t.tile_u % wu != 0 ||
+        t.tile_v % (32 / wu) != 0 || t.tile_u * t.tile_v > 512)
+        return fail(ctx, TOMO_ERR_ARG,
+                    "tile %dx%d incompatible with warp_u %d (<= 512 threads)",
+                    t.tile_u, t.tile_v, wu);
+    return TOMO_OK;
+}
+
+bool aligned(const void *p, size_t a)
+{
+    return ((uintptr_t)p % a) == 0;
+}
+
+uint64_t fnv1a(uint64_t h, const void *data, size_t n)
+{
+    const unsigned char *c = (const unsigned char *)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+CubeDev cube_dev(const tomo_cube_geom *c)
+{
+    CubeDev d;
+    d.nx = c->nx;
+    d.ny = c->ny;
+    d.nz = c->nz;
+    d.lo[0] = c->x0;
+    d.lo[1] = c->y0;
+    d.lo[2] = c->z0;
+    d.d[0] = c->dx;
+    d.d[1] = c->dy;
+    d.d[2] = c->dz;
+    return d;
+}
+
+// Builds (or reuses) the ray records and image parameters of a geometry on
+// `s`.  On return, work on `s` is ordered after the records are complete.
+tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
+                         int32_t n_frames, const tomo_image_geom *g,
+                         const tomo_pointing *ptg, cudaStream_t s)
+{
+    uint64_t h = 1469598103934665603ull;
+    const int32_t cn[4] = { c->nx, c->ny, c->nz, n_frames };
+    const double cv[6] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz };
+    h = fnv1a(h, cn, sizeof(cn));
+    h = fnv1a(h, cv, sizeof(cv));
+    h = fnv1a(h, g, sizeof(*g));
+    h = fnv1a(h, ptg, sizeof(tomo_pointing) * (size_t)g->n_img);
+    if (ctx->ray_cache && ctx->key_valid && ctx->key == h) {
+        CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
+        return TOMO_OK;
+    }
+    ctx->key_valid = false;
+    const size_t n_img = (size_t)g->n_img;
+    const size_t npix = n_img * g->nu * g->nv;
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->ptg, sizeof(tomo_pointing) * n_img)) ||
+        (st = ensure(ctx, ctx->frames, sizeof(Frame) * n_img)) ||
+        (st = ensure(ctx, ctx->tan_u, sizeof(double) * n_img * g->nu)) ||
+        (st = ensure(ctx, ctx->tan_v, sizeof(double) * n_img * g->nv)) ||
+        (st = ensure(ctx, ctx->params, sizeof(ImgParam) * n_img)) ||
+        (st = ensure(ctx, ctx->rays, sizeof(RayRec) * npix)))
+        return st;
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
+                                  cudaMemcpyHostToDevice, s));
+    LAUNCH(ctx, TOMO_K_SETUP, s,
+           launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
+                         g->nv, n_frames, (Frame *)ctx->frames.p,
+                         (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
+                         (ImgParam *)ctx->params.p, s));
+    LAUNCH(ctx, TOMO_K_SETUP, s,
+           launch_ray_setup((const Frame *)ctx->frames.p,
+                            (const double *)ctx->tan_u.p,
+                            (const double *)ctx->tan_v.p, cube_dev(c),
+                            g->n_img, g->nu, g->nv, (RayRec *)ctx->rays.p, s));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->setup_done, s));
+    ctx->key = h;
+    ctx->key_valid = true;
+    return TOMO_OK;
+}
+
+tomo_status common_checks(tomo_ctx *ctx, const tomo_cube_geom *c,
+                          int32_t n_frames, const tomo_image_geom *g,
+                          const tomo_pointing *ptg)
+{
+    tomo_status st;
+    if ((st = check_cube(ctx, c, n_frames)) || (st = check_img(ctx, g)) ||
+        (st = check_pointing(ctx, ptg, g, n_frames)) ||
+        (st = check_tiling(ctx)))
+        return st;
+    return TOMO_OK;
+}
+
+int reduce_grid(const tomo_ctx *ctx, int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    int64_t cap = 4LL * (ctx->num_sms > 0 ? ctx->num_sms : 152);
+    if (cap > kMaxReduceBlocks) cap = kMaxReduceBlocks;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tomo_status_string(tomo_status s)
+{
+    switch (s) {
+    case TOMO_OK: return "ok";
+    case TOMO_ERR_ARG: return "invalid argument";
+    case TOMO_ERR_CUDA: return "CUDA error";
+    case TOMO_ERR_UNSUPPORTED: return "unsupported";
+    case TOMO_ERR_OOM: return "out of device memory";
+    case TOMO_ERR_TIMEOUT: return "device wait timed out";
+    case TOMO_ERR_NUMERIC: return "numerical breakdown";
+    }
+    return "unknown status";
+}
+
+const char *tomo_last_error(const tomo_ctx *ctx)
+{
+    return ctx ? ctx->err : "";
+}
+
+tomo_status tomo_create(tomo_ctx **out, int32_t device)
+{
+    if (!out) return TOMO_ERR_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 ||
+        device >= count) {
+        cudaGetLastError();
+        return TOMO_ERR_ARG;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return TOMO_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return TOMO_ERR_UNSUPPORTED;
+    DeviceGuard guard(device);
+    if (!guard.ok) return TOMO_ERR_CUDA;
+    tomo_ctx *ctx = new tomo_ctx();
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    if (cudaEventCreateWithFlags(&ctx->setup_done, cudaEventDisableTiming) !=
+        cudaSuccess) {
+        delete ctx;
+        return TOMO_ERR_CUDA;
+    }
+    *out = ctx;
+    return TOMO_OK;
+}
+
+void tomo_destroy(tomo_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    DevBuf *bufs[] = { &ctx->ptg, &ctx->frames, &ctx->tan_u, &ctx->tan_v,
+                       &ctx->params, &ctx->rays, &ctx->b, &ctx->r, &ctx->p,
+                       &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
+                       &ctx->counter, &ctx->count64 };
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (ctx->setup_done) cudaEventDestroy(ctx->setup_done);
+    for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ev_stop) cudaEventDestroy(e);
+    delete ctx;
+}
+
+tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    switch (option) {
+    case TOMO_OPT_RAY_CACHE:
+        ctx->ray_cache = value != 0;
+        if (!ctx->ray_cache) ctx->key_valid = false;
+        return TOMO_OK;
+    case TOMO_OPT_TILE_U:
+        if (value < 1 || value > 512) break;
+        ctx->tiling.tile_u = (int32_t)value;
+        return TOMO_OK;
+    case TOMO_OPT_TILE_V:
+        if (value < 1 || value > 512) break;
+        ctx->tiling.tile_v = (int32_t)value;
+        return TOMO_OK;
+    case TOMO_OPT_WARP_U:
+        if (value < 1 || value > 32) break;
+        ctx->tiling.warp_u = (int32_t)value;
+        return TOMO_OK;
+    case TOMO_OPT_PROFILE:
+        ctx->profile = value != 0;
+        return TOMO_OK;
+    default:
+        return fail(ctx, TOMO_ERR_ARG, "unknown option %d", option);
+    }
+    return fail(ctx, TOMO_ERR_ARG, "option %d: value %lld out of range", option,
+                (long long)value);
+}
+
+tomo_status tomo_clear_cache(tomo_ctx *ctx)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->key_valid = false;
+    return TOMO_OK;
+}
+
+tomo_status tomo_profile_read(tomo_ctx *ctx, tomo_profile *out, int32_t reset)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    DeviceGuard guard(ctx->device);
+    tomo_status st = TOMO_OK;
+    for (size_t i = 0; i < ctx->ev_pending_slot.size(); ++i) {
+        const int slot = ctx->ev_pending_slot[i];
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(ctx->ev_stop[slot]);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, ctx->ev_start[slot], ctx->ev_stop[slot]);
+        if (e != cudaSuccess && st == TOMO_OK)
+            st = fail(ctx, TOMO_ERR_CUDA, "profile events: %s",
+                      cudaGetErrorString(e));
+        ctx->ms[ctx->ev_pending_kind[i]] += ms;
+        ctx->ev_free.push_back(slot);
+    }
+    ctx->ev_pending_slot.clear();
+    ctx->ev_pending_kind.clear();
+    if (out) {
+        for (int k = 0; k < TOMO_K_COUNT; ++k) {
+            out->launches[k] = ctx->launches[k];
+            out->ms[k] = ctx->ms[k];
+        }
+    }
+    if (reset) {
+        for (int k = 0; k < TOMO_K_COUNT; ++k) {
+            ctx->launches[k] = 0;
+            ctx->ms[k] = 0.0;
+        }
+    }
+    return st;
+}
+
+tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                         int32_t n_frames, const void *cube_dev,
+                         tomo_dtype dtype, const tomo_image_geom *img,
+                         const tomo_pointing *pointing_host,
+                         const uint8_t *mask_dev, float *images_dev,
+                         void *stream)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = common_checks(ctx, cube, n_frames, img, pointing_host);
+    if (st) return st;
+    if (dtype != TOMO_F32 && dtype != TOMO_BF16)
+        return fail(ctx, TOMO_ERR_ARG, "unknown dtype %d", (int)dtype);
+    if (img->n_img == 0) return TOMO_OK;
+    if (!cube_dev || !images_dev)
+        return fail(ctx, TOMO_ERR_ARG, "cube_dev / images_dev is NULL");
+    if (!aligned(cube_dev, dtype == TOMO_F32 ? 4 : 2) || !aligned(images_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "misaligned cube_dev / images_dev");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
+    const int64_t fstride = (int64_t)cube->nx * cube->ny * cube->nz;
+    LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward((const RayRec *)ctx->rays.p,
+                                 (const ImgParam *)ctx->params.p, cube_dev,
+                                 dtype, fstride, n_frames > 1, mask_dev,
+                                 images_dev, img->n_img, img->nu, img->nv,
+                                 cube->nx, cube->nx * cube->ny, ctx->tiling,
+                                 nullptr, s));
+    return TOMO_OK;
+}
+
+tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                             int32_t n_frames, const tomo_image_geom *img,
+                             const tomo_pointing *pointing_host,
+                             const uint8_t *mask_dev, const float *images_dev,
+                             float *cube_dev, uint32_t flags, void *stream)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = common_checks(ctx, cube, n_frames, img, pointing_host);
+    if (st) return st;
+    if (flags & ~TOMO_ACCUMULATE)
+        return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
+    if (!cube_dev) return fail(ctx, TOMO_ERR_ARG, "cube_dev is NULL");
+    if (!aligned(cube_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "misaligned cube_dev");
+    if (img->n_img > 0 && (!images_dev || !aligned(images_dev, 4)))
+        return fail(ctx, TOMO_ERR_ARG, "images_dev NULL or misaligned");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t fstride = (int64_t)cube->nx * cube->ny * cube->nz;
+    if (!(flags & TOMO_ACCUMULATE))
+        CUDA_TRY(ctx, cudaMemsetAsync(cube_dev, 0,
+                                      sizeof(float) * fstride * n_frames, s));
+    if (img->n_img == 0) return TOMO_OK;
+    if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
+    LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint((const RayRec *)ctx->rays.p,
+                                 (const ImgParam *)ctx->params.p, images_dev,
+                                 mask_dev, cube_dev, fstride, n_frames > 1,
+                                 img->n_img, img->nu, img->nv, cube->nx,
+                                 cube->nx * cube->ny, ctx->tiling, nullptr, s));
+    return TOMO_OK;
+}
+
+tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                             const float *x_dev, float *q_dev, double lambda,
+                             uint32_t flags, void *stream)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = check_cube(ctx, cube, 1);
+    if (st) return st;
+    if (flags & ~TOMO_ACCUMULATE)
+        return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
+    if (!x_dev || !q_dev || !aligned(x_dev, 4) || !aligned(q_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "x_dev / q_dev NULL or misaligned");
+    if (!isfinite(lambda) || lambda < 0)
+        return fail(ctx, TOMO_ERR_ARG, "lambda must be finite and >= 0");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    LAUNCH(ctx, TOMO_K_PRIOR, s,
+           launch_prior(cube_dev(cube), x_dev, q_dev, (float)lambda,
+                        (flags & TOMO_ACCUMULATE) != 0, nullptr, s));
+    return TOMO_OK;
+}
+
+tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                                const tomo_image_geom *img,
+                                const tomo_pointing *pointing_host,
+                                const uint8_t *mask_dev, int64_t *count_host,
+                                void *stream)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = common_checks(ctx, cube, 1, img, pointing_host);
+    if (st) return st;
+    if (!count_host) return fail(ctx, TOMO_ERR_ARG, "count_host is NULL");
+    *count_host = 0;
+    if (img->n_img == 0) return TOMO_OK;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = prepare_rays(ctx, cube, 1, img, pointing_host, s))) return st;
+    if ((st = ensure(ctx, ctx->count64, sizeof(unsigned long long)))) return st;
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->count64.p, 0, sizeof(unsigned long long), s));
+    LAUNCH(ctx, TOMO_K_FORWARD, s, launch_count((const RayRec *)ctx->rays.p, mask_dev, img->n_img,
+                               img->nu, img->nv, ctx->tiling,
+                               (unsigned long long *)ctx->count64.p, s));
+    unsigned long long n = 0;
+    CUDA_TRY(ctx, cudaMemcpyAsync(&n, ctx->count64.p, sizeof(n),
+                                  cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    *count_host = (int64_t)n;
+    return TOMO_OK;
+}
+
+tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                       const tomo_image_geom *img,
+                       const tomo_pointing *pointing_host,
+                       const uint8_t *mask_dev, const float *y_dev,
+                       float *x_dev, double lambda, int32_t max_iter,
+                       double tol, uint32_t flags, double *report_host,
+                       int32_t *iters_host, void *stream)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = common_checks(ctx, cube, 1, img, pointing_host);
+    if (st) return st;
+    if (flags & ~(TOMO_SOLVE_X0 | TOMO_SOLVE_BF16))
+        return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
+    if (!isfinite(lambda) || lambda < 0)
+        return fail(ctx, TOMO_ERR_ARG, "lambda must be finite and >= 0");
+    if (max_iter < 0 || max_iter > 1000000)
+        return fail(ctx, TOMO_ERR_ARG, "max_iter must be in [0, 1e6]");
+    if (!isfinite(tol) || tol < 0)
+        return fail(ctx, TOMO_ERR_ARG, "tol must be finite and >= 0");
+    if (!x_dev || !aligned(x_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "x_dev NULL or misaligned");
+    if (img->n_img > 0 && (!y_dev || !aligned(y_dev, 4)))
+        return fail(ctx, TOMO_ERR_ARG, "y_dev NULL or misaligned");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    const int64_t n = (int64_t)cube->nx * cube->ny * cube->nz;
+    const int64_t m = (int64_t)img->n_img * img->nu * img->nv;
+    const bool bf16 = (flags & TOMO_SOLVE_BF16) != 0;
+    const size_t n_report = 2 * ((size_t)max_iter + 1);
+    if ((st = ensure(ctx, ctx->b, sizeof(float) * n)) ||
+        (st = ensure(ctx, ctx->r, sizeof(float) * n)) ||
+        (st = ensure(ctx, ctx->p, sizeof(float) * n)) ||
+        (st = ensure(ctx, ctx->q, sizeof(float) * n)) ||
+        (st = ensure(ctx, ctx->t, sizeof(float) * (m > 0 ? m : 1))) ||
+        (bf16 && (st = ensure(ctx, ctx->p16, sizeof(uint16_t) * n))) ||
+        (st = ensure(ctx, ctx->S, sizeof(double) * (S_NSLOTS + n_report))) ||
+        (st = ensure(ctx, ctx->partials, sizeof(double) * 2 * kMaxReduceBlocks)) ||
+        (st = ensure(ctx, ctx->counter, sizeof(unsigned int))))
+        return st;
+    if (img->n_img > 0 &&
+        (st = prepare_rays(ctx, cube, 1, img, pointing_host, s)))
+        return st;
+
+    float *b = (float *)ctx->b.p, *r = (float *)ctx->r.p;
+    float *p = (float *)ctx->p.p, *q = (float *)ctx->q.p;
+    float *t = (float *)ctx->t.p;
+    uint16_t *p16 = bf16 ? (uint16_t *)ctx->p16.p : nullptr;
+    double *S = (double *)ctx->S.p;
+    double *report = S + S_NSLOTS;
+    double *partials = (double *)ctx->partials.p;
+    unsigned int *counter = (unsigned int *)ctx->counter.p;
+    const double *done = S + S_DONE;
+    const RayRec *rays = (const RayRec *)ctx->rays.p;
+    const ImgParam *prm = (const ImgParam *)ctx->params.p;
+    const CubeDev cd = cube_dev(cube);
+    const int nxny = cube->nx * cube->ny;
+    const float lam = (float)lambda;
+    const int grid = reduce_grid(ctx, n > m ? n : m);
+    const Tiling tl = ctx->tiling;
+
+    CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+    CUDA_TRY(ctx, cudaMemsetAsync(S, 0, sizeof(double) * S_NSLOTS, s));
+    LAUNCH(ctx, TOMO_K_VECTOR, s, launch_fill_f64(report, NAN, (int64_t)n_report, s));
+    // y^T M y and b = P^T M y
+    if (m > 0) {
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_masked_sumsq(y_dev, mask_dev, m, partials, counter,
+                                          S, grid, s));
+    }
+    CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
+    if (m > 0)
+        LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, y_dev, mask_dev, b, n, false,
+                                     img->n_img, img->nu, img->nv, cube->nx,
+                                     nxny, tl, nullptr, s));
+    if (flags & TOMO_SOLVE_X0) {
+        // r0 = b - (P^T M P + lambda D^T D) x0
+        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, q, lam, false, nullptr, s));
+        if (m > 0) {
+            LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward(rays, prm, x_dev, TOMO_F32, n, false,
+                                         mask_dev, t, img->n_img, img->nu,
+                                         img->nv, cube->nx, nxny, tl, nullptr, s));
+            LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, t, mask_dev, q, n, false,
+                                         img->n_img, img->nu, img->nv, cube->nx,
+                                         nxny, tl, nullptr, s));
+        }
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, n, tol * tol,
+                                     partials, counter, S, report, grid, s));
+    } else {
+        CUDA_TRY(ctx, cudaMemsetAsync(x_dev, 0, sizeof(float) * n, s));
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, nullptr, nullptr, r, p, p16, n,
+                                     tol * tol, partials, counter, S, report,
+                                     grid, s));
+    }
+    const void *p_gather = bf16 ? (const void *)p16 : (const void *)p;
+    const tomo_dtype p_dtype = bf16 ? TOMO_BF16 : TOMO_F32;
+    for (int32_t k = 0; k < max_iter; ++k) {
+        // q = (P^T M P + lambda D^T D) p
+        if (m > 0)
+            LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward(rays, prm, p_gather, p_dtype, n, false,
+                                         mask_dev, t, img->n_img, img->nu,
+                                         img->nv, cube->nx, nxny, tl, done, s));
+        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, q, lam, false, done, s));
+        if (m > 0)
+            LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, t, mask_dev, q, n, false,
+                                         img->n_img, img->nu, img->nv, cube->nx,
+                                         nxny, tl, done, s));
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, n, partials, counter,
+                                       S, report, grid, s));
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_direction(r, p, p16, n, S, grid, s));
+    }
+    if (report_host || iters_host) {
+        double host_S[S_NSLOTS];
+        CUDA_TRY(ctx, cudaMemcpyAsync(host_S, S, sizeof(host_S),
+                                      cudaMemcpyDeviceToHost, s));
+        if (report_host)
+            CUDA_TRY(ctx, cudaMemcpyAsync(report_host, report,
+                                          sizeof(double) * n_report,
+                                          cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        if (iters_host) *iters_host = (int32_t)host_S[S_ITERS];
+        if (host_S[S_ERR] != 0.0)
+            return fail(ctx, TOMO_ERR_NUMERIC,
+                        "CG breakdown after %d iterations (p.q = %g)",
+                        (int)host_S[S_ITERS], host_S[S_PQ]);
+    }
+    return TOMO_OK;
+}
+
+}  // extern "C"

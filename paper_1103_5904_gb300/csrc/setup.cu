@@ -1,0 +1,177 @@
+// Ray setup: pointing records -> per-pixel Siddon walk records, in FP64.
+//
+// The observer sits ~215 solar radii from a cube a few radii wide, so the
+// entry parameter of a ray is ~215 while a voxel is ~0.01: in float32 the
+// entry point would be off by a sizeable fraction of a voxel.  Everything up
+// to and including the entry point is therefore computed in double; the walk
+// itself is then re-based to the entry point (t = 0 there), where float32
+// keeps ~1e-7 relative precision over the whole chord.
+//
+// Geometry reading (the paper names the WCS keywords, Section 3.2, but gives
+// no formulas): Sun-centred frame with z along the rotation axis; observer
+// o = d (cos lat cos lon, cos lat sin lon, sin lat); boresight w = -o/|o|;
+// e1 = unit(w x z), e2 = e1 x w, turned by the roll angle about w; gnomonic
+// (TAN) pixel angles theta = (i - crpix) cdelt + crval per axis; ray
+// direction unit(w + tan(theta_u) e1 + tan(theta_v) e2).
+#include <math.h>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+namespace {
+
+// One block per image: the FP64 frame, the image parameters and the tangent
+// tables tan(theta_u), tan(theta_v) (one value per column / row).
+__global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
+                         int32_t nv, int32_t n_frames, Frame *frames,
+                         double *tan_u, double *tan_v, ImgParam *params)
+{
+    const int img = blockIdx.x;
+    const tomo_pointing p = ptg[img];
+    if (threadIdx.x == 0) {
+        Frame f;
+        const double cl = cos(p.lat), sl = sin(p.lat);
+        const double co = cos(p.lon), so = sin(p.lon);
+        f.o[0] = p.d_obs * cl * co;
+        f.o[1] = p.d_obs * cl * so;
+        f.o[2] = p.d_obs * sl;
+        f.w[0] = -cl * co;
+        f.w[1] = -cl * so;
+        f.w[2] = -sl;
+        // w x z = (w_y, -w_x, 0), of length cos(lat)
+        const double n1 = sqrt(f.w[0] * f.w[0] + f.w[1] * f.w[1]);
+        const double a1[3] = { f.w[1] / n1, -f.w[0] / n1, 0.0 };
+        const double a2[3] = { a1[1] * f.w[2] - a1[2] * f.w[1],
+                               a1[2] * f.w[0] - a1[0] * f.w[2],
+                               a1[0] * f.w[1] - a1[1] * f.w[0] };
+        const double cr = cos(p.roll), sr = sin(p.roll);
+        for (int a = 0; a < 3; ++a) {
+            f.e1[a] = cr * a1[a] + sr * a2[a];
+            f.e2[a] = -sr * a1[a] + cr * a2[a];
+        }
+        frames[img] = f;
+        ImgParam q;
+        q.gain = (float)p.gain;
+        q.pad = 0;
+        if (n_frames > 1) {
+            int k = (int)floor(p.time);
+            if (k > n_frames - 2) k = n_frames - 2;
+            if (k < 0) k = 0;
+            q.frame = k;
+            q.w = (float)(p.time - k);
+        } else {
+            q.frame = 0;
+            q.w = 0.0f;
+        }
+        params[img] = q;
+    }
+    for (int i = threadIdx.x; i < nu; i += blockDim.x)
+        tan_u[(int64_t)img * nu + i] = tan((i - p.crpix_u) * p.cdelt_u + p.crval_u);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x)
+        tan_v[(int64_t)img * nv + i] = tan((i - p.crpix_v) * p.cdelt_v + p.crval_v);
+}
+
+// One thread per pixel.  Slab clip of the half-line o + a u (a >= 0) in FP64,
+// entry voxel by the half-open rule, then per-axis first crossing and
+// crossing spacing relative to the entry point.
+__global__ void k_ray_setup(const Frame *__restrict__ frames,
+                            const double *__restrict__ tan_u,
+                            const double *__restrict__ tan_v, CubeDev c,
+                            int32_t nu, int32_t nv, RayRec *rays)
+{
+    const int img = blockIdx.y;
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= (int64_t)nu * nv) return;
+    const int iu = (int)(pix % nu), iv = (int)(pix / nu);
+    const Frame &f = frames[img];
+    const double tu = tan_u[(int64_t)img * nu + iu];
+    const double tv = tan_v[(int64_t)img * nv + iv];
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = f.w[a] + tu * f.e1[a] + tv * f.e2[a];
+    const double inv = 1.0 / sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int a = 0; a < 3; ++a) u[a] *= inv;
+
+    const int n[3] = { c.nx, c.ny, c.nz };
+    double amin = 0.0, amax = INFINITY;
+    bool hit = true;
+    for (int a = 0; a < 3; ++a) {
+        const double lo = c.lo[a], hi = c.lo[a] + n[a] * c.d[a];
+        if (u[a] == 0.0) {
+            if (f.o[a] < lo || f.o[a] >= hi) hit = false;
+        } else {
+            const double a0 = (lo - f.o[a]) / u[a];
+            const double a1 = (hi - f.o[a]) / u[a];
+            amin = fmax(amin, fmin(a0, a1));
+            amax = fmin(amax, fmax(a0, a1));
+        }
+    }
+    RayRec r;
+    r.t0x = r.t0y = r.t0z = 0.0f;
+    r.dtx = r.dty = r.dtz = 0.0f;
+    r.idx0 = 0;
+    r.chord = -1.0f;
+    if (hit && amin < amax) {
+        float chord = (float)(amax - amin);
+        int idx[3];
+        float t0f[3], dtf[3];
+        for (int a = 0; a < 3; ++a) {
+            const double pa = f.o[a] + amin * u[a];
+            const double g = (pa - c.lo[a]) / c.d[a];  // voxel coordinate
+            int ia = (u[a] < 0.0) ? (int)ceil(g) - 1 : (int)floor(g);
+            ia = ia < 0 ? 0 : (ia > n[a] - 1 ? n[a] - 1 : ia);
+            idx[a] = ia;
+            if (u[a] != 0.0) {
+                const double plane = (u[a] > 0.0) ? ia + 1.0 : (double)ia;
+                const double t0 = fmax((plane - g) * c.d[a] / u[a], 0.0);
+                const float dt = (float)(c.d[a] / fabs(u[a]));
+                const int rem = (u[a] > 0.0) ? n[a] - 1 - ia : ia;
+                t0f[a] = (float)t0;
+                // last in-cube plane of this axis, in the walk's arithmetic
+                chord = fminf(chord, fmaf((float)rem, dt, t0f[a]));
+                dtf[a] = (u[a] > 0.0) ? dt : -dt;
+            } else {
+                t0f[a] = 1e30f;
+                dtf[a] = 0.0f;
+            }
+        }
+        if (chord > 0.0f) {
+            r.t0x = t0f[0];
+            r.t0y = t0f[1];
+            r.t0z = t0f[2];
+            r.dtx = dtf[0];
+            r.dty = dtf[1];
+            r.dtz = dtf[2];
+            r.chord = chord;
+            r.idx0 = (idx[2] * c.ny + idx[1]) * c.nx + idx[0];
+        }
+    }
+    rays[(int64_t)img * nu * nv + pix] = r;
+}
+
+}  // namespace
+
+cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
+                          int32_t nu, int32_t nv, int32_t n_frames,
+                          Frame *frames, double *tan_u, double *tan_v,
+                          ImgParam *params, cudaStream_t s)
+{
+    if (n_img <= 0) return cudaSuccess;
+    k_frames<<<n_img, 128, 0, s>>>(ptg_dev, nu, nv, n_frames, frames, tan_u,
+                                   tan_v, params);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
+                             const double *tan_v, CubeDev cube, int32_t n_img,
+                             int32_t nu, int32_t nv, RayRec *rays,
+                             cudaStream_t s)
+{
+    if (n_img <= 0) return cudaSuccess;
+    const int64_t npix = (int64_t)nu * nv;
+    dim3 grid((unsigned)((npix + 255) / 256), (unsigned)n_img);
+    k_ray_setup<<<grid, 256, 0, s>>>(frames, tan_u, tan_v, cube, nu, nv, rays);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

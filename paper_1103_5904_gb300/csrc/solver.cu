@@ -1,0 +1,327 @@
+// Conjugate-gradient building blocks: the finite-difference prior D^T D and
+// the vector updates of CG with FP64 reductions.
+//
+// The criterion (Section 2.2, Eq. criterion) is ||M (y - P x)||^2 +
+// lambda ||D x||^2 with D the finite differences along each axis of the map
+// (Section 3.3.1).  Reading where the paper is silent: forward differences
+// x[i+1] - x[i] along x, y and z without wrap-around, one lambda for all
+// axes.  Then D^T D is, on every line, the path-graph Laplacian: a 7-point
+// stencil whose end points see only their one neighbour.
+//
+// CG scalars (alpha, beta, r.r, p.q, the criterion) live in device memory in
+// FP64, so the iteration loop needs no host round trip.  Every dot product
+// is a two-stage reduction: each CTA writes its FP64 partial sum, and the
+// last CTA to finish (found with one atomic counter, no waiting) adds the
+// partials in a fixed order, which makes the result deterministic, and then
+// applies the scalar update of that CG step.  A "done" flag in the same slot
+// array lets every later kernel of the loop return at once after
+// convergence or a breakdown.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA; the result is valid in thread 0.  Ends with a barrier so
+// the shared scratch can be reused by the next call.
+__device__ double block_sum(double v, double *sm)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sm[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// Two-stage reduction of K values.  Returns true in the last CTA, where
+// total[] (valid in thread 0) holds the grid-wide sums.
+template <int K>
+__device__ bool grid_sum(double (&v)[K], double *partials,
+                         unsigned int *counter, double (&total)[K])
+{
+    __shared__ double sm[32];
+    __shared__ bool last;
+    for (int k = 0; k < K; ++k) v[k] = block_sum(v[k], sm);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) partials[blockIdx.x * K + k] = v[k];
+        __threadfence();
+        const unsigned int prev = atomicAdd(counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x)
+            s += __ldcg(partials + i * K + k);
+        total[k] = block_sum(s, sm);
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ uint16_t to_bf16_bits(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+__global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
+                        float *__restrict__ q, float lam, bool accumulate,
+                        const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const int64_t v = k * sz + j * sy + i;
+    const float xc = x[v];
+    float s = 0.0f;
+    if (i > 0) s += xc - x[v - 1];
+    if (i < nx - 1) s += xc - x[v + 1];
+    if (j > 0) s += xc - x[v - sy];
+    if (j < ny - 1) s += xc - x[v + sy];
+    if (k > 0) s += xc - x[v - sz];
+    if (k < nz - 1) s += xc - x[v + sz];
+    const float val = lam * s;
+    q[v] = accumulate ? q[v] + val : val;
+}
+
+__global__ void k_fill_f32(float *p, float v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_fill_f64(double *p, double v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_masked_sumsq(const float *__restrict__ y,
+                               const uint8_t *__restrict__ mask, int64_t n,
+                               double *partials, unsigned int *counter,
+                               double *S)
+{
+    double v[1] = { 0.0 };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (mask == nullptr || mask[i] == 0) {
+            const double yi = y[i];
+            v[0] += yi * yi;
+        }
+    }
+    double tot[1];
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0)
+        S[S_YMY] = tot[0];
+}
+
+__global__ void k_cg_init(const float *__restrict__ b,
+                          const float *__restrict__ q,
+                          const float *__restrict__ x, float *__restrict__ r,
+                          float *__restrict__ p, uint16_t *__restrict__ p16,
+                          int64_t n, double tol2, double *partials,
+                          unsigned int *counter, double *S, double *report)
+{
+    double v[2] = { 0.0, 0.0 };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float bi = b[i];
+        const float ri = (q != nullptr) ? bi - q[i] : bi;
+        r[i] = ri;
+        p[i] = ri;
+        if (p16 != nullptr) p16[i] = to_bf16_bits(ri);
+        v[0] += (double)ri * ri;
+        if (x != nullptr) v[1] += (double)x[i] * ((double)ri + bi);
+    }
+    double tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        S[S_RR] = tot[0];
+        S[S_RR0] = tot[0];
+        S[S_TOL2] = tol2;
+        S[S_ITERS] = 0.0;
+        S[S_ERR] = 0.0;
+        S[S_DONE] = (tot[0] == 0.0) ? 1.0 : 0.0;
+        if (report != nullptr) {
+            report[0] = S[S_YMY] - tot[1];
+            report[1] = tot[0];
+        }
+    }
+}
+
+__global__ void k_cg_pq(const float *__restrict__ p, const float *__restrict__ q,
+                        int64_t n, double *partials, unsigned int *counter,
+                        double *S)
+{
+    if (S[S_DONE] != 0.0) return;
+    double v[1] = { 0.0 };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[0] += (double)p[i] * q[i];
+    double tot[1];
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        S[S_PQ] = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            S[S_DONE] = 1.0;
+            S[S_ERR] = 1.0;
+        } else {
+            S[S_ALPHA] = S[S_RR] / pq;
+        }
+    }
+}
+
+__global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
+                            const float *__restrict__ p,
+                            const float *__restrict__ q,
+                            const float *__restrict__ b, int64_t n,
+                            double *partials, unsigned int *counter,
+                            double *S, double *report)
+{
+    if (S[S_DONE] != 0.0) return;
+    const float alpha = (float)S[S_ALPHA];
+    double v[2] = { 0.0, 0.0 };
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float xi = fmaf(alpha, p[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        x[i] = xi;
+        r[i] = ri;
+        v[0] += (double)ri * ri;
+        v[1] += (double)xi * ((double)ri + b[i]);
+    }
+    double tot[2];
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+        const int k = (int)S[S_ITERS];
+        const double rr_new = tot[0];
+        S[S_BETA] = rr_new / S[S_RR];
+        S[S_RR] = rr_new;
+        S[S_ITERS] = k + 1;
+        if (report != nullptr) {
+            report[2 * (k + 1)] = S[S_YMY] - tot[1];
+            report[2 * (k + 1) + 1] = rr_new;
+        }
+        if (!isfinite(rr_new)) {
+            S[S_DONE] = 1.0;
+            S[S_ERR] = 1.0;
+        } else if (rr_new <= S[S_TOL2] * S[S_RR0]) {
+            S[S_DONE] = 1.0;
+        }
+    }
+}
+
+__global__ void k_cg_direction(const float *__restrict__ r, float *p,
+                               uint16_t *__restrict__ p16, int64_t n,
+                               const double *__restrict__ S)
+{
+    if (S[S_DONE] != 0.0) return;
+    const float beta = (float)S[S_BETA];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float pi = fmaf(beta, p[i], r[i]);
+        p[i] = pi;
+        if (p16 != nullptr) p16[i] = to_bf16_bits(pi);
+    }
+}
+
+unsigned int fill_grid(int64_t n)
+{
+    const int64_t g = (n + kThreads - 1) / kThreads;
+    return (unsigned int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+}  // namespace
+
+cudaError_t launch_prior(CubeDev c, const float *x, float *q, float lam,
+                         bool accumulate, const double *done, cudaStream_t s)
+{
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
+                    (unsigned)c.nz);
+    k_prior<<<grid, block, 0, s>>>(c.nx, c.ny, c.nz, x, q, lam, accumulate,
+                                   done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f32(float *p, float v, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fill_f32<<<fill_grid(n), kThreads, 0, s>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_f64(double *p, double v, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fill_f64<<<fill_grid(n), kThreads, 0, s>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_masked_sumsq(const float *y, const uint8_t *mask,
+                                int64_t n, double *partials,
+                                unsigned int *counter, double *S, int grid,
+                                cudaStream_t s)
+{
+    k_masked_sumsq<<<grid, kThreads, 0, s>>>(y, mask, n, partials, counter, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(const float *b, const float *q, const float *x,
+                           float *r, float *p, uint16_t *p16, int64_t n,
+                           double tol2, double *partials,
+                           unsigned int *counter, double *S, double *report,
+                           int grid, cudaStream_t s)
+{
+    k_cg_init<<<grid, kThreads, 0, s>>>(b, q, x, r, p, p16, n, tol2, partials,
+                                        counter, S, report);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pq(const float *p, const float *q, int64_t n,
+                         double *partials, unsigned int *counter, double *S,
+                         int grid, cudaStream_t s)
+{
+    k_cg_pq<<<grid, kThreads, 0, s>>>(p, q, n, partials, counter, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(float *x, float *r, const float *p,
+                             const float *q, const float *b, int64_t n,
+                             double *partials, unsigned int *counter,
+                             double *S, double *report, int grid,
+                             cudaStream_t s)
+{
+    k_cg_update<<<grid, kThreads, 0, s>>>(x, r, p, q, b, n, partials, counter,
+                                          S, report);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_direction(const float *r, float *p, uint16_t *p16,
+                                int64_t n, const double *S, int grid,
+                                cudaStream_t s)
+{
+    k_cg_direction<<<grid, kThreads, 0, s>>>(r, p, p16, n, S);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

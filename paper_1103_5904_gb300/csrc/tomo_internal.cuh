@@ -1,0 +1,128 @@
+// Internal declarations of libtomo (not part of the C ABI).
+//
+// Data layout in device memory
+//   RayRec  one 32-byte record per pixel, [n_img][nv][nu]: the Siddon walk of
+//           that pixel's line of sight, re-based to its entry point into the
+//           cube (built in FP64 by the setup kernel, walked in FP32).
+//   ImgParam one 16-byte record per image: gain, time weight, frame index.
+//   Frame   per-image FP64 observer frame (o, w, e1, e2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tomo.h"
+
+namespace tomo {
+
+// Walk of one line of sight, relative to its entry point into the cube.
+// t is the distance travelled from the entry point.  The walk crosses the
+// k-th plane (k = 0, 1, ...) of axis a at t = fmaf(k, |dt_a|, t0_a); the sign
+// bit of dt_a is the step direction along a.  The walk ends at t = chord,
+// which the setup kernel has already lowered, in the walk's own float
+// arithmetic, to the last in-cube plane of every axis, so the voxel index
+// never leaves the cube.  chord <= 0 marks a ray that misses the cube.
+struct __align__(16) RayRec {
+    float t0x, t0y, t0z, chord;
+    float dtx, dty, dtz;
+    int32_t idx0;  // linear index (within one frame) of the entry voxel
+};
+static_assert(sizeof(RayRec) == 32, "RayRec must stay 32 bytes");
+
+struct __align__(16) ImgParam {
+    float gain;     // image gain g_n
+    float w;        // weight of frame k + 1
+    int32_t frame;  // k (0 when T == 1)
+    int32_t pad;
+};
+
+struct Frame {
+    double o[3], w[3], e1[3], e2[3];
+};
+
+struct CubeDev {
+    int32_t nx, ny, nz;
+    double lo[3], d[3];
+};
+
+struct Tiling {
+    int32_t tile_u, tile_v, warp_u;
+};
+
+// Device-side scalar slots of the CG solver (FP64).
+enum : int {
+    S_RR = 0,     // r.r of the current residual
+    S_PQ = 1,     // p.q
+    S_ALPHA = 2,  // step length
+    S_BETA = 3,   // direction update
+    S_YMY = 4,    // y^T M y
+    S_RR0 = 5,    // r0.r0
+    S_DONE = 6,   // nonzero: stop (converged or breakdown)
+    S_ITERS = 7,  // iterations done
+    S_ERR = 8,    // nonzero: numerical breakdown
+    S_TOL2 = 9,   // tol^2
+    S_NSLOTS = 16
+};
+
+constexpr int kMaxReduceBlocks = 2048;
+
+// ---- setup.cu
+cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
+                          int32_t nu, int32_t nv, int32_t n_frames,
+                          Frame *frames, double *tan_u, double *tan_v,
+                          ImgParam *params, cudaStream_t s);
+cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
+                             const double *tan_v, CubeDev cube, int32_t n_img,
+                             int32_t nu, int32_t nv, RayRec *rays,
+                             cudaStream_t s);
+
+// ---- siddon.cu
+cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
+                           const void *cube, tomo_dtype dtype,
+                           int64_t frame_stride, bool time_interp,
+                           const uint8_t *mask, float *out, int32_t n_img,
+                           int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
+                           Tiling t, const double *done, cudaStream_t s);
+cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
+                           const float *images, const uint8_t *mask,
+                           float *cube, int64_t frame_stride,
+                           bool time_interp, int32_t n_img, int32_t nu,
+                           int32_t nv, int32_t nx, int32_t nxny, Tiling t,
+                           const double *done, cudaStream_t s);
+cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
+                         int32_t n_img, int32_t nu, int32_t nv, Tiling t,
+                         unsigned long long *count, cudaStream_t s);
+
+// ---- solver.cu
+cudaError_t launch_prior(CubeDev cube, const float *x, float *q, float lam,
+                         bool accumulate, const double *done, cudaStream_t s);
+cudaError_t launch_fill_f32(float *p, float v, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_f64(double *p, double v, int64_t n, cudaStream_t s);
+// S[S_YMY] = sum over unmasked pixels of y^2
+cudaError_t launch_masked_sumsq(const float *y, const uint8_t *mask,
+                                int64_t n, double *partials,
+                                unsigned int *counter, double *S,
+                                int grid, cudaStream_t s);
+// r = b - q (or r = b if q == NULL); p = r (+ bf16 copy); S[RR], S[RR0],
+// report row 0 from r.r and x.(r + b)
+cudaError_t launch_cg_init(const float *b, const float *q, const float *x,
+                           float *r, float *p, uint16_t *p16, int64_t n,
+                           double tol2, double *partials,
+                           unsigned int *counter, double *S, double *report,
+                           int grid, cudaStream_t s);
+// S[S_PQ] = p.q, S[S_ALPHA] = rr / pq
+cudaError_t launch_cg_pq(const float *p, const float *q, int64_t n,
+                         double *partials, unsigned int *counter, double *S,
+                         int grid, cudaStream_t s);
+// x += alpha p; r -= alpha q; S[RR] <- r.r, beta, report row
+cudaError_t launch_cg_update(float *x, float *r, const float *p,
+                             const float *q, const float *b, int64_t n,
+                             double *partials, unsigned int *counter,
+                             double *S, double *report, int grid,
+                             cudaStream_t s);
+// p = r + beta p (+ bf16 copy)
+cudaError_t launch_cg_direction(const float *r, float *p, uint16_t *p16,
+                                int64_t n, const double *S, int grid,
+                                cudaStream_t s);
+
+}  // namespace tomo

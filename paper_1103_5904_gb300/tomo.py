@@ -1,0 +1,382 @@
+"""Python binding of libtomo (``include/tomo.h``): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Tensors are
+PyTorch CUDA tensors (device memory and streams only); all computation
+happens in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or cannot be loaded, every call raises.
+
+Geometry arguments:
+  ``geom``      dict with nx, ny, nz, x0, y0, z0, dx, dy, dz (the layout of
+                ``synth.cube_geom``)
+  ``pointing``  float64 array (n_img, 12), one pointing record per row in the
+                field order of ``tomo_pointing``
+"""
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtomo.so")
+
+TOMO_F32, TOMO_BF16 = 0, 1
+TOMO_ACCUMULATE, TOMO_SOLVE_X0, TOMO_SOLVE_BF16 = 1, 2, 4
+TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3, 4
+TOMO_OPT_PROFILE = 5
+KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector")
+
+STATUS = {0: "TOMO_OK", -1: "TOMO_ERR_ARG", -2: "TOMO_ERR_CUDA",
+          -3: "TOMO_ERR_UNSUPPORTED", -4: "TOMO_ERR_OOM",
+          -5: "TOMO_ERR_TIMEOUT", -6: "TOMO_ERR_NUMERIC"}
+
+
+class CubeGeom(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("reserved", C.c_int32), ("x0", C.c_double),
+                ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
+                ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class ImageGeom(C.Structure):
+    _fields_ = [("n_img", C.c_int32), ("nu", C.c_int32), ("nv", C.c_int32)]
+
+
+class Pointing(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "d_obs", "lon", "lat", "roll", "cdelt_u", "cdelt_v", "crpix_u",
+        "crpix_v", "crval_u", "crval_v", "gain", "time")]
+
+
+class Profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5)]
+
+
+assert C.sizeof(CubeGeom) == 64 and C.sizeof(Pointing) == 96
+
+
+class TomoError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status,
+                                          message))
+        self.status = status
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# name -> (restype, argtypes); the exported surface of include/tomo.h
+_VP, _CP = C.c_void_p, C.c_char_p
+_SIGNATURES = {
+    "tomo_create": (C.c_int, [C.POINTER(_VP), C.c_int32]),
+    "tomo_destroy": (None, [_VP]),
+    "tomo_status_string": (_CP, [C.c_int]),
+    "tomo_last_error": (_CP, [_VP]),
+    "tomo_set_option": (C.c_int, [_VP, C.c_int32, C.c_int64]),
+    "tomo_clear_cache": (C.c_int, [_VP]),
+    "tomo_profile_read": (C.c_int, [_VP, C.POINTER(Profile), C.c_int32]),
+    "tomo_project": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32, _VP,
+                               C.c_int, C.POINTER(ImageGeom),
+                               C.POINTER(Pointing), _VP, _VP, _VP]),
+    "tomo_backproject": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32,
+                                   C.POINTER(ImageGeom), C.POINTER(Pointing),
+                                   _VP, _VP, _VP, C.c_uint32, _VP]),
+    "tomo_solve": (C.c_int, [_VP, C.POINTER(CubeGeom), C.POINTER(ImageGeom),
+                             C.POINTER(Pointing), _VP, _VP, _VP, C.c_double,
+                             C.c_int32, C.c_double, C.c_uint32,
+                             C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                             _VP]),
+    "tomo_prior_apply": (C.c_int, [_VP, C.POINTER(CubeGeom), _VP, _VP,
+                                   C.c_double, C.c_uint32, _VP]),
+    "tomo_count_segments": (C.c_int, [_VP, C.POINTER(CubeGeom),
+                                      C.POINTER(ImageGeom),
+                                      C.POINTER(Pointing), _VP,
+                                      C.POINTER(C.c_int64), _VP]),
+}
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def load_library(path=LIB_PATH):
+    """Load libtomo.so (built by ``paper_1103_5904_gb300.build``)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(
+                "libtomo.so not found at %s: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+# ----------------------------------------------------------------- contexts
+
+class Context:
+    """One libtomo context (workspace + ray-record cache) on one device."""
+
+    def __init__(self, device=None):
+        lib = load_library()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = int(device)
+        h = _VP()
+        st = lib.tomo_create(C.byref(h), self.device)
+        if st != 0:
+            raise TomoError(st, lib.tomo_status_string(st).decode())
+        self.handle = h
+
+    def check(self, st):
+        if st != 0:
+            lib = load_library()
+            raise TomoError(st, lib.tomo_last_error(self.handle).decode())
+
+    def set_option(self, option, value):
+        self.check(load_library().tomo_set_option(self.handle, int(option),
+                                                  int(value)))
+
+    def set_tiling(self, tile_u, tile_v, warp_u):
+        self.set_option(TOMO_OPT_WARP_U, warp_u)
+        self.set_option(TOMO_OPT_TILE_U, tile_u)
+        self.set_option(TOMO_OPT_TILE_V, tile_v)
+
+    def clear_cache(self):
+        self.check(load_library().tomo_clear_cache(self.handle))
+
+    def profile(self, reset=False):
+        """Launch counts and (with TOMO_OPT_PROFILE) summed device ms per
+        kernel class: ``{"setup": (launches, ms), ...}``."""
+        p = Profile()
+        self.check(load_library().tomo_profile_read(self.handle, C.byref(p),
+                                                    1 if reset else 0))
+        return {k: (int(p.launches[i]), float(p.ms[i]))
+                for i, k in enumerate(KERNEL_CLASSES)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().tomo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default_ctx = {}
+
+
+def default_context(device=None):
+    if device is None:
+        device = torch.cuda.current_device()
+    if device not in _default_ctx:
+        _default_ctx[device] = Context(device)
+    return _default_ctx[device]
+
+
+# -------------------------------------------------------------- marshalling
+
+def cube_geom_struct(geom):
+    return CubeGeom(int(geom["nx"]), int(geom["ny"]), int(geom["nz"]), 0,
+                    float(geom["x0"]), float(geom["y0"]), float(geom["z0"]),
+                    float(geom["dx"]), float(geom["dy"]), float(geom["dz"]))
+
+
+def pointing_array(pointing):
+    a = np.ascontiguousarray(pointing, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != 12:
+        raise ValueError("pointing must be a (n_img, 12) float64 table")
+    return a
+
+
+def _ptg_ptr(a):
+    return a.ctypes.data_as(C.POINTER(Pointing))
+
+
+def _dev(t, dtype, name):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _check_mask(mask, n_img, nu, nv):
+    _dev(mask, torch.uint8, "mask")
+    if mask is not None and mask.numel() != n_img * nu * nv:
+        raise ValueError("mask must have n_img * nv * nu = %d elements (got %d)"
+                         % (n_img * nu * nv, mask.numel()))
+
+
+def _stream_ptr(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return _VP(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else _VP(t.data_ptr())
+
+
+def _ctx(ctx):
+    return ctx if ctx is not None else default_context()
+
+
+# ------------------------------------------------------------- entry points
+
+def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
+                 out=None, ctx=None, stream=None):
+    """``y = P x``: images ``[n_img][nv][nu]`` float32 from a float32 or
+    bfloat16 cube ``[T][nz][ny][nx]``."""
+    ctx = _ctx(ctx)
+    ptg = pointing_array(pointing)
+    n_img = ptg.shape[0]
+    if cube.dtype == torch.float32:
+        dtype = TOMO_F32
+    elif cube.dtype == torch.bfloat16:
+        dtype = TOMO_BF16
+    else:
+        raise TypeError("cube must be float32 or bfloat16")
+    _dev(cube, cube.dtype, "cube")
+    nvox = int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"])
+    if cube.numel() != nvox * int(n_frames):
+        raise ValueError("cube has %d elements, geometry needs %d"
+                         % (cube.numel(), nvox * int(n_frames)))
+    if out is None:
+        out = torch.empty((n_img, nv, nu), dtype=torch.float32,
+                          device=cube.device)
+    _dev(out, torch.float32, "out")
+    if out.numel() != n_img * nu * nv:
+        raise ValueError("out must have n_img * nv * nu elements")
+    _check_mask(mask, n_img, nu, nv)
+    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, int(nu), int(nv))
+    ctx.check(load_library().tomo_project(
+        ctx.handle, C.byref(cg), int(n_frames), _ptr(cube), dtype,
+        C.byref(ig), _ptg_ptr(ptg), _ptr(mask), _ptr(out),
+        _stream_ptr(stream, cube.device)))
+    return out
+
+
+def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
+                     accumulate=False, ctx=None, stream=None):
+    """``x = P^T y``: float32 cube ``[T][nz][ny][nx]`` from float32 images
+    ``[n_img][nv][nu]``."""
+    ctx = _ctx(ctx)
+    ptg = pointing_array(pointing)
+    _dev(images, torch.float32, "images")
+    n_img, nv, nu = images.shape
+    if n_img != ptg.shape[0]:
+        raise ValueError("one pointing record per image")
+    shape = (int(geom["nz"]), int(geom["ny"]), int(geom["nx"]))
+    if n_frames > 1:
+        shape = (int(n_frames),) + shape
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=images.device)
+        accumulate = False
+    _dev(out, torch.float32, "out")
+    if out.numel() != int(np.prod(shape)):
+        raise ValueError("out has the wrong size")
+    _check_mask(mask, n_img, nu, nv)
+    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
+    ctx.check(load_library().tomo_backproject(
+        ctx.handle, C.byref(cg), int(n_frames), C.byref(ig), _ptg_ptr(ptg),
+        _ptr(mask), _ptr(images), _ptr(out),
+        TOMO_ACCUMULATE if accumulate else 0,
+        _stream_ptr(stream, images.device)))
+    return out
+
+
+def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
+               x0=None, bf16=False, out=None, report=True, ctx=None,
+               stream=None):
+    """CG on ``(P^T M P + lam D^T D) x = P^T M y``.  Returns ``(x, info)``
+    with ``info = {"J": ..., "rr": ..., "iters": ...}`` when ``report``."""
+    ctx = _ctx(ctx)
+    ptg = pointing_array(pointing)
+    _dev(y, torch.float32, "y")
+    n_img, nv, nu = y.shape
+    shape = (int(geom["nz"]), int(geom["ny"]), int(geom["nx"]))
+    flags = 0
+    if n_img != ptg.shape[0]:
+        raise ValueError("one pointing record per image")
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=y.device)
+    _dev(out, torch.float32, "out")
+    if out.numel() != int(np.prod(shape)):
+        raise ValueError("out has the wrong size")
+    if x0 is not None:
+        out.copy_(x0.reshape(shape))
+        flags |= TOMO_SOLVE_X0
+    if bf16:
+        flags |= TOMO_SOLVE_BF16
+    _check_mask(mask, n_img, nu, nv)
+    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
+    rep = np.full(2 * (int(max_iter) + 1), np.nan) if report else None
+    iters = C.c_int32(0)
+    ctx.check(load_library().tomo_solve(
+        ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
+        _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
+        rep.ctypes.data_as(C.POINTER(C.c_double)) if report else None,
+        C.byref(iters) if report else None, _stream_ptr(stream, y.device)))
+    info = None
+    if report:
+        r = rep.reshape(-1, 2)
+        info = {"J": r[:, 0].copy(), "rr": r[:, 1].copy(),
+                "iters": int(iters.value)}
+    return out, info
+
+
+def tomo_prior_apply(x, geom, lam, out=None, accumulate=False, ctx=None,
+                     stream=None):
+    """``q = lam D^T D x`` (+ q with ``accumulate``)."""
+    ctx = _ctx(ctx)
+    _dev(x, torch.float32, "x")
+    if out is None:
+        out = torch.empty_like(x)
+        accumulate = False
+    _dev(out, torch.float32, "out")
+    nvox = int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"])
+    if x.numel() != nvox or out.numel() != nvox:
+        raise ValueError("x and out must have nx * ny * nz elements")
+    cg = cube_geom_struct(geom)
+    ctx.check(load_library().tomo_prior_apply(
+        ctx.handle, C.byref(cg), _ptr(x), _ptr(out), float(lam),
+        TOMO_ACCUMULATE if accumulate else 0, _stream_ptr(stream, x.device)))
+    return out
+
+
+def tomo_count_segments(geom, pointing, nu, nv, mask=None, ctx=None,
+                        stream=None, device=None):
+    """Number of positive-length Siddon segments of the unmasked rays."""
+    ctx = _ctx(ctx)
+    ptg = pointing_array(pointing)
+    _check_mask(mask, ptg.shape[0], int(nu), int(nv))
+    cg, ig = cube_geom_struct(geom), ImageGeom(ptg.shape[0], int(nu), int(nv))
+    n = C.c_int64(0)
+    dev = torch.device("cuda", ctx.device)
+    ctx.check(load_library().tomo_count_segments(
+        ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
+        C.byref(n), _stream_ptr(stream, dev)))
+    return int(n.value)
+
+
+# short aliases
+project = tomo_project
+backproject = tomo_backproject
+solve = tomo_solve
+prior_apply = tomo_prior_apply
+count_segments = tomo_count_segments

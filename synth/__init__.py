@@ -15,7 +15,7 @@ stand-in with the shapes, sizes and structure of those workloads.
 from .geometry import (POINTING_COLUMNS, cube_geom, pointing_table,
                        cdelt_for_fov, voxel_centres)
 from .corona import (radial_exp, radial_power, add_structures, random_axes,
-                     uniform_noise, corona_cube)
+                     uniform_noise, corona_cube, corona_frames)
 from .masks import occulter_mask
 from .configs import (CONFIGS, make_config, noise_draw, add_noise,
                       problem_seeds_batched)
@@ -23,7 +23,7 @@ from .configs import (CONFIGS, make_config, noise_draw, add_noise,
 __all__ = [
     "POINTING_COLUMNS", "cube_geom", "pointing_table", "cdelt_for_fov",
     "voxel_centres", "radial_exp", "radial_power", "add_structures",
-    "random_axes", "uniform_noise", "corona_cube", "occulter_mask",
+    "random_axes", "uniform_noise", "corona_cube", "corona_frames", "occulter_mask",
     "CONFIGS", "make_config", "noise_draw", "add_noise",
     "problem_seeds_batched",
 ]

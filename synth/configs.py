@@ -42,7 +42,7 @@ reduced copy of the same scene can be built for the oracle.
 import numpy as np
 
 from .geometry import cube_geom, pointing_table
-from .corona import corona_cube, random_axes
+from .corona import corona_cube, corona_frames, random_axes
 from .masks import occulter_mask
 
 D_OBS = 215.0  # observer distance [R_sun] (about 1 AU)
@@ -113,12 +113,9 @@ def _temporal_frames(seed, n_frames):
         rng = np.random.default_rng(seed)
         axes = random_axes(rng, 6)
         phase = rng.uniform(0.0, 2.0 * np.pi, 6)
-        frames = []
-        for t in range(n_frames):
-            amp = 3.0 * (1.0 + 0.5 * np.sin(2.0 * np.pi * t / n_frames + phase))
-            frames.append(corona_cube(geom, "exp",
-                                      structures=[(axes, 0.05, amp)]))
-        return np.stack(frames)
+        t = np.arange(n_frames)[:, None]
+        amps = 3.0 * (1.0 + 0.5 * np.sin(2.0 * np.pi * t / n_frames + phase))
+        return corona_frames(geom, axes, 0.05, amps)
     return f
 
 

@@ -75,6 +75,29 @@ def uniform_noise(x, rng, frac):
     return x * (1.0 + frac * rng.uniform(-1.0, 1.0, size=x.shape))
 
 
+def corona_frames(geom, axes, width, amps, background="exp", slab=16):
+    """Frames ``[T][nz][ny][nx]`` float32 of a background plus cylinders of
+    one ``width`` whose amplitudes change from frame to frame: frame t holds
+    ``n_bg + sum_s amps[t][s] * profile_s`` (see :func:`add_structures`)."""
+    bgf = _BACKGROUNDS[background]
+    amps = np.asarray(amps, dtype=np.float64)
+    xs = voxel_centres(geom, "x")
+    ys = voxel_centres(geom, "y")
+    zs = voxel_centres(geom, "z")
+    nz, ny, nx = geom["nz"], geom["ny"], geom["nx"]
+    out = np.empty((amps.shape[0], nz, ny, nx), dtype=np.float32)
+    for z0 in range(0, nz, slab):
+        pz, py, px = np.meshgrid(zs[z0:z0 + slab], ys, xs, indexing="ij")
+        bg = bgf(np.sqrt(px * px + py * py + pz * pz))
+        prof = [add_structures(px, py, pz, bg, [a], width, 1.0) for a in axes]
+        for t in range(amps.shape[0]):
+            val = bg.copy()
+            for s, p in enumerate(prof):
+                val += amps[t, s] * p
+            out[t, z0:z0 + slab] = val
+    return out
+
+
 def corona_cube(geom, background="exp", structures=(), noise_frac=0.0,
                 noise_rng=None, slab=16):
     """Density cube ``[nz][ny][nx]`` float32.
