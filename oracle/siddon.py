@@ -53,6 +53,8 @@ def lib():
                                       C.c_int32, dp, up, dp, C.c_int64, lp,
                                       dp]
         L.orc_backproject.restype = C.c_int
+        L.orc_crossing_weights.argtypes = L.orc_backproject.argtypes
+        L.orc_crossing_weights.restype = C.c_int
         L.orc_count_segments.argtypes = [cp, C.c_int32, C.c_int32, C.c_int32,
                                          dp, up, C.c_int64, lp]
         L.orc_count_segments.restype = C.c_int64
@@ -163,6 +165,27 @@ def backproject(geom, images, pointing, nu, nv, mask=None, n_frames=1,
     rc = lib().orc_backproject(C.byref(c), int(n_frames), n_img, int(nu),
                                int(nv), _dp(ptg), mp, _dp(img), nr, rp,
                                _dp(out))
+    if rc != 0:
+        raise ValueError("invalid pointing or time stamp")
+    return out
+
+
+def crossing_weights(geom, images, pointing, nu, nv, mask=None, n_frames=1,
+                     ray_ids=None):
+    """C_j = sum of |g_k y_k| over the rays k crossing voxel j (positive
+    length), time-weighted like the transpose."""
+    c = _cube(geom)
+    ptg = _f64(pointing)
+    n_img = ptg.shape[0]
+    img = _f64(images).reshape(-1)
+    m, mp = _mask_ptr(mask)
+    r, nr, rp = _rays(ray_ids)
+    T = max(int(n_frames), 1)
+    shape = (geom["nz"], geom["ny"], geom["nx"])
+    out = np.zeros(((T,) if n_frames > 1 else ()) + shape)
+    rc = lib().orc_crossing_weights(C.byref(c), int(n_frames), n_img, int(nu),
+                                    int(nv), _dp(ptg), mp, _dp(img), nr, rp,
+                                    _dp(out))
     if rc != 0:
         raise ValueError("invalid pointing or time stamp")
     return out

@@ -326,10 +326,12 @@ int orc_project(const orc_cube *c, int32_t n_frames, const double *cube,
  * transpose of orc_project applied to images ([n_img][nv][nu]), restricted to
  * the listed rays when ray_ids is not NULL (images is then indexed by ray
  * id as a full image stack).  Masked pixels contribute nothing. */
-int orc_backproject(const orc_cube *c, int32_t n_frames, int32_t n_img,
-                    int32_t nu, int32_t nv, const double *pointing,
-                    const uint8_t *mask, const double *images, int64_t n_rays,
-                    const int64_t *ray_ids, double *cube_out)
+static int backproject_impl(const orc_cube *c, int32_t n_frames,
+                            int32_t n_img, int32_t nu, int32_t nv,
+                            const double *pointing, const uint8_t *mask,
+                            const double *images, int64_t n_rays,
+                            const int64_t *ray_ids, double *cube_out,
+                            int crossing_weights)
 {
     if (check_pointing(n_frames, n_img, pointing) != 0) return -1;
     int64_t n_all = (int64_t)n_img * nv * nu;
@@ -350,6 +352,7 @@ int orc_backproject(const orc_cube *c, int32_t n_frames, int32_t n_img,
             const double *p = pointing + (size_t)n * C_NCOL;
             if (mask && mask[id]) continue;
             double yk = p[C_GAIN] * images[id];
+            if (crossing_weights) yk = fabs(yk);
             if (yk == 0.0) continue;
             double o[3], u[3];
             orc_ray(p, iu, iv, o, u);
@@ -358,6 +361,7 @@ int orc_backproject(const orc_cube *c, int32_t n_frames, int32_t n_img,
             time_weights(n_frames, p[C_TIME], &k, &w);
             int64_t s = orc_segments(c, o, u, idx, len, NULL, NULL);
             for (int64_t q = 0; q < s; ++q) {
+                if (crossing_weights) len[q] = 1.0;
                 if (n_frames <= 1) {
 #pragma omp atomic
                     cube_out[idx[q]] += len[q] * yk;
@@ -374,6 +378,31 @@ int orc_backproject(const orc_cube *c, int32_t n_frames, int32_t n_img,
         free(len);
     }
     return 0;
+}
+
+/* x = P^T y (header: Eq. lo transposed). */
+int orc_backproject(const orc_cube *c, int32_t n_frames, int32_t n_img,
+                    int32_t nu, int32_t nv, const double *pointing,
+                    const uint8_t *mask, const double *images, int64_t n_rays,
+                    const int64_t *ray_ids, double *cube_out)
+{
+    return backproject_impl(c, n_frames, n_img, nu, nv, pointing, mask,
+                            images, n_rays, ray_ids, cube_out, 0);
+}
+
+/* Crossing weights C_j = sum over the rays k with a positive-length segment
+ * in voxel j of |g_k y_k| (time-weighted like the transpose): the transpose
+ * with every length replaced by 1 and every pixel value by its magnitude.
+ * It scales the error bound of a transpose whose segment lengths carry an
+ * absolute rounding error independent of their length. */
+int orc_crossing_weights(const orc_cube *c, int32_t n_frames, int32_t n_img,
+                         int32_t nu, int32_t nv, const double *pointing,
+                         const uint8_t *mask, const double *images,
+                         int64_t n_rays, const int64_t *ray_ids,
+                         double *cube_out)
+{
+    return backproject_impl(c, n_frames, n_img, nu, nv, pointing, mask,
+                            images, n_rays, ray_ids, cube_out, 1);
 }
 
 /* Total number of Siddon segments (positive-length voxel intersections) of

@@ -2,15 +2,21 @@
 
 Tolerances (FP32 path vs the FP64 oracle):
   projection, per pixel:  |y - y*| <= 1e-5 |y*| + 1e-7 max|y*|
-  transpose, per voxel:   |x - x*| <= 1e-5 |x*| + 1e-7 max|x*|  (non-negative
-                          images, so the sums do not cancel)
+  transpose, per voxel:   |x - x*| <= 1e-5 |x*| + 8 u t_max C_j, u = 2^-24,
+                          t_max = the cube's diagonal, C_j = sum of |g y| over
+                          the rays crossing voxel j (oracle crossing weights)
   bf16-stored cube:       the same bound against the oracle on the rounded
                           cube; 1e-2 relative against the float32 cube
-The relative 1e-5 is the stated accuracy of the FP32 path.  The absolute
-floor is one FP32 ulp-scale (1e-7) of the largest value: pixels whose rays
-only graze the cube hold values far below the bright ones, and FP32 cannot
-resolve them relative to themselves better than the rounding of the entry
-point, which is set by the bright pixels' scale of lengths.
+The relative 1e-5 is the stated accuracy of the FP32 path.  Every FP32
+segment length is a difference of two crossing parameters measured from the
+ray's entry point, so it carries an absolute error of a few ulp(t) <= a few
+u t_max whatever its length: along a ray these errors telescope (P), but a
+voxel that a ray only clips at a corner receives that absolute error on a
+tiny length.  The transpose bound therefore adds 8 u t_max per crossing ray,
+weighted by the ray's |g y|.  The projection's absolute floor, 1e-7 of the
+largest pixel, covers pixels whose rays only graze the cube: their values
+are far below the bright ones, and one crossing's rounding is not small
+relative to them.
 """
 
 import numpy as np
@@ -45,6 +51,22 @@ def assert_close(got, want, what, rtol=RTOL_F32, atol_frac=ATOL_FRAC):
         "%s: %d of %d values outside %.1e rel + %.1e x max (max %.3e); worst "
         "rel err %.3e" % (what, int(bad.sum()), bad.size, rtol, atol_frac,
                           scale, float(rel[bad].max())))
+
+
+def assert_transpose_close(got, want, cw, geom, what, rtol=RTOL_F32):
+    """Per-voxel transpose bound (module docstring); ``cw`` are the oracle's
+    crossing weights for the same images."""
+    t_max = float(np.sqrt(sum((geom["n" + a] * geom["d" + a]) ** 2
+                              for a in "xyz")))
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    bound = rtol * np.abs(want) + 8.0 * 2.0 ** -24 * t_max * np.asarray(cw)
+    err = np.abs(got - want)
+    bad = err > bound
+    assert not bad.any(), (
+        "%s: %d of %d voxels outside the bound; worst err/bound %.3f"
+        % (what, int(bad.sum()), bad.size, float((err / np.maximum(
+            bound, 1e-300)).max())))
 
 
 def to_dev(a, dtype=torch.float32):

@@ -13,8 +13,8 @@ import torch
 
 import synth
 from oracle import siddon
-from tests.gpu_util import (assert_close, mask_dev, require_gpu, to_dev,
-                            RTOL_F32)
+from tests.gpu_util import (assert_close, assert_transpose_close, mask_dev,
+                            require_gpu, to_dev, RTOL_F32)
 
 pytestmark = pytest.mark.gpu
 
@@ -65,8 +65,9 @@ def test_small_config_full_transpose_and_dot(T):
     rng = np.random.default_rng(0)
     y = rng.random((8, c["nv"], c["nu"])).astype(np.float32)
     want = siddon.backproject(c["geom"], y, c["pointing"], c["nu"], c["nv"])
+    cw = siddon.crossing_weights(c["geom"], y, c["pointing"], c["nu"], c["nv"])
     got = T.tomo_backproject(to_dev(y), c["geom"], c["pointing"]).cpu().numpy()
-    assert_close(got, want, "P^T small")
+    assert_transpose_close(got, want, cw, c["geom"], "P^T small")
     # adjoint identity with FP64 dots of FP32 results
     x = c["cube"]
     Px = T.tomo_project(to_dev(x), c["geom"], c["pointing"], c["nu"],
@@ -86,8 +87,9 @@ def test_ragged_masked_gains_roll(T, seed):
     assert np.all(got[mask != 0] == 0.0)
     y = np.random.default_rng(seed + 10).random((5, 53, 37)).astype(np.float32)
     want_t = siddon.backproject(g, y, ptg, 37, 53, mask)
+    cw = siddon.crossing_weights(g, y, ptg, 37, 53, mask)
     got_t = T.tomo_backproject(to_dev(y), g, ptg, mask=md).cpu().numpy()
-    assert_close(got_t, want_t, "P^T ragged")
+    assert_transpose_close(got_t, want_t, cw, g, "P^T ragged")
 
 
 def test_tilings_agree(T):
@@ -146,9 +148,10 @@ def test_time_interpolation(T):
     assert_close(got, want, "P time")
     y = np.random.default_rng(16).random((5, 53, 37)).astype(np.float32)
     want_t = siddon.backproject(g, y, ptg, 37, 53, mask, n_frames=4)
+    cw = siddon.crossing_weights(g, y, ptg, 37, 53, mask, n_frames=4)
     got_t = T.tomo_backproject(to_dev(y), g, ptg, mask=md,
                                n_frames=4).cpu().numpy()
-    assert_close(got_t, want_t, "P^T time")
+    assert_transpose_close(got_t, want_t, cw, g, "P^T time")
 
 
 def test_bf16_cube(T):
@@ -196,9 +199,11 @@ def test_single_config_full(T):
     y = want.astype(np.float32)
     want_t = siddon.backproject(c["geom"], y, c["pointing"], c["nu"], c["nv"],
                                 c["mask"])
+    cw = siddon.crossing_weights(c["geom"], y, c["pointing"], c["nu"],
+                                 c["nv"], c["mask"])
     got_t = T.tomo_backproject(to_dev(y), c["geom"], c["pointing"],
                                mask=md).cpu().numpy()
-    assert_close(got_t, want_t, "P^T single")
+    assert_transpose_close(got_t, want_t, cw, c["geom"], "P^T single")
 
 
 def _sampled_parity(T, c, frac, seed, dtype=torch.float32):

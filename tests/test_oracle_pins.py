@@ -466,3 +466,28 @@ def test_cg_warm_start_and_J_identity():
                                      rel=1e-10)
     x_more, rep_more = solver.cg(pb, 30, x0=x5)
     assert rep_more["J"][-1] <= rep5["J"][-1]
+
+
+def test_crossing_weights():
+    """C_j with unit images counts the rays crossing each voxel: it matches
+    the brute-force clip (positive lengths), and its total is the number of
+    segments; with |y| weights it bounds |P^T y| / (largest length)."""
+    g, ptg, mask, rng = _small_scene()
+    ones = np.ones((5, 6, 10))
+    p1 = ptg.copy()
+    p1[:, 10] = 1.0
+    Cw = siddon.crossing_weights(g, ones, p1, 10, 6, mask)
+    want = np.zeros(g["nx"] * g["ny"] * g["nz"])
+    for r in range(300):
+        n, iv, iu = r // 60, (r // 10) % 6, r % 10
+        if mask.reshape(-1)[r]:
+            continue
+        o, u = siddon.ray(p1[n], iu, iv)
+        want += checks.brute_force_ray(g, o, u) > 0
+    np.testing.assert_array_equal(Cw.reshape(-1), want)
+    assert Cw.sum() == siddon.count_segments(g, p1, 10, 6, mask)
+    y = rng.standard_normal((5, 6, 10))
+    Cy = siddon.crossing_weights(g, y, ptg, 10, 6, mask)
+    Pty = siddon.backproject(g, y, ptg, 10, 6, mask)
+    diag = np.sqrt(sum((g["n" + a] * g["d" + a]) ** 2 for a in "xyz"))
+    assert np.all(np.abs(Pty) <= Cy * min(diag, max(g["dx"], g["dy"], g["dz"]) * np.sqrt(3)) + 1e-12)
