@@ -64,6 +64,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--images", type=int, default=0,
+                    help="keep only this many images (evenly spaced) of the "
+                         "workload: a reduced case for profiler captures")
     return ap.parse_args(argv)
 
 
@@ -157,9 +160,16 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- workload
 
-def make_workload(name):
+def make_workload(name, n_images=0):
     import synth
-    return synth.make_config(name)
+    c = synth.make_config(name)
+    if n_images and n_images < c["pointing"].shape[0]:
+        keep = np.linspace(0, c["pointing"].shape[0] - 1, n_images).astype(int)
+        c["pointing"] = np.ascontiguousarray(c["pointing"][keep])
+        if c["mask"] is not None:
+            c["mask"] = np.ascontiguousarray(c["mask"][keep])
+        c["name"] += "-%dimg" % n_images
+    return c
 
 
 def algorithmic_bytes(n_rays, n_live, segments, kind):
@@ -231,7 +241,7 @@ def run_reference(args, rank, world):
     """The reference arm: the FP64 oracle, on the host cores."""
     if rank != 0:
         return 0
-    c = make_workload(args.workload)
+    c = make_workload(args.workload, args.images)
     per_step = max(0.5, min(5.0, 60.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(c, per_step, seed=1)
@@ -269,7 +279,7 @@ def run_gpu(args, rank, local_rank, world):
     lib_build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    c = make_workload(args.workload)
+    c = make_workload(args.workload, args.images)
     g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
     n_img = ptg.shape[0]
     ctx = T.Context(local_rank)
@@ -399,7 +409,9 @@ def run_gpu(args, rank, local_rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {
-                "workload": WORKLOAD_TEXT[args.workload],
+                "workload": WORKLOAD_TEXT[args.workload] + (
+                    " (reduced to %d images)" % args.images if args.images
+                    else ""),
                 "step": ("one tomo_solve: FP64 ray setup, b = P^T M y, %d CG "
                          "iterations" % args.iters),
                 "cg_iters_per_step": args.iters,

@@ -10,43 +10,13 @@
 
 #include <cuda_runtime.h>
 
-#include "tomo_internal.cuh"
+#include "host.h"
 
 using namespace tomo;
+using namespace tomo::host;
 
-namespace {
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-}  // namespace
-
-struct tomo_ctx {
-    int device = 0;
-    int num_sms = 0;
-    char err[512] = { 0 };
-    bool ray_cache = true;
-    Tiling tiling = { 32, 8, 8 };
-    // geometry cache
-    bool key_valid = false;
-    uint64_t key = 0;
-    cudaEvent_t setup_done = nullptr;
-    // per-geometry buffers
-    DevBuf ptg, frames, tan_u, tan_v, params, rays;
-    // solver workspace
-    DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
-    // launch counts and optional per-launch event timing
-    bool profile = false;
-    int64_t launches[TOMO_K_COUNT] = { 0 };
-    double ms[TOMO_K_COUNT] = { 0 };
-    std::vector<cudaEvent_t> ev_start, ev_stop;  // event pool (pairs)
-    std::vector<int> ev_free;                    // free pair slots
-    std::vector<int> ev_pending_slot, ev_pending_kind;
-};
-
-namespace {
+namespace tomo {
+namespace host {
 
 tomo_status fail(tomo_ctx *ctx, tomo_status st, const char *fmt, ...)
 {
@@ -59,72 +29,6 @@ tomo_status fail(tomo_ctx *ctx, tomo_status st, const char *fmt, ...)
     return st;
 }
 
-#define CUDA_TRY(ctx, call)                                                  \
-    do {                                                                     \
-        cudaError_t e_ = (call);                                             \
-        if (e_ != cudaSuccess)                                               \
-            return fail((ctx), e_ == cudaErrorMemoryAllocation               \
-                                   ? TOMO_ERR_OOM : TOMO_ERR_CUDA,           \
-                        "%s: %s", #call, cudaGetErrorString(e_));            \
-    } while (0)
-
-// Launch a kernel through its host launcher `call`, counted and (optionally)
-// timed as class `kind` on stream `s`.
-#define LAUNCH(ctx, kind, s, call)                                           \
-    do {                                                                     \
-        Launch L_((ctx), (kind), (s));                                       \
-        CUDA_TRY((ctx), (call));                                             \
-    } while (0)
-
-// Makes the context's device current for the call and restores the caller's.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) return;
-        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-// Counts one kernel launch of class `kind`; with profiling on, brackets it
-// with a pair of CUDA events on the launching stream.
-struct Launch {
-    tomo_ctx *ctx;
-    int kind;
-    cudaStream_t s;
-    int slot = -1;
-    Launch(tomo_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k), s(st)
-    {
-        ctx->launches[kind] += 1;
-        if (!ctx->profile) return;
-        if (ctx->ev_free.empty()) {
-            cudaEvent_t a, b;
-            if (cudaEventCreate(&a) != cudaSuccess) return;
-            if (cudaEventCreate(&b) != cudaSuccess) {
-                cudaEventDestroy(a);
-                return;
-            }
-            ctx->ev_start.push_back(a);
-            ctx->ev_stop.push_back(b);
-            ctx->ev_free.push_back((int)ctx->ev_start.size() - 1);
-        }
-        slot = ctx->ev_free.back();
-        ctx->ev_free.pop_back();
-        cudaEventRecord(ctx->ev_start[slot], s);
-    }
-    ~Launch()
-    {
-        if (slot < 0) return;
-        cudaEventRecord(ctx->ev_stop[slot], s);
-        ctx->ev_pending_slot.push_back(slot);
-        ctx->ev_pending_kind.push_back(kind);
-    }
-};
 
 tomo_status ensure(tomo_ctx *ctx, DevBuf &b, size_t bytes)
 {
@@ -223,9 +127,8 @@ tomo_status check_pointing(tomo_ctx *ctx, const tomo_pointing *p,
     return TOMO_OK;
 }
 
-tomo_status check_tiling(tomo_ctx *ctx)
+tomo_status check_tiling(tomo_ctx *ctx, Tiling t)
 {
-    const Tiling t = ctx->tiling;
     const int wu = t.warp_u;
     if (wu < 1 || wu > 32 || (wu & (wu - 1)) != 0)
         return fail(ctx, TOMO_ERR_ARG, "warp_u must be a power of 2 in [1, 32]");
@@ -320,9 +223,19 @@ tomo_status common_checks(tomo_ctx *ctx, const tomo_cube_geom *c,
     tomo_status st;
     if ((st = check_cube(ctx, c, n_frames)) || (st = check_img(ctx, g)) ||
         (st = check_pointing(ctx, ptg, g, n_frames)) ||
-        (st = check_tiling(ctx)))
+        (st = check_tiling(ctx, tiling_for(ctx, c, g))))
         return st;
     return TOMO_OK;
+}
+
+Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                  const tomo_image_geom *g)
+{
+    for (const Tuned &t : ctx->tuned)
+        if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.nu == g->nu &&
+            t.nv == g->nv)
+            return t.tl;
+    return ctx->tiling;
 }
 
 int reduce_grid(const tomo_ctx *ctx, int64_t n)
@@ -334,7 +247,9 @@ int reduce_grid(const tomo_ctx *ctx, int64_t n)
     return (int)(g < 1 ? 1 : g);
 }
 
-}  // namespace
+
+}  // namespace host
+}  // namespace tomo
 
 extern "C" {
 
@@ -395,6 +310,8 @@ void tomo_destroy(tomo_ctx *ctx)
                        &ctx->counter, &ctx->count64 };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
+    free_plan(ctx);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->setup_done) cudaEventDestroy(ctx->setup_done);
     for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->ev_stop) cudaEventDestroy(e);
@@ -499,8 +416,8 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                  (const ImgParam *)ctx->params.p, cube_dev,
                                  dtype, fstride, n_frames > 1, mask_dev,
                                  images_dev, img->n_img, img->nu, img->nv,
-                                 cube->nx, cube->nx * cube->ny, ctx->tiling,
-                                 nullptr, s));
+                                 cube->nx, cube->nx * cube->ny,
+                                 tiling_for(ctx, cube, img), nullptr, s));
     return TOMO_OK;
 }
 
@@ -534,7 +451,8 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                  (const ImgParam *)ctx->params.p, images_dev,
                                  mask_dev, cube_dev, fstride, n_frames > 1,
                                  img->n_img, img->nu, img->nv, cube->nx,
-                                 cube->nx * cube->ny, ctx->tiling, nullptr, s));
+                                 cube->nx * cube->ny,
+                                 tiling_for(ctx, cube, img), nullptr, s));
     return TOMO_OK;
 }
 
@@ -581,7 +499,7 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = ensure(ctx, ctx->count64, sizeof(unsigned long long)))) return st;
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->count64.p, 0, sizeof(unsigned long long), s));
     LAUNCH(ctx, TOMO_K_FORWARD, s, launch_count((const RayRec *)ctx->rays.p, mask_dev, img->n_img,
-                               img->nu, img->nv, ctx->tiling,
+                               img->nu, img->nv, tiling_for(ctx, cube, img),
                                (unsigned long long *)ctx->count64.p, s));
     unsigned long long n = 0;
     CUDA_TRY(ctx, cudaMemcpyAsync(&n, ctx->count64.p, sizeof(n),
@@ -652,7 +570,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const int nxny = cube->nx * cube->ny;
     const float lam = (float)lambda;
     const int grid = reduce_grid(ctx, n > m ? n : m);
-    const Tiling tl = ctx->tiling;
+    const Tiling tl = tiling_for(ctx, cube, img);
 
     CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
     CUDA_TRY(ctx, cudaMemsetAsync(S, 0, sizeof(double) * S_NSLOTS, s));

@@ -1,0 +1,266 @@
+// Batched projector, transpose and CG over many independent problems of
+// uneven sizes (cube side, image count and image size differ per problem).
+//
+// Ray kernels are persistent: one grid of (SM count x resident CTAs) CTAs
+// pulls work items from an atomic counter until the list is exhausted (no
+// CTA ever waits for another).  An item is one pixel tile of one image of
+// one problem; problems are laid out back to back in item space through a
+// prefix array, and each problem carries its own tile shape (256 threads per
+// CTA for all of them), chosen by the autotuner.  The walk is the same
+// Siddon walk as the single-problem kernels (walk.cuh).
+//
+// Vector kernels run over (problem, chunk of kChunk elements) items: a CTA
+// handles one chunk, writes its FP64 partial sums, and a finalize kernel
+// with one CTA per problem adds that problem's partials in a fixed order and
+// applies the CG scalar step (reduce.cuh).  Every problem has its own FP64
+// slots and "done" flag, so problems that converge early stop working while
+// the others continue.
+#include <cuda_bf16.h>
+
+#include "batch.cuh"
+#include "reduce.cuh"
+#include "walk.cuh"
+
+namespace tomo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Problem owning `item`: the largest p with prefix[p] <= item.
+__device__ __forceinline__ int owner(const int64_t *__restrict__ prefix,
+                                     int n_probs, int64_t item)
+{
+    int lo = 0, hi = n_probs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool kAdjoint>
+__global__ void __launch_bounds__(kThreads)
+k_walk_batched(const WalkDesc *__restrict__ descs,
+               const int64_t *__restrict__ prefix, int n_probs,
+               unsigned long long *next_item)
+{
+    __shared__ long long s_item;
+    const int64_t n_items = prefix[n_probs];
+    for (;;) {
+        __syncthreads();  // every thread has read the previous s_item
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+        __syncthreads();
+        const int64_t item = s_item;
+        if (item >= n_items) break;
+        const int p = owner(prefix, n_probs, item);
+        const WalkDesc d = descs[p];
+        if (d.done != nullptr && *d.done != 0.0) continue;
+        const int64_t t = item - prefix[p];
+        const int tu = (int)(t % d.tiles_u);
+        const int64_t rest = t / d.tiles_u;
+        const int tv = (int)(rest % d.tiles_v);
+        const int img = (int)(rest / d.tiles_v);
+        int iu, iv;
+        if (!pixel_of_thread(d.tl, tu, tv, d.nu, d.nv, iu, iv)) continue;
+        const int64_t id = ((int64_t)img * d.nv + iv) * d.nu + iu;
+        const bool masked = d.mask != nullptr && d.mask[id] != 0;
+        const float gain = d.prm[img].gain;
+        if (!kAdjoint) {
+            float y = 0.0f;
+            if (!masked) {
+                const RayRec r = load_ray(d.rays + id);
+                if (r.chord > 0.0f) {
+                    GatherOp<float> op;
+                    op.c = d.src;
+                    op.acc = 0.0f;
+                    siddon_walk(r, d.nx, d.nxny, op);
+                    y = gain * op.acc;
+                }
+            }
+            d.dst[id] = y;
+        } else if (!masked) {
+            const float yv = gain * d.src[id];
+            if (yv != 0.0f) {
+                const RayRec r = load_ray(d.rays + id);
+                if (r.chord > 0.0f) {
+                    ScatterOp op;
+                    op.c = d.dst;
+                    op.y = yv;
+                    siddon_walk(r, d.nx, d.nxny, op);
+                }
+            }
+        }
+    }
+}
+
+// Operation codes (batch.cuh): what one vector pass does.
+constexpr int V_SUMSQ = BV_SUMSQ, V_ZERO = BV_ZERO, V_INIT = BV_INIT,
+              V_PRIOR = BV_PRIOR, V_PQ = BV_PQ, V_UPDATE = BV_UPDATE,
+              V_DIR = BV_DIR, V_PRIOR_X = BV_PRIOR_X;
+
+__global__ void __launch_bounds__(kThreads)
+k_vec_batched(int op, const VecDesc *__restrict__ descs,
+              const int64_t *__restrict__ prefix, int n_probs, bool warm,
+              double *partials)
+{
+    __shared__ double sm[32];
+    const int64_t n_items = prefix[n_probs];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int p = owner(prefix, n_probs, item);
+        const VecDesc &d = descs[p];
+        const int64_t len = (op == V_SUMSQ) ? d.m : d.n;
+        // this item's chunk of its problem: elements [c.c0, c.c1)
+        struct { int64_t c0, c1; } c;
+        c.c0 = (item - prefix[p]) * kChunk;
+        c.c1 = c.c0 + kChunk < len ? c.c0 + kChunk : len;
+        double s0 = 0.0, s1 = 0.0;
+        const bool done = d.S[S_DONE] != 0.0;
+        if (op == V_SUMSQ) {
+            for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x)
+                if (d.mask == nullptr || d.mask[i] == 0) {
+                    const double yi = d.y[i];
+                    s0 += yi * yi;
+                }
+        } else if (op == V_ZERO) {
+            for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
+                d.b[i] = 0.0f;
+                if (!warm) d.x[i] = 0.0f;
+            }
+        } else if (op == V_INIT) {
+            for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
+                const float bi = d.b[i];
+                const float ri = warm ? bi - d.q[i] : bi;
+                d.r[i] = ri;
+                d.p[i] = ri;
+                s0 += (double)ri * ri;
+                if (warm) s1 += (double)d.x[i] * ((double)ri + bi);
+            }
+        } else if (op == V_PRIOR || op == V_PRIOR_X) {
+            if (!done) {
+                const float *src = (op == V_PRIOR_X) ? d.x : d.p;
+                const int nx = d.nx, ny = d.ny, nz = d.nz;
+                for (int64_t v = c.c0 + threadIdx.x; v < c.c1; v += blockDim.x) {
+                    const int i = (int)(v % nx);
+                    const int64_t r = v / nx;
+                    const int j = (int)(r % ny), k = (int)(r / ny);
+                    d.q[v] = prior_at(src, v, i, j, k, nx, ny, nz, d.lam);
+                }
+            }
+        } else if (op == V_PQ) {
+            if (!done)
+                for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x)
+                    s0 += (double)d.p[i] * d.q[i];
+        } else if (op == V_UPDATE) {
+            if (!done) {
+                const float alpha = (float)d.S[S_ALPHA];
+                for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
+                    const float xi = fmaf(alpha, d.p[i], d.x[i]);
+                    const float ri = fmaf(-alpha, d.q[i], d.r[i]);
+                    d.x[i] = xi;
+                    d.r[i] = ri;
+                    s0 += (double)ri * ri;
+                    s1 += (double)xi * ((double)ri + d.b[i]);
+                }
+            }
+        } else if (op == V_DIR) {
+            if (!done) {
+                const float beta = (float)d.S[S_BETA];
+                for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x)
+                    d.p[i] = fmaf(beta, d.p[i], d.r[i]);
+            }
+        }
+        if (op == V_SUMSQ || op == V_INIT || op == V_PQ || op == V_UPDATE) {
+            s0 = block_sum(s0, sm);
+            s1 = block_sum(s1, sm);
+            if (threadIdx.x == 0) {
+                partials[2 * item] = s0;
+                partials[2 * item + 1] = s1;
+            }
+        }
+    }
+}
+
+// One CTA per problem: add its partials in item order, apply the step.
+__global__ void __launch_bounds__(kThreads)
+k_finalize_batched(int op, const VecDesc *__restrict__ descs,
+                   const int64_t *__restrict__ prefix, int n_probs,
+                   double tol2, const double *__restrict__ partials)
+{
+    __shared__ double sm[32];
+    for (int p = blockIdx.x; p < n_probs; p += gridDim.x) {
+        const VecDesc &d = descs[p];
+        if ((op == V_PQ || op == V_UPDATE) && d.S[S_DONE] != 0.0) continue;
+        double s0 = 0.0, s1 = 0.0;
+        for (int64_t i = prefix[p] + threadIdx.x; i < prefix[p + 1];
+             i += blockDim.x) {
+            s0 += partials[2 * i];
+            s1 += partials[2 * i + 1];
+        }
+        s0 = block_sum(s0, sm);
+        s1 = block_sum(s1, sm);
+        if (threadIdx.x != 0) continue;
+        if (op == V_SUMSQ)
+            d.S[S_YMY] = s0;
+        else if (op == V_INIT)
+            cg_finalize_init(d.S, d.report, s0, s1, tol2);
+        else if (op == V_PQ)
+            cg_finalize_pq(d.S, s0);
+        else if (op == V_UPDATE)
+            cg_finalize_update(d.S, d.report, s0, s1);
+    }
+}
+
+}  // namespace
+
+int walk_batched_blocks_per_sm()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, k_walk_batched<false>, kThreads, 0) != cudaSuccess)
+        return 1;
+    int m = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &m, k_walk_batched<true>, kThreads, 0) != cudaSuccess)
+        return 1;
+    return n < m ? (n > 0 ? n : 1) : (m > 0 ? m : 1);
+}
+
+cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,
+                                const int64_t *prefix, int n_probs,
+                                unsigned long long *next_item, int grid,
+                                cudaStream_t s)
+{
+    if (adjoint)
+        k_walk_batched<true><<<grid, kThreads, 0, s>>>(descs, prefix, n_probs,
+                                                        next_item);
+    else
+        k_walk_batched<false><<<grid, kThreads, 0, s>>>(descs, prefix, n_probs,
+                                                         next_item);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vec_batched(int op, const VecDesc *descs,
+                               const int64_t *prefix, int n_probs, bool warm,
+                               double *partials, int grid, cudaStream_t s)
+{
+    k_vec_batched<<<grid, kThreads, 0, s>>>(op, descs, prefix, n_probs, warm,
+                                            partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize_batched(int op, const VecDesc *descs,
+                                    const int64_t *prefix, int n_probs,
+                                    double tol2, const double *partials,
+                                    cudaStream_t s)
+{
+    const int grid = n_probs < 1024 ? n_probs : 1024;
+    k_finalize_batched<<<grid, kThreads, 0, s>>>(op, descs, prefix, n_probs,
+                                                 tol2, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

@@ -1,0 +1,149 @@
+// Host-side internals of libtomo shared by the C ABI translation units:
+// the context, argument checks, workspace growth, launch accounting.
+#pragma once
+
+#include <stdarg.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+namespace host {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// A tile shape chosen by the autotuner for one problem size.
+struct Tuned {
+    int32_t nx, ny, nz, nu, nv;
+    Tiling tl;
+    float fwd_ms, adj_ms;
+};
+
+struct BatchPlan;  // batch_api.cu
+
+}  // namespace host
+}  // namespace tomo
+
+struct tomo_ctx {
+    int device = 0;
+    int num_sms = 0;
+    char err[512] = { 0 };
+    bool ray_cache = true;
+    tomo::Tiling tiling = { 32, 8, 8 };
+    // geometry cache
+    bool key_valid = false;
+    uint64_t key = 0;
+    cudaEvent_t setup_done = nullptr;
+    // per-geometry buffers
+    tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
+    // solver workspace
+    tomo::host::DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
+    // tuned tile shapes per problem size, and the cached batch plan
+    std::vector<tomo::host::Tuned> tuned;
+    tomo::host::BatchPlan *plan = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    // launch counts and optional per-launch event timing
+    bool profile = false;
+    int64_t launches[TOMO_K_COUNT] = { 0 };
+    double ms[TOMO_K_COUNT] = { 0 };
+    std::vector<cudaEvent_t> ev_start, ev_stop;  // event pool (pairs)
+    std::vector<int> ev_free;                    // free pair slots
+    std::vector<int> ev_pending_slot, ev_pending_kind;
+};
+
+namespace tomo {
+namespace host {
+
+tomo_status fail(tomo_ctx *ctx, tomo_status st, const char *fmt, ...);
+tomo_status ensure(tomo_ctx *ctx, DevBuf &b, size_t bytes);
+tomo_status check_cube(tomo_ctx *ctx, const tomo_cube_geom *c, int32_t n_frames);
+tomo_status check_img(tomo_ctx *ctx, const tomo_image_geom *g);
+tomo_status check_pointing(tomo_ctx *ctx, const tomo_pointing *p,
+                           const tomo_image_geom *g, int32_t n_frames);
+tomo_status check_tiling(tomo_ctx *ctx, Tiling t);
+bool aligned(const void *p, size_t a);
+uint64_t fnv1a(uint64_t h, const void *data, size_t n);
+CubeDev cube_dev(const tomo_cube_geom *c);
+int reduce_grid(const tomo_ctx *ctx, int64_t n);
+// Tile shape for a problem: the tuned one for its size if any, else the
+// context's option.
+Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                  const tomo_image_geom *g);
+void free_plan(tomo_ctx *ctx);
+
+#define CUDA_TRY(ctx, call)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess)                                               \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation               \
+                                   ? TOMO_ERR_OOM : TOMO_ERR_CUDA,           \
+                        "%s: %s", #call, cudaGetErrorString(e_));            \
+    } while (0)
+
+// Launch a kernel through its host launcher `call`, counted and (optionally)
+// timed as class `kind` on stream `s`.
+#define LAUNCH(ctx, kind, s, call)                                           \
+    do {                                                                     \
+        Launch L_((ctx), (kind), (s));                                       \
+        CUDA_TRY((ctx), (call));                                             \
+    } while (0)
+
+// Makes the context's device current for the call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Counts one kernel launch of class `kind`; with profiling on, brackets it
+// with a pair of CUDA events on the launching stream.
+struct Launch {
+    tomo_ctx *ctx;
+    int kind;
+    cudaStream_t s;
+    int slot = -1;
+    Launch(tomo_ctx *c, int k, cudaStream_t st) : ctx(c), kind(k), s(st)
+    {
+        ctx->launches[kind] += 1;
+        if (!ctx->profile) return;
+        if (ctx->ev_free.empty()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) {
+                cudaEventDestroy(a);
+                return;
+            }
+            ctx->ev_start.push_back(a);
+            ctx->ev_stop.push_back(b);
+            ctx->ev_free.push_back((int)ctx->ev_start.size() - 1);
+        }
+        slot = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        cudaEventRecord(ctx->ev_start[slot], s);
+    }
+    ~Launch()
+    {
+        if (slot < 0) return;
+        cudaEventRecord(ctx->ev_stop[slot], s);
+        ctx->ev_pending_slot.push_back(slot);
+        ctx->ev_pending_kind.push_back(kind);
+    }
+};
+
+}  // namespace host
+}  // namespace tomo

@@ -1,0 +1,104 @@
+// FP64 block reductions and the scalar steps of conjugate gradients, shared
+// by the single-problem and the batched solvers.
+//
+// CG on (P^T M P + lambda D^T D) x = P^T M y (Eq. criterion, normal
+// equations), textbook Hestenes-Stiefel form:
+//   alpha = r.r / p.q;  x += alpha p;  r -= alpha q;
+//   beta = r'.r' / r.r; p = r' + beta p.
+// The criterion is reported through J = y^T M y - x^T (r + b), exact for
+// every CG iterate (b = P^T M y, r = b - A x).
+#pragma once
+
+#include <math.h>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the CTA; valid in thread 0.  Ends with a barrier so `sm` (32
+// doubles of shared memory) can be reused by the next call.
+__device__ __forceinline__ double block_sum(double v, double *sm)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sm[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// Scalar steps; called by one thread with the grid-wide sums.
+
+__device__ __forceinline__ void cg_finalize_init(double *S, double *report,
+                                                 double rr, double xrb,
+                                                 double tol2)
+{
+    S[S_RR] = rr;
+    S[S_RR0] = rr;
+    S[S_TOL2] = tol2;
+    S[S_ITERS] = 0.0;
+    S[S_ERR] = 0.0;
+    S[S_DONE] = (rr == 0.0) ? 1.0 : 0.0;
+    if (report != nullptr) {
+        report[0] = S[S_YMY] - xrb;
+        report[1] = rr;
+    }
+}
+
+__device__ __forceinline__ void cg_finalize_pq(double *S, double pq)
+{
+    S[S_PQ] = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        S[S_DONE] = 1.0;
+        S[S_ERR] = 1.0;
+    } else {
+        S[S_ALPHA] = S[S_RR] / pq;
+    }
+}
+
+__device__ __forceinline__ void cg_finalize_update(double *S, double *report,
+                                                   double rr_new, double xrb)
+{
+    const int k = (int)S[S_ITERS];
+    S[S_BETA] = rr_new / S[S_RR];
+    S[S_RR] = rr_new;
+    S[S_ITERS] = k + 1;
+    if (report != nullptr) {
+        report[2 * (k + 1)] = S[S_YMY] - xrb;
+        report[2 * (k + 1) + 1] = rr_new;
+    }
+    if (!isfinite(rr_new)) {
+        S[S_DONE] = 1.0;
+        S[S_ERR] = 1.0;
+    } else if (rr_new <= S[S_TOL2] * S[S_RR0]) {
+        S[S_DONE] = 1.0;
+    }
+}
+
+// The 7-point stencil of lambda D^T D at voxel (i, j, k) of x.
+__device__ __forceinline__ float prior_at(const float *__restrict__ x,
+                                          int64_t v, int i, int j, int k,
+                                          int nx, int ny, int nz, float lam)
+{
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    const float xc = x[v];
+    float s = 0.0f;
+    if (i > 0) s += xc - x[v - 1];
+    if (i < nx - 1) s += xc - x[v + 1];
+    if (j > 0) s += xc - x[v - sy];
+    if (j < ny - 1) s += xc - x[v + sy];
+    if (k > 0) s += xc - x[v - sz];
+    if (k < nz - 1) s += xc - x[v + sz];
+    return lam * s;
+}
+
+}  // namespace tomo

@@ -19,34 +19,13 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
-#include "tomo_internal.cuh"
+#include "reduce.cuh"
 
 namespace tomo {
 
 namespace {
 
 constexpr int kThreads = 256;
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the CTA; the result is valid in thread 0.  Ends with a barrier so
-// the shared scratch can be reused by the next call.
-__device__ double block_sum(double v, double *sm)
-{
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sm[w] = v;
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    v = (threadIdx.x < nw) ? sm[threadIdx.x] : 0.0;
-    if (w == 0) v = warp_sum(v);
-    __syncthreads();
-    return v;
-}
 
 // Two-stage reduction of K values.  Returns true in the last CTA, where
 // total[] (valid in thread 0) holds the grid-wide sums.
@@ -76,9 +55,18 @@ __device__ bool grid_sum(double (&v)[K], double *partials,
     return true;
 }
 
-__device__ __forceinline__ uint16_t to_bf16_bits(float v)
+// Stores one element of the CG direction.  With a bf16 copy (p16 != NULL)
+// the direction itself is rounded to bf16 (round to nearest even) and the
+// float copy keeps exactly that value, so the projector (which gathers the
+// bf16 copy), the prior and the vector updates all use the same p, and CG
+// stays an exact line search along a slightly perturbed direction.
+__device__ __forceinline__ float direction_store(float v, uint16_t *p16,
+                                                 int64_t i)
 {
-    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    if (p16 == nullptr) return v;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    p16[i] = __bfloat16_as_ushort(h);
+    return __bfloat162float(h);
 }
 
 __global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
@@ -90,17 +78,8 @@ __global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= nx || j >= ny) return;
-    const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const int64_t v = k * sz + j * sy + i;
-    const float xc = x[v];
-    float s = 0.0f;
-    if (i > 0) s += xc - x[v - 1];
-    if (i < nx - 1) s += xc - x[v + 1];
-    if (j > 0) s += xc - x[v - sy];
-    if (j < ny - 1) s += xc - x[v + sy];
-    if (k > 0) s += xc - x[v - sz];
-    if (k < nz - 1) s += xc - x[v + sz];
-    const float val = lam * s;
+    const int64_t v = ((int64_t)k * ny + j) * nx + i;
+    const float val = prior_at(x, v, i, j, k, nx, ny, nz, lam);
     q[v] = accumulate ? q[v] + val : val;
 }
 
@@ -149,24 +128,13 @@ __global__ void k_cg_init(const float *__restrict__ b,
         const float bi = b[i];
         const float ri = (q != nullptr) ? bi - q[i] : bi;
         r[i] = ri;
-        p[i] = ri;
-        if (p16 != nullptr) p16[i] = to_bf16_bits(ri);
+        p[i] = direction_store(ri, p16, i);
         v[0] += (double)ri * ri;
         if (x != nullptr) v[1] += (double)x[i] * ((double)ri + bi);
     }
     double tot[2];
-    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-        S[S_RR] = tot[0];
-        S[S_RR0] = tot[0];
-        S[S_TOL2] = tol2;
-        S[S_ITERS] = 0.0;
-        S[S_ERR] = 0.0;
-        S[S_DONE] = (tot[0] == 0.0) ? 1.0 : 0.0;
-        if (report != nullptr) {
-            report[0] = S[S_YMY] - tot[1];
-            report[1] = tot[0];
-        }
-    }
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
+        cg_finalize_init(S, report, tot[0], tot[1], tol2);
 }
 
 __global__ void k_cg_pq(const float *__restrict__ p, const float *__restrict__ q,
@@ -179,16 +147,8 @@ __global__ void k_cg_pq(const float *__restrict__ p, const float *__restrict__ q
          i += (int64_t)gridDim.x * blockDim.x)
         v[0] += (double)p[i] * q[i];
     double tot[1];
-    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0) {
-        const double pq = tot[0];
-        S[S_PQ] = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            S[S_DONE] = 1.0;
-            S[S_ERR] = 1.0;
-        } else {
-            S[S_ALPHA] = S[S_RR] / pq;
-        }
-    }
+    if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0)
+        cg_finalize_pq(S, tot[0]);
 }
 
 __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
@@ -211,23 +171,8 @@ __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
         v[1] += (double)xi * ((double)ri + b[i]);
     }
     double tot[2];
-    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0) {
-        const int k = (int)S[S_ITERS];
-        const double rr_new = tot[0];
-        S[S_BETA] = rr_new / S[S_RR];
-        S[S_RR] = rr_new;
-        S[S_ITERS] = k + 1;
-        if (report != nullptr) {
-            report[2 * (k + 1)] = S[S_YMY] - tot[1];
-            report[2 * (k + 1) + 1] = rr_new;
-        }
-        if (!isfinite(rr_new)) {
-            S[S_DONE] = 1.0;
-            S[S_ERR] = 1.0;
-        } else if (rr_new <= S[S_TOL2] * S[S_RR0]) {
-            S[S_DONE] = 1.0;
-        }
-    }
+    if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
+        cg_finalize_update(S, report, tot[0], tot[1]);
 }
 
 __global__ void k_cg_direction(const float *__restrict__ r, float *p,
@@ -238,9 +183,7 @@ __global__ void k_cg_direction(const float *__restrict__ r, float *p,
     const float beta = (float)S[S_BETA];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float pi = fmaf(beta, p[i], r[i]);
-        p[i] = pi;
-        if (p16 != nullptr) p16[i] = to_bf16_bits(pi);
+        p[i] = direction_store(fmaf(beta, p[i], r[i]), p16, i);
     }
 }
 

@@ -1,0 +1,148 @@
+// Device-side Siddon walk shared by the single-problem and batched kernels.
+//
+// The walk is the incremental form of Siddon's method (Amanatides-Woo
+// ordering): at every step the axis whose next voxel plane is nearest is
+// crossed.  Crossing parameters are evaluated as t0 + k dt with one fused
+// multiply-add (never accumulated), so every crossing carries a single
+// float rounding relative to the entry point, and segment lengths, being
+// differences of consecutive crossings, telescope to the chord.
+#pragma once
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+__device__ __forceinline__ RayRec load_ray(const RayRec *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1);
+    RayRec r;
+    r.t0x = a.x;
+    r.t0y = a.y;
+    r.t0z = a.z;
+    r.chord = a.w;
+    r.dtx = b.x;
+    r.dty = b.y;
+    r.dtz = b.z;
+    r.idx0 = __float_as_int(b.w);
+    return r;
+}
+
+// Map this thread to a pixel of tile (tu, tv) of an image; false past the
+// image edge.  A warp covers warp_u x (32 / warp_u) pixels.
+__device__ __forceinline__ bool pixel_of_thread(const Tiling t, int tu, int tv,
+                                                int nu, int nv, int &iu,
+                                                int &iv)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows = 32 / t.warp_u;
+    const int warps_u = t.tile_u / t.warp_u;
+    iu = tu * t.tile_u + (warp % warps_u) * t.warp_u + (lane % t.warp_u);
+    iv = tv * t.tile_v + (warp / warps_u) * rows + (lane / t.warp_u);
+    return iu < nu && iv < nv;
+}
+
+// Walk one ray; op(idx, len) is called for every step, including steps of
+// zero length at ties (two planes crossed at the same parameter).  The loop
+// ends after at most (#planes inside the cube + 1) steps: each step that does
+// not end the walk advances one axis, and no axis can advance past its last
+// in-cube plane because the setup kernel capped the chord there.
+template <class Op>
+__device__ __forceinline__ void siddon_walk(const RayRec &r, int nx, int nxny,
+                                            Op &op)
+{
+    const float chord = r.chord;
+    const float ax = fabsf(r.dtx), ay = fabsf(r.dty), az = fabsf(r.dtz);
+    const int sx = signbit(r.dtx) ? -1 : 1;
+    const int sy = signbit(r.dty) ? -nx : nx;
+    const int sz = signbit(r.dtz) ? -nxny : nxny;
+    float kx = 0.0f, ky = 0.0f, kz = 0.0f;
+    float tx = r.t0x, ty = r.t0y, tz = r.t0z;
+    float t = 0.0f;
+    int idx = r.idx0;
+    for (;;) {
+        const float tm = fminf(tx, fminf(ty, tz));
+        const float te = fminf(tm, chord);
+        op(idx, te - t);
+        if (te >= chord) break;
+        t = te;
+        if (tx == tm) {
+            kx += 1.0f;
+            tx = fmaf(kx, ax, r.t0x);
+            idx += sx;
+        } else if (ty == tm) {
+            ky += 1.0f;
+            ty = fmaf(ky, ay, r.t0y);
+            idx += sy;
+        } else {
+            kz += 1.0f;
+            tz = fmaf(kz, az, r.t0z);
+            idx += sz;
+        }
+    }
+}
+
+__device__ __forceinline__ float load_voxel(const float *c, int idx)
+{
+    return __ldg(c + idx);
+}
+
+__device__ __forceinline__ float load_voxel(const uint16_t *c, int idx)
+{
+    // bfloat16 -> float32 is exact: the bf16 bits are the top half
+    return __uint_as_float(((uint32_t)__ldg(c + idx)) << 16);
+}
+
+template <typename CubeT>
+struct GatherOp {
+    const CubeT *c;
+    float acc;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        acc = fmaf(len, load_voxel(c, idx), acc);
+    }
+};
+
+template <typename CubeT>
+struct GatherTimeOp {
+    const CubeT *c0;
+    const CubeT *c1;
+    float w0, w1, acc;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        const float v = fmaf(w0, load_voxel(c0, idx), w1 * load_voxel(c1, idx));
+        acc = fmaf(len, v, acc);
+    }
+};
+
+struct ScatterOp {
+    float *c;
+    float y;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        if (len > 0.0f) atomicAdd(c + idx, len * y);
+    }
+};
+
+struct ScatterTimeOp {
+    float *c0;
+    float *c1;
+    float y0, y1;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        if (len > 0.0f) {
+            atomicAdd(c0 + idx, len * y0);
+            atomicAdd(c1 + idx, len * y1);
+        }
+    }
+};
+
+struct CountOp {
+    unsigned int n;
+    __device__ __forceinline__ void operator()(int, float len)
+    {
+        n += (len > 0.0f) ? 1u : 0u;
+    }
+};
+
+}  // namespace tomo

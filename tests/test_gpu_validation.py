@@ -45,8 +45,15 @@ def _status(T, fn, *a, **k):
 def test_bad_geometry_and_pointing(T):
     g, ptg = _scene()
     cube = torch.ones((16, 16, 16), device="cuda")
-    bad = dict(g, nx=0)
-    assert _status(T, T.tomo_project, cube, bad, ptg, 16, 16) == ARG
+    lib = T.load_library()
+    ctx = T.default_context()
+    out = torch.empty((2, 16, 16), device="cuda")
+    cg = T.tomo.cube_geom_struct(dict(g, nx=0))
+    ig = T.tomo.ImageGeom(2, 16, 16)
+    assert lib.tomo_project(ctx.handle, C.byref(cg), 1,
+                            C.c_void_p(cube.data_ptr()), 0, C.byref(ig),
+                            T.tomo._ptg_ptr(np.ascontiguousarray(ptg)), None,
+                            C.c_void_p(out.data_ptr()), None) == ARG
     bad = dict(g, dy=-0.1)
     assert _status(T, T.tomo_project, cube, bad, ptg, 16, 16) == ARG
     p = ptg.copy()
