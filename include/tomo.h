@@ -217,6 +217,55 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                 const uint8_t *mask_dev, int64_t *count_host,
                                 void *stream);
 
+/* ---------------------------------------------------------------------
+ * Forward projection without any device allocation.
+ *
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot let a library allocate device memory.  tomo_project keeps its
+ * ray records and per-image tables in workspace that the context allocates
+ * with cudaMalloc on first use; some programs cannot accept that: programs
+ * that reserve the device memory they may use up front and hand out pieces
+ * of it themselves (a framework's caching allocator, a fixed memory budget
+ * shared with other jobs), and latency-critical loops in which a cudaMalloc
+ * or cudaFree, which can wait for work already queued on the device, would
+ * stall other streams.  tomo_project_noalloc computes the same projection
+ * (same kernels, same results) with its scratch in a fixed array that is
+ * part of the library image.
+ *
+ * Scratch: one array of TOMO_NOALLOC_SCRATCH_BYTES per device, compiled into
+ * the library and therefore held by every device on which this entry point
+ * has been called, until the process exits.  A call needs, each part
+ * rounded up to 256 bytes,
+ *     96 n_img + 96 n_img + 16 n_img + 8 n_img nu + 8 n_img nv
+ *     + 32 n_img nu nv   bytes
+ * (pointing copy, observer frames, image parameters, tangent tables, one
+ * 32-byte ray record per pixel); a call that needs more returns
+ * TOMO_ERR_UNSUPPORTED before launching anything.
+ *
+ * Every call uses the same array and leaves its contents behind; each call
+ * rewrites all of the scratch it reads, so nothing has to start at zero.
+ * Calls whose work overlaps on the GPU (other streams, or other host
+ * threads) race on the array: order them on one stream, or wait for one to
+ * finish before the next starts.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and remembers it; make
+ * that first call before any stream capture.
+ *
+ * Arguments are those of tomo_project without the context: the current
+ * device is used, the stream is a cudaStream_t passed as void* (NULL = the
+ * legacy default stream), and the call is asynchronous on it.  The
+ * pointing table is copied during the call.  No cudaMalloc, cudaFree or
+ * other allocating routine is called. */
+#define TOMO_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+tomo_status tomo_project_noalloc(const tomo_cube_geom *cube, int32_t n_frames,
+                                 const void *cube_dev, tomo_dtype dtype,
+                                 const tomo_image_geom *img,
+                                 const tomo_pointing *pointing_host,
+                                 const uint8_t *mask_dev, float *images_dev,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

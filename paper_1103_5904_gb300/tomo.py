@@ -94,6 +94,9 @@ _SIGNATURES = {
                                       C.POINTER(ImageGeom),
                                       C.POINTER(Pointing), _VP,
                                       C.POINTER(C.c_int64), _VP]),
+    "tomo_project_noalloc": (C.c_int, [C.POINTER(CubeGeom), C.c_int32, _VP,
+                                       C.c_int, C.POINTER(ImageGeom),
+                                       C.POINTER(Pointing), _VP, _VP, _VP]),
 }
 
 
