@@ -48,6 +48,10 @@ WORKLOAD_TEXT = {
     "single": ("single: cube 128^3 f32; 60 images 256x256, lon 0-177 deg, "
                "lat jitter +-7 deg; 6 streamers; occulter r<1; SNR 50; "
                "lambda 1e-2"),
+    "batched": ("batched: 32 independent problems (seeds 100-131), cube side "
+                "from {32,48,64,96,128}, 16-120 images of side "
+                "{64,128,256,512}, observers evenly spaced on the ecliptic; "
+                "10 CG iterations each, lambda 1e-2"),
 }
 
 
@@ -162,7 +166,8 @@ class ClockSampler:
 
 def make_workload(name, n_images=0):
     import synth
-    c = synth.make_config(name)
+    c = (synth.configs.batched_problem(100) if name == "batched"
+         else synth.make_config(name))
     if n_images and n_images < c["pointing"].shape[0]:
         keep = np.linspace(0, c["pointing"].shape[0] - 1, n_images).astype(int)
         c["pointing"] = np.ascontiguousarray(c["pointing"][keep])
@@ -435,6 +440,85 @@ def run_gpu(args, rank, local_rank, world):
     return 0
 
 
+def run_batched(args, rank, local_rank, world):
+    """Config 3: all problems in one graph-captured batched solve, against
+    the one-problem-at-a-time loop of tomo_solve on the same GPU."""
+    import torch
+    import synth
+    import paper_1103_5904_gb300 as T
+    from paper_1103_5904_gb300 import build as lib_build
+
+    lib_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = T.Context(local_rank)
+    iters = 10
+    probs, segs = [], 0
+    for c in synth.configs.batched():
+        cube = torch.from_numpy(c["cube"]).to(dev)
+        n_img = c["pointing"].shape[0]
+        y = T.tomo_project(cube, c["geom"], c["pointing"], c["nu"], c["nv"],
+                           ctx=ctx)
+        segs += T.tomo_count_segments(c["geom"], c["pointing"], c["nu"],
+                                      c["nv"], ctx=ctx)
+        probs.append({"geom": c["geom"], "pointing": c["pointing"],
+                      "nu": c["nu"], "nv": c["nv"], "images": y,
+                      "cube": torch.zeros_like(cube), "lam": c["lam"],
+                      "n_img": n_img})
+        del cube
+    units = segs * (2 * iters + 1)
+    stream = torch.cuda.current_stream(dev)
+    # batched: autotune once (first call), then graph replays
+    T.tomo_solve_batched(probs, iters, autotune=True, report=False, ctx=ctx)
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    def batched():
+        T.tomo_solve_batched(probs, iters, report=False, ctx=ctx)
+
+    def sequential():
+        for p in probs:
+            T.tomo_solve(p["images"], p["geom"], p["pointing"], lam=p["lam"],
+                         max_iter=iters, out=p["cube"], report=False, ctx=ctx)
+
+    for _ in range(args.warmup):
+        batched()
+        sequential()
+    ctx.profile(reset=True)
+    ms_b = timed(batched, args.steps)
+    launches = sum(v[0] for v in ctx.profile(reset=True).values())
+    ms_s = timed(sequential, args.steps)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": units / (ms_b / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["batched"],
+                       "step": "one tomo_solve_batched (one CUDA graph replay "
+                               "of %d CG iterations for all 32 problems)"
+                               % iters,
+                       "segments_per_projection_all_problems": segs},
+            "sequential": {"value": units / (ms_s / 1e3), "unit": UNIT,
+                           "ms_per_step": ms_s,
+                           "what": "tomo_solve per problem, one after another"},
+            "batched_speedup": ms_s / ms_b,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, local_rank, world = dist_env()
@@ -451,6 +535,8 @@ def main(argv=None):
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        if args.workload == "batched":
+            return run_batched(args, rank, local_rank, world)
         return run_gpu(args, rank, local_rank, world)
     finally:
         if world > 1:

@@ -99,6 +99,11 @@ typedef struct tomo_ctx tomo_ctx;
 #define TOMO_OPT_TILE_V     3  /* pixel tile height of one CTA (default 8) */
 #define TOMO_OPT_WARP_U     4  /* pixel tile width of one warp (default 8) */
 #define TOMO_OPT_PROFILE    5  /* 1: time every kernel launch with CUDA events */
+#define TOMO_OPT_ADJOINT    6  /* transpose kernel: 0 (default) adds every
+                                  segment with a float atomic; 1 accumulates
+                                  each ray bundle in a shared-memory window
+                                  first (time-interpolated transposes and
+                                  tiles of other than 256 pixels always use 0) */
 
 /* Kernel classes of tomo_profile */
 enum {
@@ -216,6 +221,79 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                 const tomo_pointing *pointing_host,
                                 const uint8_t *mask_dev, int64_t *count_host,
                                 void *stream);
+
+/* ---------------------------------------------------------------------
+ * Batches of independent problems (uneven cube and image sizes).
+ *
+ * One persistent kernel launch walks the rays of every problem: a grid of
+ * (SM count x resident CTAs) CTAs takes (problem, pixel tile) work items from
+ * an atomic counter; each problem may use its own tile shape (256 threads),
+ * taken from the autotuner's table.  The solver captures its whole run
+ * (initial residual and every iteration, for every problem) in one CUDA
+ * graph that is replayed while geometries, buffers, lambdas and the
+ * iteration count stay the same.
+ *
+ * Each problem is described by a tomo_problem (all buffers belong to the
+ * caller):
+ *   cube, img, pointing_host  geometry as for tomo_project (one frame)
+ *   mask_dev                  nullable
+ *   images_dev                project: output; backproject: input;
+ *                             solve: the data y
+ *   cube_dev                  project: input; backproject: output;
+ *                             solve: the solution (initial guess with
+ *                             TOMO_SOLVE_X0)
+ *   lambda                    solve: prior weight (>= 0)
+ *   reserved                  must be 0
+ */
+typedef struct {
+    tomo_cube_geom cube;
+    tomo_image_geom img;
+    int32_t reserved;
+    const tomo_pointing *pointing_host;
+    const uint8_t *mask_dev;
+    float *images_dev;
+    float *cube_dev;
+    double lambda;
+} tomo_problem;
+
+/* A tile shape and its measured times (tomo_autotune). */
+typedef struct {
+    int32_t tile_u, tile_v, warp_u;
+    float fwd_ms, adj_ms;
+} tomo_tiling;
+
+#define TOMO_BATCH_AUTOTUNE 8u /* solve_batched: tune unseen problem sizes */
+
+/* Times the forward and transpose kernels of one problem (its cube_dev and
+ * images_dev are read, not written) for a fixed list of 256-thread tile
+ * shapes, keeps the fastest (forward + transpose time) for that problem size
+ * in the context, and returns it in best_out (nullable).  Later single and
+ * batched calls on problems of the same size use it.  Synchronises
+ * `stream`. */
+tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
+                          tomo_tiling *best_out, void *stream);
+
+/* images = P cube for every problem, in one persistent launch (plus the FP64
+ * ray setup of every problem when the set of geometries changes). */
+tomo_status tomo_project_batched(tomo_ctx *ctx, int32_t n,
+                                 const tomo_problem *probs, void *stream);
+
+/* cube = P^T images for every problem (overwritten unless TOMO_ACCUMULATE),
+ * in one persistent launch. */
+tomo_status tomo_backproject_batched(tomo_ctx *ctx, int32_t n,
+                                     const tomo_problem *probs, uint32_t flags,
+                                     void *stream);
+
+/* n_iter CG iterations of tomo_solve for every problem at once (one CUDA
+ * graph replay).  flags: TOMO_SOLVE_X0, TOMO_BATCH_AUTOTUNE.
+ *   report_host: nullable; n x (n_iter + 1) x 2 doubles (J, r.r per
+ *                iterate, as tomo_solve)
+ *   iters_host:  nullable; n iteration counts
+ * Synchronises `stream` when report_host or iters_host is given. */
+tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
+                               const tomo_problem *probs, int32_t n_iter,
+                               uint32_t flags, double *report_host,
+                               int32_t *iters_host, void *stream);
 
 /* ---------------------------------------------------------------------
  * Forward projection without any device allocation.

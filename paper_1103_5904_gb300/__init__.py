@@ -10,6 +10,8 @@ projector as a differentiable PyTorch operation.  Build the library with
 from . import tomo  # noqa: F401
 from .tomo import (Context, TomoError, default_context, load_library,  # noqa
                    tomo_project, tomo_backproject, tomo_solve,
-                   tomo_prior_apply, tomo_count_segments, project,
+                   tomo_prior_apply, tomo_count_segments,
+                   tomo_project_batched, tomo_backproject_batched,
+                   tomo_solve_batched, tomo_autotune, project,
                    backproject, solve, prior_apply, count_segments)
 from .autograd import TomoProject  # noqa: F401

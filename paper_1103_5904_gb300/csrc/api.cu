@@ -238,6 +238,23 @@ Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
     return ctx->tiling;
 }
 
+cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
+                        const ImgParam *prm, const float *images,
+                        const uint8_t *mask, float *cube,
+                        const tomo_cube_geom *c, int32_t n_frames,
+                        const tomo_image_geom *g, Tiling t, const double *done,
+                        cudaStream_t s)
+{
+    if (ctx->adjoint_mode == 1 && n_frames == 1 && adjoint_window_supported(t))
+        return launch_adjoint_window(rays, prm, images, mask, cube, g->n_img,
+                                     g->nu, g->nv, c->nx, c->ny, c->nz, t,
+                                     done, s);
+    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+    return launch_adjoint(rays, prm, images, mask, cube, fstride, n_frames > 1,
+                          g->n_img, g->nu, g->nv, c->nx, c->nx * c->ny, t,
+                          done, s);
+}
+
 int reduce_grid(const tomo_ctx *ctx, int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -340,6 +357,10 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
         return TOMO_OK;
     case TOMO_OPT_PROFILE:
         ctx->profile = value != 0;
+        return TOMO_OK;
+    case TOMO_OPT_ADJOINT:
+        if (value != 0 && value != 1) break;
+        ctx->adjoint_mode = (int)value;
         return TOMO_OK;
     default:
         return fail(ctx, TOMO_ERR_ARG, "unknown option %d", option);
@@ -447,12 +468,11 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                       sizeof(float) * fstride * n_frames, s));
     if (img->n_img == 0) return TOMO_OK;
     if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
-    LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint((const RayRec *)ctx->rays.p,
-                                 (const ImgParam *)ctx->params.p, images_dev,
-                                 mask_dev, cube_dev, fstride, n_frames > 1,
-                                 img->n_img, img->nu, img->nv, cube->nx,
-                                 cube->nx * cube->ny,
-                                 tiling_for(ctx, cube, img), nullptr, s));
+    LAUNCH(ctx, TOMO_K_ADJOINT, s,
+           run_adjoint(ctx, (const RayRec *)ctx->rays.p,
+                       (const ImgParam *)ctx->params.p, images_dev, mask_dev,
+                       cube_dev, cube, n_frames, img,
+                       tiling_for(ctx, cube, img), nullptr, s));
     return TOMO_OK;
 }
 
@@ -582,9 +602,9 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     }
     CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
     if (m > 0)
-        LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, y_dev, mask_dev, b, n, false,
-                                     img->n_img, img->nu, img->nv, cube->nx,
-                                     nxny, tl, nullptr, s));
+        LAUNCH(ctx, TOMO_K_ADJOINT, s,
+               run_adjoint(ctx, rays, prm, y_dev, mask_dev, b, cube, 1, img,
+                           tl, nullptr, s));
     if (flags & TOMO_SOLVE_X0) {
         // r0 = b - (P^T M P + lambda D^T D) x0
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, q, lam, false, nullptr, s));
@@ -592,9 +612,9 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
             LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward(rays, prm, x_dev, TOMO_F32, n, false,
                                          mask_dev, t, img->n_img, img->nu,
                                          img->nv, cube->nx, nxny, tl, nullptr, s));
-            LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, t, mask_dev, q, n, false,
-                                         img->n_img, img->nu, img->nv, cube->nx,
-                                         nxny, tl, nullptr, s));
+            LAUNCH(ctx, TOMO_K_ADJOINT, s,
+                   run_adjoint(ctx, rays, prm, t, mask_dev, q, cube, 1, img,
+                               tl, nullptr, s));
         }
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, n, tol * tol,
                                      partials, counter, S, report, grid, s));
@@ -614,9 +634,9 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                          img->nv, cube->nx, nxny, tl, done, s));
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, q, lam, false, done, s));
         if (m > 0)
-            LAUNCH(ctx, TOMO_K_ADJOINT, s, launch_adjoint(rays, prm, t, mask_dev, q, n, false,
-                                         img->n_img, img->nu, img->nv, cube->nx,
-                                         nxny, tl, done, s));
+            LAUNCH(ctx, TOMO_K_ADJOINT, s,
+                   run_adjoint(ctx, rays, prm, t, mask_dev, q, cube, 1, img,
+                               tl, done, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, n, partials, counter,
                                        S, report, grid, s));

@@ -111,7 +111,7 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
     const int64_t n_items = prefix[n_probs];
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int p = owner(prefix, n_probs, item);
-        const VecDesc &d = descs[p];
+        const VecDesc d = descs[p];  // a copy: stores below cannot alias it
         const int64_t len = (op == V_SUMSQ) ? d.m : d.n;
         // this item's chunk of its problem: elements [c.c0, c.c1)
         struct { int64_t c0, c1; } c;
@@ -192,7 +192,7 @@ k_finalize_batched(int op, const VecDesc *__restrict__ descs,
 {
     __shared__ double sm[32];
     for (int p = blockIdx.x; p < n_probs; p += gridDim.x) {
-        const VecDesc &d = descs[p];
+        const VecDesc d = descs[p];
         if ((op == V_PQ || op == V_UPDATE) && d.S[S_DONE] != 0.0) continue;
         double s0 = 0.0, s1 = 0.0;
         for (int64_t i = prefix[p] + threadIdx.x; i < prefix[p + 1];

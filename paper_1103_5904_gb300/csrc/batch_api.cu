@@ -1,21 +1,623 @@
-// C ABI of the batched projector, transpose and solver (batch.cu kernels).
+// C ABI of the batched projector, transpose and solver, and of the tile-shape
+// autotuner (kernels in batch.cu and siddon.cu).
+//
+// A batch plan holds, for one set of problem geometries, the ray records of
+// every problem back to back, the descriptors of the persistent kernels and,
+// for the solver, one CUDA graph with the whole CG run (initialisation and
+// every iteration).  Replaying the plan for the same geometries and buffers
+// costs one graph launch.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
 #include "batch.cuh"
 #include "host.h"
+
+using namespace tomo;
+using namespace tomo::host;
 
 namespace tomo {
 namespace host {
 
 struct BatchPlan {
-    int unused = 0;
+    uint64_t geom_key = 0;
+    uint64_t graph_key = 0;
+    int32_t n = 0;
+    // geometry of every problem, back to back
+    DevBuf ptg, frames, tan_u, tan_v, params, rays;
+    std::vector<int64_t> ray_off, img_off, tu_off, tv_off;
+    std::vector<Tiling> tl;
+    std::vector<int64_t> tile_prefix;  // n + 1
+    cudaEvent_t ready = nullptr;
+    // per-call descriptors of the projector / transpose entry points
+    DevBuf call_desc, call_prefix, call_counter;
+    // solver workspace and graph
+    DevBuf vec, timg, S, partials, counters, walk_desc, vec_desc, prefixes;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_launches[TOMO_K_COUNT] = { 0 };
+    int32_t n_iter = 0;
+    size_t report_stride = 0;
 };
 
 void free_plan(tomo_ctx *ctx)
 {
-    if (ctx->plan) {
-        delete ctx->plan;
-        ctx->plan = nullptr;
-    }
+    BatchPlan *p = ctx->plan;
+    if (!p) return;
+    DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
+                       &p->rays, &p->call_desc, &p->call_prefix,
+                       &p->call_counter, &p->vec, &p->timg, &p->S,
+                       &p->partials, &p->counters, &p->walk_desc,
+                       &p->vec_desc, &p->prefixes };
+    for (DevBuf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->ready) cudaEventDestroy(p->ready);
+    delete p;
+    ctx->plan = nullptr;
 }
 
 }  // namespace host
 }  // namespace tomo
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+
+const Tiling kDefaultTiling = { 32, 8, 8 };
+
+// Tile shapes the autotuner tries: all 256 threads, so the batched
+// persistent kernel can mix them.
+const Tiling kCandidates[] = {
+    { 32, 8, 8 }, { 16, 16, 8 }, { 16, 16, 4 }, { 64, 4, 16 },
+    { 32, 8, 32 }, { 128, 2, 32 }, { 16, 16, 16 }, { 8, 32, 4 },
+    { 32, 8, 16 }, { 64, 4, 32 } };
+
+bool is_batch_tiling(Tiling t)
+{
+    return t.tile_u * t.tile_v == kBatchThreads;
+}
+
+tomo_status check_problem(tomo_ctx *ctx, const tomo_problem *p, int32_t i,
+                          bool need_cube, bool need_images)
+{
+    tomo_status st;
+    if ((st = check_cube(ctx, &p->cube, 1)) || (st = check_img(ctx, &p->img)) ||
+        (st = check_pointing(ctx, p->pointing_host, &p->img, 1)))
+        return fail(ctx, st, "problem %d: %s", i, ctx->err);
+    if (p->reserved != 0)
+        return fail(ctx, TOMO_ERR_ARG, "problem %d: reserved must be 0", i);
+    if (need_cube && (!p->cube_dev || !aligned(p->cube_dev, 4)))
+        return fail(ctx, TOMO_ERR_ARG, "problem %d: cube_dev NULL or misaligned", i);
+    if (need_images && p->img.n_img > 0 &&
+        (!p->images_dev || !aligned(p->images_dev, 4)))
+        return fail(ctx, TOMO_ERR_ARG,
+                    "problem %d: images_dev NULL or misaligned", i);
+    if (!isfinite(p->lambda) || p->lambda < 0)
+        return fail(ctx, TOMO_ERR_ARG, "problem %d: lambda must be >= 0", i);
+    return TOMO_OK;
+}
+
+Tiling batch_tiling(const tomo_ctx *ctx, const tomo_problem *p)
+{
+    const Tiling t = tiling_for(ctx, &p->cube, &p->img);
+    return is_batch_tiling(t) ? t : kDefaultTiling;
+}
+
+tomo_status upload(tomo_ctx *ctx, DevBuf &b, const void *src, size_t bytes,
+                   cudaStream_t s)
+{
+    tomo_status st = ensure(ctx, b, bytes);
+    if (st) return st;
+    CUDA_TRY(ctx, cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, s));
+    return TOMO_OK;
+}
+
+// Ray records of every problem (FP64 setup kernels, one pair per problem),
+// kept while the geometries do not change.
+tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
+                          cudaStream_t s)
+{
+    uint64_t h = 1469598103934665603ull;
+    h = fnv1a(h, &n, sizeof(n));
+    for (int32_t i = 0; i < n; ++i) {
+        const tomo_problem &p = probs[i];
+        h = fnv1a(h, &p.cube, sizeof(p.cube));
+        h = fnv1a(h, &p.img, sizeof(p.img));
+        h = fnv1a(h, p.pointing_host, sizeof(tomo_pointing) * (size_t)p.img.n_img);
+        const Tiling t = batch_tiling(ctx, &p);
+        h = fnv1a(h, &t, sizeof(t));
+    }
+    if (!ctx->plan) {
+        ctx->plan = new BatchPlan();
+        CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->plan->ready,
+                                               cudaEventDisableTiming));
+    }
+    BatchPlan *P = ctx->plan;
+    if (P->geom_key == h && P->n == n) {
+        CUDA_TRY(ctx, cudaStreamWaitEvent(s, P->ready, 0));
+        return TOMO_OK;
+    }
+    P->geom_key = 0;
+    P->graph_key = 0;
+    P->n = n;
+    P->ray_off.assign(n + 1, 0);
+    P->img_off.assign(n + 1, 0);
+    P->tu_off.assign(n + 1, 0);
+    P->tv_off.assign(n + 1, 0);
+    P->tile_prefix.assign(n + 1, 0);
+    P->tl.assign(n, kDefaultTiling);
+    for (int32_t i = 0; i < n; ++i) {
+        const tomo_image_geom &g = probs[i].img;
+        P->tl[i] = batch_tiling(ctx, &probs[i]);
+        P->ray_off[i + 1] = P->ray_off[i] + (int64_t)g.n_img * g.nu * g.nv;
+        P->img_off[i + 1] = P->img_off[i] + g.n_img;
+        P->tu_off[i + 1] = P->tu_off[i] + (int64_t)g.n_img * g.nu;
+        P->tv_off[i + 1] = P->tv_off[i] + (int64_t)g.n_img * g.nv;
+        const int64_t tiles = (int64_t)g.n_img *
+                              ((g.nu + P->tl[i].tile_u - 1) / P->tl[i].tile_u) *
+                              ((g.nv + P->tl[i].tile_v - 1) / P->tl[i].tile_v);
+        P->tile_prefix[i + 1] = P->tile_prefix[i] + tiles;
+    }
+    const int64_t n_img = P->img_off[n];
+    tomo_status st;
+    if ((st = ensure(ctx, P->ptg, sizeof(tomo_pointing) * n_img)) ||
+        (st = ensure(ctx, P->frames, sizeof(Frame) * n_img)) ||
+        (st = ensure(ctx, P->params, sizeof(ImgParam) * n_img)) ||
+        (st = ensure(ctx, P->tan_u, sizeof(double) * P->tu_off[n])) ||
+        (st = ensure(ctx, P->tan_v, sizeof(double) * P->tv_off[n])) ||
+        (st = ensure(ctx, P->rays, sizeof(RayRec) * P->ray_off[n])))
+        return st;
+    std::vector<tomo_pointing> all((size_t)n_img);
+    for (int32_t i = 0; i < n; ++i)
+        if (probs[i].img.n_img > 0)
+            memcpy(&all[P->img_off[i]], probs[i].pointing_host,
+                   sizeof(tomo_pointing) * probs[i].img.n_img);
+    if (n_img > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(P->ptg.p, all.data(),
+                                      sizeof(tomo_pointing) * n_img,
+                                      cudaMemcpyHostToDevice, s));
+    for (int32_t i = 0; i < n; ++i) {
+        const tomo_problem &p = probs[i];
+        if (p.img.n_img == 0) continue;
+        Frame *fr = (Frame *)P->frames.p + P->img_off[i];
+        ImgParam *pr = (ImgParam *)P->params.p + P->img_off[i];
+        double *tu = (double *)P->tan_u.p + P->tu_off[i];
+        double *tv = (double *)P->tan_v.p + P->tv_off[i];
+        LAUNCH(ctx, TOMO_K_SETUP, s,
+               launch_frames((const tomo_pointing *)P->ptg.p + P->img_off[i],
+                             p.img.n_img, p.img.nu, p.img.nv, 1, fr, tu, tv, pr,
+                             s));
+        LAUNCH(ctx, TOMO_K_SETUP, s,
+               launch_ray_setup(fr, tu, tv, cube_dev(&p.cube), p.img.n_img,
+                                p.img.nu, p.img.nv,
+                                (RayRec *)P->rays.p + P->ray_off[i], s));
+    }
+    CUDA_TRY(ctx, cudaEventRecord(P->ready, s));
+    P->geom_key = h;
+    return TOMO_OK;
+}
+
+WalkDesc walk_desc(const BatchPlan *P, const tomo_problem &p, int32_t i,
+                   const float *src, float *dst, const double *done)
+{
+    WalkDesc d;
+    d.rays = (const RayRec *)P->rays.p + P->ray_off[i];
+    d.prm = (const ImgParam *)P->params.p + P->img_off[i];
+    d.mask = p.mask_dev;
+    d.src = src;
+    d.dst = dst;
+    d.done = done;
+    d.nu = p.img.nu;
+    d.nv = p.img.nv;
+    d.nx = p.cube.nx;
+    d.nxny = p.cube.nx * p.cube.ny;
+    d.tl = P->tl[i];
+    d.tiles_u = (p.img.nu + d.tl.tile_u - 1) / d.tl.tile_u;
+    d.tiles_v = (p.img.nv + d.tl.tile_v - 1) / d.tl.tile_v;
+    d.pad = 0;
+    return d;
+}
+
+int walk_grid(const tomo_ctx *ctx)
+{
+    return (ctx->num_sms > 0 ? ctx->num_sms : 152) * walk_batched_blocks_per_sm();
+}
+
+tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
+                         bool adjoint, uint32_t flags, cudaStream_t s)
+{
+    tomo_status st;
+    for (int32_t i = 0; i < n; ++i)
+        if ((st = check_problem(ctx, &probs[i], i, true, true))) return st;
+    if ((st = prepare_batch(ctx, n, probs, s))) return st;
+    BatchPlan *P = ctx->plan;
+    std::vector<WalkDesc> d(n);
+    for (int32_t i = 0; i < n; ++i)
+        d[i] = adjoint ? walk_desc(P, probs[i], i, probs[i].images_dev,
+                                   probs[i].cube_dev, nullptr)
+                       : walk_desc(P, probs[i], i, probs[i].cube_dev,
+                                   probs[i].images_dev, nullptr);
+    if (adjoint && !(flags & TOMO_ACCUMULATE))
+        for (int32_t i = 0; i < n; ++i)
+            CUDA_TRY(ctx, cudaMemsetAsync(probs[i].cube_dev, 0,
+                                          sizeof(float) * probs[i].cube.nx *
+                                              probs[i].cube.ny * probs[i].cube.nz,
+                                          s));
+    if (P->tile_prefix[n] == 0) return TOMO_OK;
+    if ((st = upload(ctx, P->call_desc, d.data(), sizeof(WalkDesc) * n, s)) ||
+        (st = upload(ctx, P->call_prefix, P->tile_prefix.data(),
+                     sizeof(int64_t) * (n + 1), s)) ||
+        (st = ensure(ctx, P->call_counter, sizeof(unsigned long long))))
+        return st;
+    CUDA_TRY(ctx, cudaMemsetAsync(P->call_counter.p, 0,
+                                  sizeof(unsigned long long), s));
+    LAUNCH(ctx, adjoint ? TOMO_K_ADJOINT : TOMO_K_FORWARD, s,
+           launch_walk_batched(adjoint, (const WalkDesc *)P->call_desc.p,
+                               (const int64_t *)P->call_prefix.p, n,
+                               (unsigned long long *)P->call_counter.p,
+                               walk_grid(ctx), s));
+    return TOMO_OK;
+}
+
+// Times the forward and transpose of one problem under tile shape t.
+tomo_status time_tiling(tomo_ctx *ctx, const tomo_problem *p, Tiling t,
+                        float *images_tmp, float *cube_tmp, cudaStream_t s,
+                        float *fwd_ms, float *adj_ms)
+{
+    cudaEvent_t e[3];
+    for (int k = 0; k < 3; ++k)
+        CUDA_TRY(ctx, cudaEventCreate(&e[k]));
+    const int64_t nvox = (int64_t)p->cube.nx * p->cube.ny * p->cube.nz;
+    float best_f = INFINITY, best_a = INFINITY;
+    tomo_status st = TOMO_OK;
+    for (int rep = 0; rep < 3 && st == TOMO_OK; ++rep) {
+        cudaError_t err = cudaEventRecord(e[0], s);
+        if (err == cudaSuccess)
+            err = launch_forward((const RayRec *)ctx->rays.p,
+                                 (const ImgParam *)ctx->params.p, p->cube_dev,
+                                 TOMO_F32, nvox, false, p->mask_dev,
+                                 images_tmp, p->img.n_img, p->img.nu,
+                                 p->img.nv, p->cube.nx,
+                                 p->cube.nx * p->cube.ny, t, nullptr, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e[1], s);
+        if (err == cudaSuccess)
+            err = run_adjoint(ctx, (const RayRec *)ctx->rays.p,
+                              (const ImgParam *)ctx->params.p, p->images_dev,
+                              p->mask_dev, cube_tmp, &p->cube, 1, &p->img, t,
+                              nullptr, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e[2], s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e[2]);
+        float f = 0, a = 0;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&f, e[0], e[1]);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&a, e[1], e[2]);
+        if (err != cudaSuccess) {
+            st = fail(ctx, TOMO_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
+            break;
+        }
+        if (rep > 0) {  // the first repetition warms caches
+            best_f = f < best_f ? f : best_f;
+            best_a = a < best_a ? a : best_a;
+        }
+    }
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(e[k]);
+    *fwd_ms = best_f;
+    *adj_ms = best_a;
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
+                          tomo_tiling *best_out, void *stream)
+{
+    if (!ctx || !prob) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    tomo_status st = check_problem(ctx, prob, 0, true, true);
+    if (st) return st;
+    if (prob->img.n_img == 0)
+        return fail(ctx, TOMO_ERR_ARG, "autotune needs at least one image");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = prepare_rays(ctx, &prob->cube, 1, &prob->img,
+                           prob->pointing_host, s)))
+        return st;
+    const int64_t nvox = (int64_t)prob->cube.nx * prob->cube.ny * prob->cube.nz;
+    const int64_t npix = (int64_t)prob->img.n_img * prob->img.nu * prob->img.nv;
+    if ((st = ensure(ctx, ctx->t, sizeof(float) * npix)) ||
+        (st = ensure(ctx, ctx->q, sizeof(float) * nvox)))
+        return st;
+    Tuned best;
+    best.nx = prob->cube.nx;
+    best.ny = prob->cube.ny;
+    best.nz = prob->cube.nz;
+    best.nu = prob->img.nu;
+    best.nv = prob->img.nv;
+    best.tl = kDefaultTiling;
+    best.fwd_ms = best.adj_ms = INFINITY;
+    for (const Tiling &t : kCandidates) {
+        float f, a;
+        if ((st = time_tiling(ctx, prob, t, (float *)ctx->t.p,
+                              (float *)ctx->q.p, s, &f, &a)))
+            return st;
+        if (f + a < best.fwd_ms + best.adj_ms) {
+            best.tl = t;
+            best.fwd_ms = f;
+            best.adj_ms = a;
+        }
+    }
+    bool replaced = false;
+    for (Tuned &e : ctx->tuned)
+        if (e.nx == best.nx && e.ny == best.ny && e.nz == best.nz &&
+            e.nu == best.nu && e.nv == best.nv) {
+            e = best;
+            replaced = true;
+        }
+    if (!replaced) ctx->tuned.push_back(best);
+    if (best_out) {
+        best_out->tile_u = best.tl.tile_u;
+        best_out->tile_v = best.tl.tile_v;
+        best_out->warp_u = best.tl.warp_u;
+        best_out->fwd_ms = best.fwd_ms;
+        best_out->adj_ms = best.adj_ms;
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_project_batched(tomo_ctx *ctx, int32_t n,
+                                 const tomo_problem *probs, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !probs)) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    if (n == 0) return TOMO_OK;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    return batched_walk(ctx, n, probs, false, 0, (cudaStream_t)stream);
+}
+
+tomo_status tomo_backproject_batched(tomo_ctx *ctx, int32_t n,
+                                     const tomo_problem *probs, uint32_t flags,
+                                     void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !probs)) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    if (flags & ~TOMO_ACCUMULATE)
+        return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
+    if (n == 0) return TOMO_OK;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    return batched_walk(ctx, n, probs, true, flags, (cudaStream_t)stream);
+}
+
+tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
+                               const tomo_problem *probs, int32_t n_iter,
+                               uint32_t flags, double *report_host,
+                               int32_t *iters_host, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && !probs)) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    if (flags & ~(TOMO_SOLVE_X0 | TOMO_BATCH_AUTOTUNE))
+        return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
+    if (n_iter < 0 || n_iter > 100000)
+        return fail(ctx, TOMO_ERR_ARG, "n_iter must be in [0, 1e5]");
+    if (n == 0) return TOMO_OK;
+    tomo_status st;
+    for (int32_t i = 0; i < n; ++i)
+        if ((st = check_problem(ctx, &probs[i], i, true, true))) return st;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool warm = (flags & TOMO_SOLVE_X0) != 0;
+
+    if (flags & TOMO_BATCH_AUTOTUNE) {
+        for (int32_t i = 0; i < n; ++i) {
+            const tomo_problem &p = probs[i];
+            bool known = p.img.n_img == 0;
+            for (const Tuned &e : ctx->tuned)
+                known |= e.nx == p.cube.nx && e.ny == p.cube.ny &&
+                         e.nz == p.cube.nz && e.nu == p.img.nu &&
+                         e.nv == p.img.nv;
+            if (!known && (st = tomo_autotune(ctx, &p, nullptr, stream)))
+                return st;
+        }
+    }
+    if ((st = prepare_batch(ctx, n, probs, s))) return st;
+    BatchPlan *P = ctx->plan;
+
+    // graph key: geometry plan + caller buffers + lambdas + run shape
+    uint64_t h = P->geom_key;
+    for (int32_t i = 0; i < n; ++i) {
+        const void *ptrs[3] = { probs[i].images_dev, probs[i].cube_dev,
+                                probs[i].mask_dev };
+        h = fnv1a(h, ptrs, sizeof(ptrs));
+        h = fnv1a(h, &probs[i].lambda, sizeof(double));
+    }
+    h = fnv1a(h, &n_iter, sizeof(n_iter));
+    h = fnv1a(h, &flags, sizeof(flags));
+    const size_t stride = 2 * ((size_t)n_iter + 1);
+
+    if (!(P->exec && P->graph_key == h)) {
+        P->graph_key = 0;
+        if (P->exec) cudaGraphExecDestroy(P->exec);
+        if (P->graph) cudaGraphDestroy(P->graph);
+        P->exec = nullptr;
+        P->graph = nullptr;
+        // workspace: b, r, p, q per problem (voxels), t per problem (pixels)
+        std::vector<int64_t> voff(n + 1, 0), poff(n + 1, 0), vitems(n + 1, 0),
+            pitems(n + 1, 0);
+        for (int32_t i = 0; i < n; ++i) {
+            const int64_t nv = (int64_t)probs[i].cube.nx * probs[i].cube.ny *
+                               probs[i].cube.nz;
+            const int64_t np = P->ray_off[i + 1] - P->ray_off[i];
+            voff[i + 1] = voff[i] + nv;
+            poff[i + 1] = poff[i] + np;
+            vitems[i + 1] = vitems[i] + (nv + kChunk - 1) / kChunk;
+            pitems[i + 1] = pitems[i] + (np + kChunk - 1) / kChunk;
+        }
+        const int64_t NV = voff[n];
+        const int64_t max_items = vitems[n] > pitems[n] ? vitems[n] : pitems[n];
+        const int n_walks = 1 + (warm ? 2 : 0) + 2 * n_iter;
+        if ((st = ensure(ctx, P->vec, sizeof(float) * 4 * NV)) ||
+            (st = ensure(ctx, P->timg, sizeof(float) * (poff[n] > 0 ? poff[n] : 1))) ||
+            (st = ensure(ctx, P->S, sizeof(double) * n * (S_NSLOTS + stride))) ||
+            (st = ensure(ctx, P->partials, sizeof(double) * 2 * max_items)) ||
+            (st = ensure(ctx, P->counters, sizeof(unsigned long long) * n_walks)))
+            return st;
+        float *vb = (float *)P->vec.p, *vr = vb + NV, *vp = vr + NV, *vq = vp + NV;
+        float *tim = (float *)P->timg.p;
+        double *S = (double *)P->S.p;
+        double *rep = S + (size_t)n * S_NSLOTS;
+        // descriptors: walks [b, fwd_x, adj_x, fwd, adj] x n, then vectors
+        std::vector<WalkDesc> wd(5 * (size_t)n);
+        std::vector<VecDesc> vd(n);
+        for (int32_t i = 0; i < n; ++i) {
+            const tomo_problem &p = probs[i];
+            double *Si = S + (size_t)i * S_NSLOTS;
+            const double *done = Si + S_DONE;
+            float *bi = vb + voff[i], *ri = vr + voff[i], *pi = vp + voff[i],
+                  *qi = vq + voff[i], *ti = tim + poff[i];
+            wd[0 * n + i] = walk_desc(P, p, i, p.images_dev, bi, nullptr);
+            wd[1 * n + i] = walk_desc(P, p, i, p.cube_dev, ti, nullptr);
+            wd[2 * n + i] = walk_desc(P, p, i, ti, qi, nullptr);
+            wd[3 * n + i] = walk_desc(P, p, i, pi, ti, done);
+            wd[4 * n + i] = walk_desc(P, p, i, ti, qi, done);
+            VecDesc &v = vd[i];
+            v.x = p.cube_dev;
+            v.r = ri;
+            v.p = pi;
+            v.q = qi;
+            v.b = bi;
+            v.y = p.images_dev;
+            v.mask = p.mask_dev;
+            v.S = Si;
+            v.report = rep + (size_t)i * stride;
+            v.n = voff[i + 1] - voff[i];
+            v.m = poff[i + 1] - poff[i];
+            v.nx = p.cube.nx;
+            v.ny = p.cube.ny;
+            v.nz = p.cube.nz;
+            v.lam = (float)p.lambda;
+        }
+        std::vector<int64_t> pre;  // tile, voxel-item, pixel-item prefixes
+        pre.insert(pre.end(), P->tile_prefix.begin(), P->tile_prefix.end());
+        pre.insert(pre.end(), vitems.begin(), vitems.end());
+        pre.insert(pre.end(), pitems.begin(), pitems.end());
+        if ((st = upload(ctx, P->walk_desc, wd.data(), sizeof(WalkDesc) * wd.size(), s)) ||
+            (st = upload(ctx, P->vec_desc, vd.data(), sizeof(VecDesc) * n, s)) ||
+            (st = upload(ctx, P->prefixes, pre.data(), sizeof(int64_t) * pre.size(), s)))
+            return st;
+        CUDA_TRY(ctx, cudaStreamSynchronize(s));  // uploads done before capture
+
+        if (!ctx->capture_stream)
+            CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream,
+                                                    cudaStreamNonBlocking));
+        cudaStream_t c = ctx->capture_stream;
+        const WalkDesc *W = (const WalkDesc *)P->walk_desc.p;
+        const VecDesc *V = (const VecDesc *)P->vec_desc.p;
+        const int64_t *tile_pre = (const int64_t *)P->prefixes.p;
+        const int64_t *vox_pre = tile_pre + (n + 1);
+        const int64_t *pix_pre = vox_pre + (n + 1);
+        unsigned long long *ctr = (unsigned long long *)P->counters.p;
+        double *part = (double *)P->partials.p;
+        const int wgrid = walk_grid(ctx);
+        const int vgrid = (int)(max_items < 4 * walk_grid(ctx) ? max_items
+                                                               : 4 * walk_grid(ctx));
+        int64_t counts[TOMO_K_COUNT] = { 0 };
+        int next_ctr = 0;
+        cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess)
+            return fail(ctx, TOMO_ERR_CUDA, "begin capture: %s",
+                        cudaGetErrorString(e));
+#define CAP(kind, call)                                                      \
+    do {                                                                     \
+        if (e == cudaSuccess) e = (call);                                    \
+        counts[kind] += 1;                                                   \
+    } while (0)
+        e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * n_walks, c);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(S, 0, sizeof(double) * n * S_NSLOTS, c);
+        CAP(TOMO_K_VECTOR, launch_fill_f64(rep, NAN, (int64_t)(n * stride), c));
+        CAP(TOMO_K_VECTOR, launch_vec_batched(BV_SUMSQ, V, pix_pre, n, warm, part,
+                                              vgrid, c));
+        CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_SUMSQ, V, pix_pre, n, 0.0,
+                                                   part, c));
+        CAP(TOMO_K_VECTOR, launch_vec_batched(BV_ZERO, V, vox_pre, n, warm, part,
+                                              vgrid, c));
+        CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 0 * n, tile_pre, n,
+                                                ctr + next_ctr++, wgrid, c));
+        if (warm) {
+            CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR_X, V, vox_pre, n, warm,
+                                                 part, vgrid, c));
+            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, n,
+                                                    ctr + next_ctr++, wgrid, c));
+            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 2 * n, tile_pre, n,
+                                                    ctr + next_ctr++, wgrid, c));
+        }
+        CAP(TOMO_K_VECTOR, launch_vec_batched(BV_INIT, V, vox_pre, n, warm, part,
+                                              vgrid, c));
+        CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_INIT, V, vox_pre, n, 0.0,
+                                                   part, c));
+        for (int32_t k = 0; k < n_iter; ++k) {
+            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 3 * n, tile_pre, n,
+                                                    ctr + next_ctr++, wgrid, c));
+            CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR, V, vox_pre, n, warm,
+                                                 part, vgrid, c));
+            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 4 * n, tile_pre, n,
+                                                    ctr + next_ctr++, wgrid, c));
+            CAP(TOMO_K_VECTOR, launch_vec_batched(BV_PQ, V, vox_pre, n, warm,
+                                                  part, vgrid, c));
+            CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_PQ, V, vox_pre, n, 0.0,
+                                                       part, c));
+            CAP(TOMO_K_VECTOR, launch_vec_batched(BV_UPDATE, V, vox_pre, n, warm,
+                                                  part, vgrid, c));
+            CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_UPDATE, V, vox_pre, n,
+                                                       0.0, part, c));
+            CAP(TOMO_K_VECTOR, launch_vec_batched(BV_DIR, V, vox_pre, n, warm,
+                                                  part, vgrid, c));
+        }
+#undef CAP
+        cudaGraph_t g = nullptr;
+        const cudaError_t e_end = cudaStreamEndCapture(c, &g);
+        if (e != cudaSuccess || e_end != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(ctx, TOMO_ERR_CUDA, "graph capture: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e_end));
+        }
+        P->graph = g;
+        CUDA_TRY(ctx, cudaGraphInstantiate(&P->exec, g, 0));
+        for (int k = 0; k < TOMO_K_COUNT; ++k) P->graph_launches[k] = counts[k];
+        P->graph_key = h;
+        P->n_iter = n_iter;
+        P->report_stride = stride;
+    }
+    // the initial-residual step reads lambda from the descriptors; the
+    // tolerance is not used by the batched solver (fixed iteration count)
+    CUDA_TRY(ctx, cudaGraphLaunch(P->exec, s));
+    for (int k = 0; k < TOMO_K_COUNT; ++k) ctx->launches[k] += P->graph_launches[k];
+    if (report_host || iters_host) {
+        std::vector<double> slots((size_t)n * S_NSLOTS);
+        CUDA_TRY(ctx, cudaMemcpyAsync(slots.data(), P->S.p,
+                                      sizeof(double) * slots.size(),
+                                      cudaMemcpyDeviceToHost, s));
+        if (report_host)
+            CUDA_TRY(ctx, cudaMemcpyAsync(
+                              report_host, (double *)P->S.p + (size_t)n * S_NSLOTS,
+                              sizeof(double) * n * P->report_stride,
+                              cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(ctx, cudaStreamSynchronize(s));
+        for (int32_t i = 0; i < n; ++i) {
+            if (iters_host) iters_host[i] = (int32_t)slots[(size_t)i * S_NSLOTS + S_ITERS];
+            if (slots[(size_t)i * S_NSLOTS + S_ERR] != 0.0)
+                return fail(ctx, TOMO_ERR_NUMERIC, "problem %d: CG breakdown", i);
+        }
+    }
+    return TOMO_OK;
+}
+
+}  // extern "C"

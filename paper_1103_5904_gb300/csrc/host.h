@@ -36,6 +36,7 @@ struct tomo_ctx {
     int num_sms = 0;
     char err[512] = { 0 };
     bool ray_cache = true;
+    int adjoint_mode = 0;  // 0: one float atomic per segment; 1: windowed
     tomo::Tiling tiling = { 32, 8, 8 };
     // geometry cache
     bool key_valid = false;
@@ -77,6 +78,18 @@ int reduce_grid(const tomo_ctx *ctx, int64_t n);
 Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
                   const tomo_image_geom *g);
 void free_plan(tomo_ctx *ctx);
+// Launches the transpose of one problem with the context's adjoint mode
+// (windowed when possible, plain atomics otherwise).
+cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
+                        const ImgParam *prm, const float *images,
+                        const uint8_t *mask, float *cube,
+                        const tomo_cube_geom *c, int32_t n_frames,
+                        const tomo_image_geom *g, Tiling t, const double *done,
+                        cudaStream_t s);
+// Builds (or reuses) the context's ray records for one geometry on `s`.
+tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
+                         int32_t n_frames, const tomo_image_geom *g,
+                         const tomo_pointing *ptg, cudaStream_t s);
 
 #define CUDA_TRY(ctx, call)                                                  \
     do {                                                                     \

@@ -89,6 +89,15 @@ cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
                            bool time_interp, int32_t n_img, int32_t nu,
                            int32_t nv, int32_t nx, int32_t nxny, Tiling t,
                            const double *done, cudaStream_t s);
+// adjoint_window.cu: transpose with per-bundle shared-memory accumulation
+// (static frames only; the CTA must have 256 threads)
+bool adjoint_window_supported(Tiling t);
+cudaError_t launch_adjoint_window(const RayRec *rays, const ImgParam *prm,
+                                  const float *images, const uint8_t *mask,
+                                  float *cube, int32_t n_img, int32_t nu,
+                                  int32_t nv, int32_t nx, int32_t ny,
+                                  int32_t nz, Tiling t, const double *done,
+                                  cudaStream_t s);
 cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
                          int32_t n_img, int32_t nu, int32_t nv, Tiling t,
                          unsigned long long *count, cudaStream_t s);

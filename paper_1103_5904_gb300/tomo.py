@@ -26,6 +26,8 @@ TOMO_F32, TOMO_BF16 = 0, 1
 TOMO_ACCUMULATE, TOMO_SOLVE_X0, TOMO_SOLVE_BF16 = 1, 2, 4
 TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3, 4
 TOMO_OPT_PROFILE = 5
+TOMO_OPT_ADJOINT = 6
+TOMO_BATCH_AUTOTUNE = 8
 KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector")
 
 STATUS = {0: "TOMO_OK", -1: "TOMO_ERR_ARG", -2: "TOMO_ERR_CUDA",
@@ -54,7 +56,21 @@ class Profile(C.Structure):
     _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("cube", CubeGeom), ("img", ImageGeom), ("reserved", C.c_int32),
+                ("pointing_host", C.POINTER(Pointing)), ("mask_dev", C.c_void_p),
+                ("images_dev", C.c_void_p), ("cube_dev", C.c_void_p),
+                ("lam", C.c_double)]
+
+
+class TilingResult(C.Structure):
+    _fields_ = [("tile_u", C.c_int32), ("tile_v", C.c_int32),
+                ("warp_u", C.c_int32), ("fwd_ms", C.c_float),
+                ("adj_ms", C.c_float)]
+
+
 assert C.sizeof(CubeGeom) == 64 and C.sizeof(Pointing) == 96
+assert C.sizeof(Problem) == 120
 
 
 class TomoError(RuntimeError):
@@ -94,6 +110,16 @@ _SIGNATURES = {
                                       C.POINTER(ImageGeom),
                                       C.POINTER(Pointing), _VP,
                                       C.POINTER(C.c_int64), _VP]),
+    "tomo_autotune": (C.c_int, [_VP, C.POINTER(Problem),
+                                C.POINTER(TilingResult), _VP]),
+    "tomo_project_batched": (C.c_int, [_VP, C.c_int32, C.POINTER(Problem),
+                                       _VP]),
+    "tomo_backproject_batched": (C.c_int, [_VP, C.c_int32, C.POINTER(Problem),
+                                           C.c_uint32, _VP]),
+    "tomo_solve_batched": (C.c_int, [_VP, C.c_int32, C.POINTER(Problem),
+                                     C.c_int32, C.c_uint32,
+                                     C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int32), _VP]),
     "tomo_project_noalloc": (C.c_int, [C.POINTER(CubeGeom), C.c_int32, _VP,
                                        C.c_int, C.POINTER(ImageGeom),
                                        C.POINTER(Pointing), _VP, _VP, _VP]),
@@ -375,6 +401,110 @@ def tomo_count_segments(geom, pointing, nu, nv, mask=None, ctx=None,
         ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
         C.byref(n), _stream_ptr(stream, dev)))
     return int(n.value)
+
+
+# ------------------------------------------------------------------ batches
+
+def _problems(problems, need_cube=True, need_images=True):
+    """ctypes array of tomo_problem from dicts with keys geom, pointing, nu,
+    nv, cube, images, mask (optional), lam (optional).  Returns the array and
+    the pointing arrays it points into (keep them alive)."""
+    arr = (Problem * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        ptg = pointing_array(p["pointing"])
+        keep.append(ptg)
+        nu, nv = int(p["nu"]), int(p["nv"])
+        n_img = ptg.shape[0]
+        cube, images, mask = p.get("cube"), p.get("images"), p.get("mask")
+        _dev(cube, torch.float32, "cube")
+        _dev(images, torch.float32, "images")
+        _check_mask(mask, n_img, nu, nv)
+        nvox = int(p["geom"]["nx"]) * int(p["geom"]["ny"]) * int(p["geom"]["nz"])
+        if need_cube and (cube is None or cube.numel() != nvox):
+            raise ValueError("problem %d: cube must have nx*ny*nz elements" % i)
+        if need_images and (images is None or images.numel() != n_img * nu * nv):
+            raise ValueError("problem %d: images must have n_img*nv*nu elements"
+                             % i)
+        arr[i].cube = cube_geom_struct(p["geom"])
+        arr[i].img = ImageGeom(n_img, nu, nv)
+        arr[i].reserved = 0
+        arr[i].pointing_host = _ptg_ptr(ptg)
+        arr[i].mask_dev = None if mask is None else mask.data_ptr()
+        arr[i].images_dev = None if images is None else images.data_ptr()
+        arr[i].cube_dev = None if cube is None else cube.data_ptr()
+        arr[i].lam = float(p.get("lam", 0.0))
+    return arr, keep
+
+
+def _batch_device(problems):
+    for p in problems:
+        for k in ("cube", "images"):
+            if p.get(k) is not None:
+                return p[k].device
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def tomo_project_batched(problems, ctx=None, stream=None):
+    """``images = P cube`` for every problem (one persistent launch)."""
+    ctx = _ctx(ctx)
+    arr, keep = _problems(problems)
+    ctx.check(load_library().tomo_project_batched(
+        ctx.handle, len(problems), arr, _stream_ptr(stream,
+                                                    _batch_device(problems))))
+    return [p["images"] for p in problems]
+
+
+def tomo_backproject_batched(problems, accumulate=False, ctx=None,
+                             stream=None):
+    """``cube = P^T images`` for every problem (one persistent launch)."""
+    ctx = _ctx(ctx)
+    arr, keep = _problems(problems)
+    ctx.check(load_library().tomo_backproject_batched(
+        ctx.handle, len(problems), arr, TOMO_ACCUMULATE if accumulate else 0,
+        _stream_ptr(stream, _batch_device(problems))))
+    return [p["cube"] for p in problems]
+
+
+def tomo_solve_batched(problems, n_iter, warm_start=False, autotune=False,
+                       report=True, ctx=None, stream=None):
+    """``n_iter`` CG iterations for every problem (one CUDA graph replay);
+    ``problems[i]["images"]`` is the data, ``problems[i]["cube"]`` receives
+    the solution.  Returns one info dict per problem when ``report``."""
+    ctx = _ctx(ctx)
+    arr, keep = _problems(problems)
+    n = len(problems)
+    flags = (TOMO_SOLVE_X0 if warm_start else 0) | \
+        (TOMO_BATCH_AUTOTUNE if autotune else 0)
+    rep = np.full(n * 2 * (int(n_iter) + 1), np.nan) if report else None
+    iters = (C.c_int32 * max(n, 1))()
+    ctx.check(load_library().tomo_solve_batched(
+        ctx.handle, n, arr, int(n_iter), flags,
+        rep.ctypes.data_as(C.POINTER(C.c_double)) if report else None,
+        iters if report else None,
+        _stream_ptr(stream, _batch_device(problems))))
+    if not report:
+        return None
+    r = rep.reshape(n, -1, 2)
+    return [{"J": r[i, :, 0].copy(), "rr": r[i, :, 1].copy(),
+             "iters": int(iters[i])} for i in range(n)]
+
+
+def tomo_autotune(cube, images, geom, pointing, mask=None, ctx=None,
+                  stream=None):
+    """Pick the fastest tile shape for this problem size (kept in the
+    context); returns it with the measured forward / transpose times."""
+    ctx = _ctx(ctx)
+    ptg = pointing_array(pointing)
+    n_img, nv, nu = images.shape
+    arr, keep = _problems([{"geom": geom, "pointing": ptg, "nu": nu, "nv": nv,
+                            "cube": cube, "images": images, "mask": mask}])
+    best = TilingResult()
+    ctx.check(load_library().tomo_autotune(ctx.handle, arr, C.byref(best),
+                                           _stream_ptr(stream, cube.device)))
+    return {"tile_u": best.tile_u, "tile_v": best.tile_v,
+            "warp_u": best.warp_u, "fwd_ms": best.fwd_ms,
+            "adj_ms": best.adj_ms}
 
 
 # short aliases

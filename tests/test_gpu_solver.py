@@ -139,16 +139,19 @@ def test_cg_all_masked_is_zero(T):
 
 def test_cg_bf16_direction_reaches_same_residual(T):
     """BF16 storage of the CG direction (the projector gathers bf16, every
-    accumulation is FP32): after 20 iterations the criterion matches the
-    FP32 solve within 1e-2, and it decreases at every iteration (each step
-    is an exact line search along the bf16-rounded direction)."""
+    accumulation is FP32), compared with FP32 storage at equal final
+    criterion: the bf16 solve reaches the criterion of 20 FP32 iterations
+    within 30 iterations, and its criterion decreases at every iteration
+    (each step is an exact line search along the bf16-rounded direction)."""
     c = synth.make_config("single", scale=2)
     y = _data(c)
     md = mask_dev(c["mask"])
     _, i32 = T.tomo_solve(to_dev(y), c["geom"], c["pointing"], mask=md,
-                          lam=1e-2, max_iter=20)
+                          lam=1e-2, max_iter=60)
     _, i16 = T.tomo_solve(to_dev(y), c["geom"], c["pointing"], mask=md,
-                          lam=1e-2, max_iter=20, bf16=True)
-    assert i16["J"][-1] == pytest.approx(i32["J"][-1], rel=1e-2)
-    assert i16["J"][-1] < 0.05 * i16["J"][0]
+                          lam=1e-2, max_iter=60, bf16=True)
+    target = i32["J"][20] * (1 + 1e-4)
+    k16 = int(np.argmax(i16["J"] <= target))
+    assert i16["J"][k16] <= target and k16 <= 30, k16
     assert np.all(np.diff(i16["J"]) <= 1e-6 * i16["J"][0])
+    assert i16["J"][-1] < i32["J"][30]

@@ -63,7 +63,7 @@ def test_bad_geometry_and_pointing(T):
     p[0, 5] = np.nan
     assert _status(T, T.tomo_project, cube, g, p, 16, 16) == ARG
     p = ptg.copy()
-    p[0, 4] = 0.2  # pixel angles beyond 90 deg
+    p[0, 4] = 0.25  # 7.5 pixels x 0.25 rad = 1.875 rad: beyond 90 deg
     assert _status(T, T.tomo_project, cube, g, p, 16, 16) == ARG
     p = ptg.copy()
     p[0, 11] = 3.5  # time outside [0, T-1]
