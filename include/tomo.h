@@ -102,8 +102,11 @@ typedef struct tomo_ctx tomo_ctx;
 #define TOMO_OPT_ADJOINT    6  /* transpose kernel: 0 (default) adds every
                                   segment with a float atomic; 1 accumulates
                                   each ray bundle in a shared-memory window
-                                  first (time-interpolated transposes and
-                                  tiles of other than 256 pixels always use 0) */
+                                  first; 2 gives every 16^3 voxel tile to one
+                                  CTA that walks the rays crossing it (no
+                                  global atomics).  Time-interpolated
+                                  transposes always use 0, and 1 needs tiles
+                                  of 256 pixels. */
 
 /* Kernel classes of tomo_profile */
 enum {

@@ -239,12 +239,17 @@ Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
 }
 
 cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
-                        const ImgParam *prm, const float *images,
+                        const ImgParam *prm, const Frame *frames,
+                        const tomo_pointing *ptg, const float *images,
                         const uint8_t *mask, float *cube,
                         const tomo_cube_geom *c, int32_t n_frames,
                         const tomo_image_geom *g, Tiling t, const double *done,
                         cudaStream_t s)
 {
+    if (ctx->adjoint_mode == 2 && n_frames == 1)
+        return launch_adjoint_tiled(rays, prm, frames, ptg, images, mask, cube,
+                                    cube_dev(c), g->n_img, g->nu, g->nv, done,
+                                    s);
     if (ctx->adjoint_mode == 1 && n_frames == 1 && adjoint_window_supported(t))
         return launch_adjoint_window(rays, prm, images, mask, cube, g->n_img,
                                      g->nu, g->nv, c->nx, c->ny, c->nz, t,
@@ -359,7 +364,7 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
         ctx->profile = value != 0;
         return TOMO_OK;
     case TOMO_OPT_ADJOINT:
-        if (value != 0 && value != 1) break;
+        if (value < 0 || value > 2) break;
         ctx->adjoint_mode = (int)value;
         return TOMO_OK;
     default:
@@ -470,7 +475,9 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
     LAUNCH(ctx, TOMO_K_ADJOINT, s,
            run_adjoint(ctx, (const RayRec *)ctx->rays.p,
-                       (const ImgParam *)ctx->params.p, images_dev, mask_dev,
+                       (const ImgParam *)ctx->params.p,
+                       (const Frame *)ctx->frames.p,
+                       (const tomo_pointing *)ctx->ptg.p, images_dev, mask_dev,
                        cube_dev, cube, n_frames, img,
                        tiling_for(ctx, cube, img), nullptr, s));
     return TOMO_OK;
@@ -586,6 +593,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const double *done = S + S_DONE;
     const RayRec *rays = (const RayRec *)ctx->rays.p;
     const ImgParam *prm = (const ImgParam *)ctx->params.p;
+    const Frame *frames = (const Frame *)ctx->frames.p;
+    const tomo_pointing *ptgd = (const tomo_pointing *)ctx->ptg.p;
     const CubeDev cd = cube_dev(cube);
     const int nxny = cube->nx * cube->ny;
     const float lam = (float)lambda;
@@ -603,7 +612,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
     if (m > 0)
         LAUNCH(ctx, TOMO_K_ADJOINT, s,
-               run_adjoint(ctx, rays, prm, y_dev, mask_dev, b, cube, 1, img,
+               run_adjoint(ctx, rays, prm, frames, ptgd, y_dev, mask_dev, b, cube, 1, img,
                            tl, nullptr, s));
     if (flags & TOMO_SOLVE_X0) {
         // r0 = b - (P^T M P + lambda D^T D) x0
@@ -613,7 +622,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                          mask_dev, t, img->n_img, img->nu,
                                          img->nv, cube->nx, nxny, tl, nullptr, s));
             LAUNCH(ctx, TOMO_K_ADJOINT, s,
-                   run_adjoint(ctx, rays, prm, t, mask_dev, q, cube, 1, img,
+                   run_adjoint(ctx, rays, prm, frames, ptgd, t, mask_dev, q, cube, 1, img,
                                tl, nullptr, s));
         }
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, n, tol * tol,
@@ -635,7 +644,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, q, lam, false, done, s));
         if (m > 0)
             LAUNCH(ctx, TOMO_K_ADJOINT, s,
-                   run_adjoint(ctx, rays, prm, t, mask_dev, q, cube, 1, img,
+                   run_adjoint(ctx, rays, prm, frames, ptgd, t, mask_dev, q, cube, 1, img,
                                tl, done, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, n, partials, counter,

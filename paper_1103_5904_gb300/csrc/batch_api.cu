@@ -285,7 +285,9 @@ tomo_status time_tiling(tomo_ctx *ctx, const tomo_problem *p, Tiling t,
         if (err == cudaSuccess) err = cudaEventRecord(e[1], s);
         if (err == cudaSuccess)
             err = run_adjoint(ctx, (const RayRec *)ctx->rays.p,
-                              (const ImgParam *)ctx->params.p, p->images_dev,
+                              (const ImgParam *)ctx->params.p,
+                              (const Frame *)ctx->frames.p,
+                              (const tomo_pointing *)ctx->ptg.p, p->images_dev,
                               p->mask_dev, cube_tmp, &p->cube, 1, &p->img, t,
                               nullptr, s);
         if (err == cudaSuccess) err = cudaEventRecord(e[2], s);

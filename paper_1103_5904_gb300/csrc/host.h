@@ -36,7 +36,7 @@ struct tomo_ctx {
     int num_sms = 0;
     char err[512] = { 0 };
     bool ray_cache = true;
-    int adjoint_mode = 0;  // 0: one float atomic per segment; 1: windowed
+    int adjoint_mode = 0;  // 0: float atomics; 1: bundle window; 2: tiles
     tomo::Tiling tiling = { 32, 8, 8 };
     // geometry cache
     bool key_valid = false;
@@ -81,7 +81,8 @@ void free_plan(tomo_ctx *ctx);
 // Launches the transpose of one problem with the context's adjoint mode
 // (windowed when possible, plain atomics otherwise).
 cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
-                        const ImgParam *prm, const float *images,
+                        const ImgParam *prm, const Frame *frames,
+                        const tomo_pointing *ptg, const float *images,
                         const uint8_t *mask, float *cube,
                         const tomo_cube_geom *c, int32_t n_frames,
                         const tomo_image_geom *g, Tiling t, const double *done,

@@ -98,6 +98,14 @@ cudaError_t launch_adjoint_window(const RayRec *rays, const ImgParam *prm,
                                   int32_t nv, int32_t nx, int32_t ny,
                                   int32_t nz, Tiling t, const double *done,
                                   cudaStream_t s);
+// adjoint_tiled.cu: transpose with one CTA per cube tile, no global atomics
+// (static frames only)
+cudaError_t launch_adjoint_tiled(const RayRec *rays, const ImgParam *prm,
+                                 const Frame *frames, const tomo_pointing *ptg,
+                                 const float *images, const uint8_t *mask,
+                                 float *cube, CubeDev c, int32_t n_img,
+                                 int32_t nu, int32_t nv, const double *done,
+                                 cudaStream_t s);
 cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
                          int32_t n_img, int32_t nu, int32_t nv, Tiling t,
                          unsigned long long *count, cudaStream_t s);
