@@ -68,6 +68,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--adjoint-mode", type=int, default=None,
+                    help="transpose kernel (TOMO_OPT_ADJOINT): 0 float "
+                         "atomics, 1 bundle window, 2 voxel tiles")
     ap.add_argument("--images", type=int, default=0,
                     help="keep only this many images (evenly spaced) of the "
                          "workload: a reduced case for profiler captures")
@@ -288,6 +291,8 @@ def run_gpu(args, rank, local_rank, world):
     g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
     n_img = ptg.shape[0]
     ctx = T.Context(local_rank)
+    if args.adjoint_mode is not None:
+        ctx.set_option(T.tomo.TOMO_OPT_ADJOINT, args.adjoint_mode)
     mask_h = c["mask"]
     mask = torch.from_numpy(mask_h).to(dev) if mask_h is not None else None
     x_true = torch.from_numpy(c["cube"]).to(dev)
@@ -360,7 +365,10 @@ def run_gpu(args, rank, local_rank, world):
                       "time_share": ms / sum(v[1] for v in prof.values())}
     dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
     peak, peak_src = peak_hbm()
-    kname = {"forward": "k_forward<float,false>", "adjoint": "k_adjoint<false>"}
+    kname = {"forward": "k_forward<float,false>",
+             "adjoint": {None: "k_adjoint<false>", 0: "k_adjoint<false>",
+                         1: "k_adjoint_window",
+                         2: "k_adjoint_tiled"}[args.adjoint_mode]}
     roofline = {"bound": "hbm", "kernel": kname[dom],
                 "achieved": kern[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
@@ -497,6 +505,12 @@ def run_batched(args, rank, local_rank, world):
     ms_b = timed(batched, args.steps)
     launches = sum(v[0] for v in ctx.profile(reset=True).values())
     ms_s = timed(sequential, args.steps)
+    # per-kernel device time of one sequential pass (CUDA events)
+    ctx.set_option(T.tomo.TOMO_OPT_PROFILE, 1)
+    ctx.profile(reset=True)
+    sequential()
+    seq_prof = ctx.profile(reset=True)
+    ctx.set_option(T.tomo.TOMO_OPT_PROFILE, 0)
     if rank == 0:
         line = {
             "metric": METRIC, "value": units / (ms_b / 1e3), "unit": UNIT,
@@ -510,7 +524,9 @@ def run_batched(args, rank, local_rank, world):
                        "segments_per_projection_all_problems": segs},
             "sequential": {"value": units / (ms_s / 1e3), "unit": UNIT,
                            "ms_per_step": ms_s,
-                           "what": "tomo_solve per problem, one after another"},
+                           "what": "tomo_solve per problem, one after another",
+                           "kernels_ms": {k: v[1] for k, v in seq_prof.items()},
+                           "launches": {k: v[0] for k, v in seq_prof.items()}},
             "batched_speedup": ms_s / ms_b,
             "gpu_launches": launches,
         }

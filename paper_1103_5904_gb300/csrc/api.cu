@@ -167,6 +167,7 @@ CubeDev cube_dev(const tomo_cube_geom *c)
     d.d[0] = c->dx;
     d.d[1] = c->dy;
     d.d[2] = c->dz;
+    for (int k = 0; k < 3; ++k) d.inv_d[k] = 1.0 / d.d[k];
     return d;
 }
 

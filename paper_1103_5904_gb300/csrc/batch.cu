@@ -4,9 +4,11 @@
 // Ray kernels are persistent: one grid of (SM count x resident CTAs) CTAs
 // pulls work items from an atomic counter until the list is exhausted (no
 // CTA ever waits for another).  An item is one pixel tile of one image of
-// one problem; problems are laid out back to back in item space through a
-// prefix array, and each problem carries its own tile shape (256 threads per
-// CTA for all of them), chosen by the autotuner.  The walk is the same
+// one problem; the schedule deals groups of kSchedGroup tiles round-robin
+// over the problems, so the transposes of all problems run side by side and
+// their float atomics spread over every cube instead of piling onto one
+// small cube at a time.  Each problem carries its own tile shape (256
+// threads per CTA for all of them), chosen by the autotuner.  The walk is the same
 // Siddon walk as the single-problem kernels (walk.cuh).
 //
 // Vector kernels run over (problem, chunk of kChunk elements) items: a CTA
@@ -43,23 +45,27 @@ __device__ __forceinline__ int owner(const int64_t *__restrict__ prefix,
 }
 
 template <bool kAdjoint>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 8)
 k_walk_batched(const WalkDesc *__restrict__ descs,
-               const int64_t *__restrict__ prefix, int n_probs,
+               const int64_t *__restrict__ prefix,
+               const int2 *__restrict__ sched, int64_t n_chunks,
                unsigned long long *next_item)
 {
     __shared__ long long s_item;
-    const int64_t n_items = prefix[n_probs];
+    const int64_t n_items = n_chunks * kSchedGroup;
     for (;;) {
         __syncthreads();  // every thread has read the previous s_item
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
         __syncthreads();
         const int64_t item = s_item;
         if (item >= n_items) break;
-        const int p = owner(prefix, n_probs, item);
+        // chunk of kSchedGroup consecutive tiles of one problem
+        const int2 ch = sched[item / kSchedGroup];
+        const int p = ch.x;
+        const int64_t t = (int64_t)ch.y + item % kSchedGroup;
+        if (t >= prefix[p + 1] - prefix[p]) continue;
         const WalkDesc d = descs[p];
         if (d.done != nullptr && *d.done != 0.0) continue;
-        const int64_t t = item - prefix[p];
         const int tu = (int)(t % d.tiles_u);
         const int64_t rest = t / d.tiles_u;
         const int tv = (int)(rest % d.tiles_v);
@@ -230,16 +236,16 @@ int walk_batched_blocks_per_sm()
 }
 
 cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,
-                                const int64_t *prefix, int n_probs,
-                                unsigned long long *next_item, int grid,
-                                cudaStream_t s)
+                                const int64_t *prefix, const int2 *sched,
+                                int64_t n_chunks, unsigned long long *next_item,
+                                int grid, cudaStream_t s)
 {
     if (adjoint)
-        k_walk_batched<true><<<grid, kThreads, 0, s>>>(descs, prefix, n_probs,
-                                                        next_item);
+        k_walk_batched<true><<<grid, kThreads, 0, s>>>(descs, prefix, sched,
+                                                        n_chunks, next_item);
     else
-        k_walk_batched<false><<<grid, kThreads, 0, s>>>(descs, prefix, n_probs,
-                                                         next_item);
+        k_walk_batched<false><<<grid, kThreads, 0, s>>>(descs, prefix, sched,
+                                                         n_chunks, next_item);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 namespace tomo {
 
 constexpr int64_t kChunk = 16384;  // elements per vector work item
+constexpr int kSchedGroup = 4;     // tiles per walk schedule entry
 
 // One problem as seen by a persistent walk kernel.  Forward: gathers `src`
 // (cube) into `dst` (images).  Adjoint: scatters `src` (images) into `dst`
@@ -36,10 +37,12 @@ struct VecDesc {
 };
 
 int walk_batched_blocks_per_sm();
+// sched[c] = (problem, first tile) of chunk c: kSchedGroup consecutive
+// tiles of one problem (tiles past the problem's count are skipped)
 cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,
-                                const int64_t *prefix, int n_probs,
-                                unsigned long long *next_item, int grid,
-                                cudaStream_t s);
+                                const int64_t *prefix, const int2 *sched,
+                                int64_t n_chunks, unsigned long long *next_item,
+                                int grid, cudaStream_t s);
 cudaError_t launch_vec_batched(int op, const VecDesc *descs,
                                const int64_t *prefix, int n_probs, bool warm,
                                double *partials, int grid, cudaStream_t s);

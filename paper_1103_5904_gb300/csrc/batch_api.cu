@@ -29,6 +29,8 @@ struct BatchPlan {
     std::vector<int64_t> ray_off, img_off, tu_off, tv_off;
     std::vector<Tiling> tl;
     std::vector<int64_t> tile_prefix;  // n + 1
+    DevBuf tpre_dev, sched_dev;        // tile prefix, walk schedule
+    int64_t n_chunks = 0;
     cudaEvent_t ready = nullptr;
     // per-call descriptors of the projector / transpose entry points
     DevBuf call_desc, call_prefix, call_counter;
@@ -46,7 +48,8 @@ void free_plan(tomo_ctx *ctx)
     BatchPlan *p = ctx->plan;
     if (!p) return;
     DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
-                       &p->rays, &p->call_desc, &p->call_prefix,
+                       &p->rays, &p->tpre_dev, &p->sched_dev,
+                       &p->call_desc, &p->call_prefix,
                        &p->call_counter, &p->vec, &p->timg, &p->S,
                        &p->partials, &p->counters, &p->walk_desc,
                        &p->vec_desc, &p->prefixes };
@@ -195,6 +198,26 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                 p.img.nu, p.img.nv,
                                 (RayRec *)P->rays.p + P->ray_off[i], s));
     }
+    // walk schedule: groups of kSchedGroup tiles dealt round-robin over
+    // the problems
+    std::vector<int2> sched;
+    std::vector<int64_t> next(n, 0);
+    for (bool any = true; any;) {
+        any = false;
+        for (int32_t i = 0; i < n; ++i) {
+            if (next[i] < P->tile_prefix[i + 1] - P->tile_prefix[i]) {
+                sched.push_back(make_int2(i, (int)next[i]));
+                next[i] += kSchedGroup;
+                any = true;
+            }
+        }
+    }
+    P->n_chunks = (int64_t)sched.size();
+    if ((st = upload(ctx, P->tpre_dev, P->tile_prefix.data(),
+                     sizeof(int64_t) * (n + 1), s)) ||
+        (st = upload(ctx, P->sched_dev, sched.data(),
+                     sizeof(int2) * (sched.empty() ? 1 : sched.size()), s)))
+        return st;
     CUDA_TRY(ctx, cudaEventRecord(P->ready, s));
     P->geom_key = h;
     return TOMO_OK;
@@ -248,15 +271,14 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                           s));
     if (P->tile_prefix[n] == 0) return TOMO_OK;
     if ((st = upload(ctx, P->call_desc, d.data(), sizeof(WalkDesc) * n, s)) ||
-        (st = upload(ctx, P->call_prefix, P->tile_prefix.data(),
-                     sizeof(int64_t) * (n + 1), s)) ||
         (st = ensure(ctx, P->call_counter, sizeof(unsigned long long))))
         return st;
     CUDA_TRY(ctx, cudaMemsetAsync(P->call_counter.p, 0,
                                   sizeof(unsigned long long), s));
     LAUNCH(ctx, adjoint ? TOMO_K_ADJOINT : TOMO_K_FORWARD, s,
            launch_walk_batched(adjoint, (const WalkDesc *)P->call_desc.p,
-                               (const int64_t *)P->call_prefix.p, n,
+                               (const int64_t *)P->tpre_dev.p,
+                               (const int2 *)P->sched_dev.p, P->n_chunks,
                                (unsigned long long *)P->call_counter.p,
                                walk_grid(ctx), s));
     return TOMO_OK;
@@ -525,6 +547,8 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int64_t *vox_pre = tile_pre + (n + 1);
         const int64_t *pix_pre = vox_pre + (n + 1);
         unsigned long long *ctr = (unsigned long long *)P->counters.p;
+        const int2 *sch = (const int2 *)P->sched_dev.p;
+        const int64_t nch = P->n_chunks;
         double *part = (double *)P->partials.p;
         const int wgrid = walk_grid(ctx);
         const int vgrid = (int)(max_items < 4 * walk_grid(ctx) ? max_items
@@ -550,14 +574,14 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                                                    part, c));
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_ZERO, V, vox_pre, n, warm, part,
                                               vgrid, c));
-        CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 0 * n, tile_pre, n,
+        CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 0 * n, tile_pre, sch, nch,
                                                 ctr + next_ctr++, wgrid, c));
         if (warm) {
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR_X, V, vox_pre, n, warm,
                                                  part, vgrid, c));
-            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, n,
+            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, sch, nch,
                                                     ctr + next_ctr++, wgrid, c));
-            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 2 * n, tile_pre, n,
+            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 2 * n, tile_pre, sch, nch,
                                                     ctr + next_ctr++, wgrid, c));
         }
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_INIT, V, vox_pre, n, warm, part,
@@ -565,11 +589,11 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_INIT, V, vox_pre, n, 0.0,
                                                    part, c));
         for (int32_t k = 0; k < n_iter; ++k) {
-            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 3 * n, tile_pre, n,
+            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 3 * n, tile_pre, sch, nch,
                                                     ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR, V, vox_pre, n, warm,
                                                  part, vgrid, c));
-            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 4 * n, tile_pre, n,
+            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 4 * n, tile_pre, sch, nch,
                                                     ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_VECTOR, launch_vec_batched(BV_PQ, V, vox_pre, n, warm,
                                                   part, vgrid, c));

@@ -93,6 +93,9 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
     for (int a = 0; a < 3; ++a) u[a] *= inv;
 
     const int n[3] = { c.nx, c.ny, c.nz };
+    // one FP64 reciprocal per axis serves the clip and the crossing spacing
+    double ru[3];
+    for (int a = 0; a < 3; ++a) ru[a] = (u[a] != 0.0) ? 1.0 / u[a] : 0.0;
     double amin = 0.0, amax = INFINITY;
     bool hit = true;
     for (int a = 0; a < 3; ++a) {
@@ -100,8 +103,8 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
         if (u[a] == 0.0) {
             if (f.o[a] < lo || f.o[a] >= hi) hit = false;
         } else {
-            const double a0 = (lo - f.o[a]) / u[a];
-            const double a1 = (hi - f.o[a]) / u[a];
+            const double a0 = (lo - f.o[a]) * ru[a];
+            const double a1 = (hi - f.o[a]) * ru[a];
             amin = fmax(amin, fmin(a0, a1));
             amax = fmin(amax, fmax(a0, a1));
         }
@@ -117,14 +120,14 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
         float t0f[3], dtf[3];
         for (int a = 0; a < 3; ++a) {
             const double pa = f.o[a] + amin * u[a];
-            const double g = (pa - c.lo[a]) / c.d[a];  // voxel coordinate
+            const double g = (pa - c.lo[a]) * c.inv_d[a];  // voxel coordinate
             int ia = (u[a] < 0.0) ? (int)ceil(g) - 1 : (int)floor(g);
             ia = ia < 0 ? 0 : (ia > n[a] - 1 ? n[a] - 1 : ia);
             idx[a] = ia;
             if (u[a] != 0.0) {
                 const double plane = (u[a] > 0.0) ? ia + 1.0 : (double)ia;
-                const double t0 = fmax((plane - g) * c.d[a] / u[a], 0.0);
-                const float dt = (float)(c.d[a] / fabs(u[a]));
+                const double t0 = fmax((plane - g) * c.d[a] * ru[a], 0.0);
+                const float dt = (float)(c.d[a] * fabs(ru[a]));
                 const int rem = (u[a] > 0.0) ? n[a] - 1 - ia : ia;
                 t0f[a] = (float)t0;
                 // last in-cube plane of this axis, in the walk's arithmetic

@@ -43,6 +43,7 @@ struct Frame {
 struct CubeDev {
     int32_t nx, ny, nz;
     double lo[3], d[3];
+    double inv_d[3];  // 1 / d
 };
 
 struct Tiling {
