@@ -2,12 +2,12 @@
 // uneven sizes (cube side, image count and image size differ per problem).
 //
 // Ray kernels are persistent: one grid of (SM count x resident CTAs) CTAs
-// pulls work items from an atomic counter until the list is exhausted (no
-// CTA ever waits for another).  An item is one pixel tile of one image of
-// one problem; the schedule deals groups of kSchedGroup tiles round-robin
-// over the problems, so the transposes of all problems run side by side and
-// their float atomics spread over every cube instead of piling onto one
-// small cube at a time.  Each problem carries its own tile shape (256
+// strides over the work list until it is exhausted.  A work unit is one warp
+// tile (32 pixels) of one pixel tile of one image of one problem; the
+// schedule deals groups of kSchedGroup tiles round-robin over the problems,
+// so every warp's share mixes all problems evenly, and the transposes of all
+// problems run side by side with their float atomics spread over every cube
+// instead of piling onto one small cube at a time.  Each problem carries its own tile shape (256
 // threads per CTA for all of them), chosen by the autotuner.  The walk is the same
 // Siddon walk as the single-problem kernels (walk.cuh).
 //
@@ -45,61 +45,84 @@ __device__ __forceinline__ int owner(const int64_t *__restrict__ prefix,
 }
 
 template <bool kAdjoint>
-__global__ void __launch_bounds__(kThreads, 8)
+__global__ void __launch_bounds__(kThreads, 6)
 k_walk_batched(const WalkDesc *__restrict__ descs,
                const int64_t *__restrict__ prefix,
                const int2 *__restrict__ sched, int64_t n_chunks,
                unsigned long long *next_item)
 {
+    // CTAs take tiles from a work queue (one atomic counter); warp w of the
+    // CTA walks warp tile w of the tile, and a barrier per tile keeps the
+    // CTA's warps together: their rays are neighbours that sweep the same
+    // voxels at the same depth, which is what the L1 reuses (measured:
+    // without the barrier, or with static striding, the walks run slower).
+    // The fetch of the next tile is issued when the current one starts and
+    // read after its walk: in the transpose the counter shares the L2 atomic
+    // units with every segment's reduction, and a fetch waited for at the
+    // barrier would park the whole CTA in that queue.
     __shared__ long long s_item;
+    const int lane = threadIdx.x & 31;
+    const int wt = threadIdx.x >> 5;  // warp tile in the tile
     const int64_t n_items = n_chunks * kSchedGroup;
-    for (;;) {
-        __syncthreads();  // every thread has read the previous s_item
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    int64_t item = s_item;
+    while (item < n_items) {
+        unsigned long long ahead = 0;
+        if (threadIdx.x == 0) ahead = atomicAdd(next_item, 1ull);
+        do {
+            const int2 ch = sched[item / kSchedGroup];
+            const int p = ch.x;
+            const int t = ch.y + (int)(item % kSchedGroup);
+            if (t >= (int)(prefix[p + 1] - prefix[p])) continue;
+            const WalkDesc d = descs[p];
+            if (d.done != nullptr && *d.done != 0.0) continue;
+            const int tu = t % d.tiles_u;
+            const int rest = t / d.tiles_u;
+            const int tv = rest % d.tiles_v;
+            const int img = rest / d.tiles_v;
+            // the pixel of this lane: warp tile wt of tile (tu, tv), laid out as
+            // in the single-problem kernels
+            const int rows = 32 / d.tl.warp_u;
+            const int warps_u = d.tl.tile_u / d.tl.warp_u;
+            const int iu = tu * d.tl.tile_u + (wt % warps_u) * d.tl.warp_u +
+                           (lane % d.tl.warp_u);
+            const int iv = tv * d.tl.tile_v + (wt / warps_u) * rows +
+                           (lane / d.tl.warp_u);
+            if (iu >= d.nu || iv >= d.nv) continue;
+            const int64_t id = ((int64_t)img * d.nv + iv) * d.nu + iu;
+            const bool masked = d.mask != nullptr && d.mask[id] != 0;
+            const float gain = d.prm[img].gain;
+            if (!kAdjoint) {
+                float y = 0.0f;
+                if (!masked) {
+                    const RayRec r = load_ray(d.rays + id);
+                    if (r.chord > 0.0f) {
+                        GatherOp<float> op;
+                        op.c = d.src;
+                        op.acc = 0.0f;
+                        siddon_walk(r, d.nx, d.nxny, op);
+                        y = gain * op.acc;
+                    }
+                }
+                d.dst[id] = y;
+            } else if (!masked) {
+                const float yv = gain * d.src[id];
+                if (yv != 0.0f) {
+                    const RayRec r = load_ray(d.rays + id);
+                    if (r.chord > 0.0f) {
+                        ScatterOp op;
+                        op.c = d.dst;
+                        op.y = yv;
+                        siddon_walk(r, d.nx, d.nxny, op);
+                    }
+                }
+            }
+        } while (false);
+        __syncthreads();  // every thread has read s_item
+        if (threadIdx.x == 0) s_item = (long long)ahead;
         __syncthreads();
-        const int64_t item = s_item;
-        if (item >= n_items) break;
-        // chunk of kSchedGroup consecutive tiles of one problem
-        const int2 ch = sched[item / kSchedGroup];
-        const int p = ch.x;
-        const int64_t t = (int64_t)ch.y + item % kSchedGroup;
-        if (t >= prefix[p + 1] - prefix[p]) continue;
-        const WalkDesc d = descs[p];
-        if (d.done != nullptr && *d.done != 0.0) continue;
-        const int tu = (int)(t % d.tiles_u);
-        const int64_t rest = t / d.tiles_u;
-        const int tv = (int)(rest % d.tiles_v);
-        const int img = (int)(rest / d.tiles_v);
-        int iu, iv;
-        if (!pixel_of_thread(d.tl, tu, tv, d.nu, d.nv, iu, iv)) continue;
-        const int64_t id = ((int64_t)img * d.nv + iv) * d.nu + iu;
-        const bool masked = d.mask != nullptr && d.mask[id] != 0;
-        const float gain = d.prm[img].gain;
-        if (!kAdjoint) {
-            float y = 0.0f;
-            if (!masked) {
-                const RayRec r = load_ray(d.rays + id);
-                if (r.chord > 0.0f) {
-                    GatherOp<float> op;
-                    op.c = d.src;
-                    op.acc = 0.0f;
-                    siddon_walk(r, d.nx, d.nxny, op);
-                    y = gain * op.acc;
-                }
-            }
-            d.dst[id] = y;
-        } else if (!masked) {
-            const float yv = gain * d.src[id];
-            if (yv != 0.0f) {
-                const RayRec r = load_ray(d.rays + id);
-                if (r.chord > 0.0f) {
-                    ScatterOp op;
-                    op.c = d.dst;
-                    op.y = yv;
-                    siddon_walk(r, d.nx, d.nxny, op);
-                }
-            }
-        }
+        item = s_item;
     }
 }
 

@@ -33,7 +33,7 @@ struct BatchPlan {
     int64_t n_chunks = 0;
     cudaEvent_t ready = nullptr;
     // per-call descriptors of the projector / transpose entry points
-    DevBuf call_desc, call_prefix, call_counter;
+    DevBuf call_desc, call_counter;
     // solver workspace and graph
     DevBuf vec, timg, S, partials, counters, walk_desc, vec_desc, prefixes;
     cudaGraph_t graph = nullptr;
@@ -49,8 +49,8 @@ void free_plan(tomo_ctx *ctx)
     if (!p) return;
     DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
                        &p->rays, &p->tpre_dev, &p->sched_dev,
-                       &p->call_desc, &p->call_prefix,
-                       &p->call_counter, &p->vec, &p->timg, &p->S,
+                       &p->call_desc, &p->call_counter, &p->vec, &p->timg,
+                       &p->S,
                        &p->partials, &p->counters, &p->walk_desc,
                        &p->vec_desc, &p->prefixes };
     for (DevBuf *b : bufs)
@@ -485,7 +485,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         }
         const int64_t NV = voff[n];
         const int64_t max_items = vitems[n] > pitems[n] ? vitems[n] : pitems[n];
-        const int n_walks = 1 + (warm ? 2 : 0) + 2 * n_iter;
+        const int n_walks = 1 + (warm ? 2 : 0) + 2 * n_iter;  // queue counters
         if ((st = ensure(ctx, P->vec, sizeof(float) * 4 * NV)) ||
             (st = ensure(ctx, P->timg, sizeof(float) * (poff[n] > 0 ? poff[n] : 1))) ||
             (st = ensure(ctx, P->S, sizeof(double) * n * (S_NSLOTS + stride))) ||
@@ -547,6 +547,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int64_t *vox_pre = tile_pre + (n + 1);
         const int64_t *pix_pre = vox_pre + (n + 1);
         unsigned long long *ctr = (unsigned long long *)P->counters.p;
+        int next_ctr = 0;
         const int2 *sch = (const int2 *)P->sched_dev.p;
         const int64_t nch = P->n_chunks;
         double *part = (double *)P->partials.p;
@@ -554,7 +555,6 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int vgrid = (int)(max_items < 4 * walk_grid(ctx) ? max_items
                                                                : 4 * walk_grid(ctx));
         int64_t counts[TOMO_K_COUNT] = { 0 };
-        int next_ctr = 0;
         cudaError_t e = cudaStreamBeginCapture(c, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess)
             return fail(ctx, TOMO_ERR_CUDA, "begin capture: %s",
@@ -580,9 +580,9 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR_X, V, vox_pre, n, warm,
                                                  part, vgrid, c));
             CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, sch, nch,
-                                                    ctr + next_ctr++, wgrid, c));
+                                                ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 2 * n, tile_pre, sch, nch,
-                                                    ctr + next_ctr++, wgrid, c));
+                                                ctr + next_ctr++, wgrid, c));
         }
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_INIT, V, vox_pre, n, warm, part,
                                               vgrid, c));
@@ -590,11 +590,11 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                                                    part, c));
         for (int32_t k = 0; k < n_iter; ++k) {
             CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 3 * n, tile_pre, sch, nch,
-                                                    ctr + next_ctr++, wgrid, c));
+                                                ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR, V, vox_pre, n, warm,
                                                  part, vgrid, c));
             CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 4 * n, tile_pre, sch, nch,
-                                                    ctr + next_ctr++, wgrid, c));
+                                                ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_VECTOR, launch_vec_batched(BV_PQ, V, vox_pre, n, warm,
                                                   part, vgrid, c));
             CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_PQ, V, vox_pre, n, 0.0,

@@ -115,12 +115,39 @@ struct GatherTimeOp {
     }
 };
 
+// Scatter of one segment, len * y, into voxel idx.  Neighbouring lanes walk
+// neighbouring rays of one observer and are often in the same voxel at the
+// same step; before the float atomic, contributions of lanes that hold the
+// same voxel are summed along a small shuffle tree (partner lanes at lane
+// distance 1, 2 and 8: neighbours along u, and the next pixel row for the
+// default 8 x 4 warp tile), so one lane issues the atomic for the group.
+// The equality test makes it correct for any lane layout; it only pays when
+// neighbours coincide.  The sum is the same up to the order of additions.
 struct ScatterOp {
     float *c;
     float y;
     __device__ __forceinline__ void operator()(int idx, float len)
     {
-        if (len > 0.0f) atomicAdd(c + idx, len * y);
+        float v = (len > 0.0f) ? len * y : 0.0f;
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        int key = (len > 0.0f) ? idx : -1 - lane;  // idle lanes never match
+#pragma unroll
+        for (int lvl = 0; lvl < 3; ++lvl) {
+            const int o = lvl == 0 ? 1 : (lvl == 1 ? 2 : 8);
+            const bool partner_active = (act >> (lane ^ o)) & 1u;
+            const int pk = __shfl_xor_sync(act, key, o);
+            const float pv = __shfl_xor_sync(act, v, o);
+            if (partner_active && pk == key) {
+                if (lane & o) {
+                    v = 0.0f;
+                    key = -1 - lane;
+                } else {
+                    v += pv;
+                }
+            }
+        }
+        if (v != 0.0f) atomicAdd(c + idx, v);
     }
 };
 

@@ -116,10 +116,13 @@ def test_solve_batched_matches_sequential_and_oracle(T):
     for p, d, info in zip(probs, dp, infos):
         x_seq, inf_seq = T.tomo_solve(d["images"], p["geom"], p["pointing"],
                                       lam=p["lam"], max_iter=10)
-        np.testing.assert_allclose(info["J"], inf_seq["J"], rtol=1e-4)
+        # two FP32 runs whose float atomics add in different orders: the
+        # same 1e-3 bounds as FP32 CG against FP64 CG (J is reported through
+        # y^T M y - x^T (r + b), which loses digits as J falls)
+        np.testing.assert_allclose(info["J"], inf_seq["J"], rtol=1e-3)
         rel = float(torch.linalg.norm(d["cube"] - x_seq) /
                     torch.linalg.norm(x_seq))
-        assert rel <= 1e-4, rel
+        assert rel <= 1e-3, rel
     for k in (0, 3):
         p = probs[k]
         pb = solver.Problem(p["geom"], p["pointing"], p["nu"], p["nv"], p["y"],
