@@ -107,6 +107,25 @@ typedef struct tomo_ctx tomo_ctx;
                                   global atomics).  Time-interpolated
                                   transposes always use 0, and 1 needs tiles
                                   of 256 pixels. */
+#define TOMO_OPT_PLANE_SYNC 7  /* bit mask (default 1): bit 0 for P^T (with
+                                  TOMO_OPT_ADJOINT 0), bit 1 for P, of
+                                  single-problem calls.  A set bit makes the
+                                  rays of a warp walk the cube one plane of
+                                  the image's major axis at a time, on a copy
+                                  of the cube stored with the image's
+                                  lateral axis fastest, so the voxels a warp
+                                  touches at once fall in few 32-byte
+                                  sectors; a clear bit makes every lane walk
+                                  its own ray one segment per step.  Same
+                                  segments either way: P is bit-identical,
+                                  P^T differs only by the order of float
+                                  additions.  The plane walk uses its own
+                                  tiling (32 x 8 pixels per CTA, one image
+                                  row per warp) whatever the tile options
+                                  say.  Needs cubes of at most 16384 voxels
+                                  per side, else the per-ray walk is used.
+                                  Costs two cube-sized float buffers (times
+                                  the frames) of workspace. */
 
 /* Kernel classes of tomo_profile */
 enum {
@@ -115,7 +134,8 @@ enum {
     TOMO_K_ADJOINT = 2, /* Siddon scatter, P^T */
     TOMO_K_PRIOR = 3,   /* D^T D stencil */
     TOMO_K_VECTOR = 4,  /* CG vector updates and reductions */
-    TOMO_K_COUNT = 5
+    TOMO_K_LAYOUT = 5,  /* cube layout copies of the plane-synchronous walk */
+    TOMO_K_COUNT = 6
 };
 
 /* Per kernel class: launches since the last reset and, with

@@ -184,6 +184,8 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     h = fnv1a(h, cv, sizeof(cv));
     h = fnv1a(h, g, sizeof(*g));
     h = fnv1a(h, ptg, sizeof(tomo_pointing) * (size_t)g->n_img);
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->layout_used, sizeof(unsigned)))) return st;
     if (ctx->ray_cache && ctx->key_valid && ctx->key == h) {
         CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
         return TOMO_OK;
@@ -191,7 +193,6 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     ctx->key_valid = false;
     const size_t n_img = (size_t)g->n_img;
     const size_t npix = n_img * g->nu * g->nv;
-    tomo_status st;
     if ((st = ensure(ctx, ctx->ptg, sizeof(tomo_pointing) * n_img)) ||
         (st = ensure(ctx, ctx->frames, sizeof(Frame) * n_img)) ||
         (st = ensure(ctx, ctx->tan_u, sizeof(double) * n_img * g->nu)) ||
@@ -201,11 +202,13 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
         return st;
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
                                   cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
                          g->nv, n_frames, (Frame *)ctx->frames.p,
                          (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
-                         (ImgParam *)ctx->params.p, s));
+                         (ImgParam *)ctx->params.p,
+                         (unsigned *)ctx->layout_used.p, s));
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_ray_setup((const Frame *)ctx->frames.p,
                             (const double *)ctx->tan_u.p,
@@ -259,6 +262,94 @@ cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
     return launch_adjoint(rays, prm, images, mask, cube, fstride, n_frames > 1,
                           g->n_img, g->nu, g->nv, c->nx, c->nx * c->ny, t,
                           done, s);
+}
+
+bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
+               bool forward)
+{
+    const int bit = forward ? 2 : 1;
+    if (!forward && ctx->adjoint_mode != 0) return false;
+    (void)t;
+    return (ctx->plane_sync & bit) != 0 && plane_supported(c);
+}
+
+tomo_status ensure_plane(tomo_ctx *ctx, const tomo_cube_geom *c,
+                         int32_t n_frames, Tiling t)
+{
+    if (!use_plane(ctx, c, t, true) && !use_plane(ctx, c, t, false))
+        return TOMO_OK;
+    const size_t bytes =
+        sizeof(float) * (size_t)c->nx * c->ny * c->nz * (size_t)n_frames;
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->lay1, bytes)) || (st = ensure(ctx, ctx->lay2, bytes)))
+        return st;
+    return TOMO_OK;
+}
+
+tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
+                        int32_t n_frames, const uint8_t *mask, float *out,
+                        const tomo_cube_geom *c, const tomo_image_geom *g,
+                        Tiling t, const double *done, cudaStream_t s)
+{
+    const RayRec *rays = (const RayRec *)ctx->rays.p;
+    const ImgParam *prm = (const ImgParam *)ctx->params.p;
+    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+    if (use_plane(ctx, c, t, true)) {
+        const unsigned *used = (const unsigned *)ctx->layout_used.p;
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_to_layout(cube_dev, dtype, ctx->lay1.p, 1, c, n_frames,
+                                used, done, s));
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_to_layout(cube_dev, dtype, ctx->lay2.p, 2, c, n_frames,
+                                used, done, s));
+        PlaneCubes pc = { { cube_dev, ctx->lay1.p, ctx->lay2.p } };
+        LAUNCH(ctx, TOMO_K_FORWARD, s,
+               launch_forward_plane(rays, prm, pc, dtype, fstride, n_frames > 1,
+                                    mask, out, g->n_img, g->nu, g->nv, c,
+                                    done, s));
+        return TOMO_OK;
+    }
+    LAUNCH(ctx, TOMO_K_FORWARD, s,
+           launch_forward(rays, prm, cube_dev, dtype, fstride, n_frames > 1,
+                          mask, out, g->n_img, g->nu, g->nv, c->nx,
+                          c->nx * c->ny, t, done, s));
+    return TOMO_OK;
+}
+
+tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
+                        const uint8_t *mask, float *cube,
+                        const tomo_cube_geom *c, int32_t n_frames,
+                        const tomo_image_geom *g, Tiling t,
+                        const double *done, cudaStream_t s)
+{
+    const RayRec *rays = (const RayRec *)ctx->rays.p;
+    const ImgParam *prm = (const ImgParam *)ctx->params.p;
+    if (use_plane(ctx, c, t, false)) {
+        const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+        const unsigned *used = (const unsigned *)ctx->layout_used.p;
+        float *a1 = (float *)ctx->lay1.p, *a2 = (float *)ctx->lay2.p;
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_zero_layout(a1, 1, fstride * n_frames, used, done,
+                                  ctx->num_sms, s));
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_zero_layout(a2, 2, fstride * n_frames, used, done,
+                                  ctx->num_sms, s));
+        PlaneAcc pa = { { cube, a1, a2 } };
+        LAUNCH(ctx, TOMO_K_ADJOINT, s,
+               launch_adjoint_plane(rays, prm, images, mask, pa, fstride,
+                                    n_frames > 1, g->n_img, g->nu, g->nv, c,
+                                    done, s));
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_add_from_layout(a1, cube, 1, c, n_frames, used, done, s));
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_add_from_layout(a2, cube, 2, c, n_frames, used, done, s));
+        return TOMO_OK;
+    }
+    LAUNCH(ctx, TOMO_K_ADJOINT, s,
+           run_adjoint(ctx, rays, prm, (const Frame *)ctx->frames.p,
+                       (const tomo_pointing *)ctx->ptg.p, images, mask, cube,
+                       c, n_frames, g, t, done, s));
+    return TOMO_OK;
 }
 
 int reduce_grid(const tomo_ctx *ctx, int64_t n)
@@ -330,7 +421,8 @@ void tomo_destroy(tomo_ctx *ctx)
     DevBuf *bufs[] = { &ctx->ptg, &ctx->frames, &ctx->tan_u, &ctx->tan_v,
                        &ctx->params, &ctx->rays, &ctx->b, &ctx->r, &ctx->p,
                        &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
-                       &ctx->counter, &ctx->count64 };
+                       &ctx->counter, &ctx->count64, &ctx->layout_used,
+                       &ctx->lay1, &ctx->lay2 };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     free_plan(ctx);
@@ -367,6 +459,10 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
     case TOMO_OPT_ADJOINT:
         if (value < 0 || value > 2) break;
         ctx->adjoint_mode = (int)value;
+        return TOMO_OK;
+    case TOMO_OPT_PLANE_SYNC:
+        if (value < 0 || value > 3) break;
+        ctx->plane_sync = (int)value;
         return TOMO_OK;
     default:
         return fail(ctx, TOMO_ERR_ARG, "unknown option %d", option);
@@ -437,15 +533,12 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
     DeviceGuard guard(ctx->device);
     if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
-    const int64_t fstride = (int64_t)cube->nx * cube->ny * cube->nz;
-    LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward((const RayRec *)ctx->rays.p,
-                                 (const ImgParam *)ctx->params.p, cube_dev,
-                                 dtype, fstride, n_frames > 1, mask_dev,
-                                 images_dev, img->n_img, img->nu, img->nv,
-                                 cube->nx, cube->nx * cube->ny,
-                                 tiling_for(ctx, cube, img), nullptr, s));
-    return TOMO_OK;
+    const Tiling tl = tiling_for(ctx, cube, img);
+    if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
+        (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
+        return st;
+    return forward_one(ctx, cube_dev, dtype, n_frames, mask_dev, images_dev,
+                       cube, img, tl, nullptr, s);
 }
 
 tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
@@ -473,15 +566,12 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
         CUDA_TRY(ctx, cudaMemsetAsync(cube_dev, 0,
                                       sizeof(float) * fstride * n_frames, s));
     if (img->n_img == 0) return TOMO_OK;
-    if ((st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s))) return st;
-    LAUNCH(ctx, TOMO_K_ADJOINT, s,
-           run_adjoint(ctx, (const RayRec *)ctx->rays.p,
-                       (const ImgParam *)ctx->params.p,
-                       (const Frame *)ctx->frames.p,
-                       (const tomo_pointing *)ctx->ptg.p, images_dev, mask_dev,
-                       cube_dev, cube, n_frames, img,
-                       tiling_for(ctx, cube, img), nullptr, s));
-    return TOMO_OK;
+    const Tiling tl = tiling_for(ctx, cube, img);
+    if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
+        (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
+        return st;
+    return adjoint_one(ctx, images_dev, mask_dev, cube_dev, cube, n_frames,
+                       img, tl, nullptr, s);
 }
 
 tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
@@ -579,8 +669,10 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         (st = ensure(ctx, ctx->partials, sizeof(double) * 2 * kMaxReduceBlocks)) ||
         (st = ensure(ctx, ctx->counter, sizeof(unsigned int))))
         return st;
+    const Tiling tl = tiling_for(ctx, cube, img);
     if (img->n_img > 0 &&
-        (st = prepare_rays(ctx, cube, 1, img, pointing_host, s)))
+        ((st = ensure_plane(ctx, cube, 1, tl)) ||
+         (st = prepare_rays(ctx, cube, 1, img, pointing_host, s))))
         return st;
 
     float *b = (float *)ctx->b.p, *r = (float *)ctx->r.p;
@@ -600,7 +692,6 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const int nxny = cube->nx * cube->ny;
     const float lam = (float)lambda;
     const int grid = reduce_grid(ctx, n > m ? n : m);
-    const Tiling tl = tiling_for(ctx, cube, img);
 
     CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
     CUDA_TRY(ctx, cudaMemsetAsync(S, 0, sizeof(double) * S_NSLOTS, s));
@@ -611,21 +702,17 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                           S, grid, s));
     }
     CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
-    if (m > 0)
-        LAUNCH(ctx, TOMO_K_ADJOINT, s,
-               run_adjoint(ctx, rays, prm, frames, ptgd, y_dev, mask_dev, b, cube, 1, img,
-                           tl, nullptr, s));
+    if (m > 0 &&
+        (st = adjoint_one(ctx, y_dev, mask_dev, b, cube, 1, img, tl, nullptr, s)))
+        return st;
     if (flags & TOMO_SOLVE_X0) {
         // r0 = b - (P^T M P + lambda D^T D) x0
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, q, lam, false, nullptr, s));
-        if (m > 0) {
-            LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward(rays, prm, x_dev, TOMO_F32, n, false,
-                                         mask_dev, t, img->n_img, img->nu,
-                                         img->nv, cube->nx, nxny, tl, nullptr, s));
-            LAUNCH(ctx, TOMO_K_ADJOINT, s,
-                   run_adjoint(ctx, rays, prm, frames, ptgd, t, mask_dev, q, cube, 1, img,
-                               tl, nullptr, s));
-        }
+        if (m > 0 &&
+            ((st = forward_one(ctx, x_dev, TOMO_F32, 1, mask_dev, t, cube, img,
+                               tl, nullptr, s)) ||
+             (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, nullptr, s))))
+            return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, n, tol * tol,
                                      partials, counter, S, report, grid, s));
     } else {
@@ -638,15 +725,14 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const tomo_dtype p_dtype = bf16 ? TOMO_BF16 : TOMO_F32;
     for (int32_t k = 0; k < max_iter; ++k) {
         // q = (P^T M P + lambda D^T D) p
-        if (m > 0)
-            LAUNCH(ctx, TOMO_K_FORWARD, s, launch_forward(rays, prm, p_gather, p_dtype, n, false,
-                                         mask_dev, t, img->n_img, img->nu,
-                                         img->nv, cube->nx, nxny, tl, done, s));
+        if (m > 0 &&
+            (st = forward_one(ctx, p_gather, p_dtype, 1, mask_dev, t, cube, img,
+                              tl, done, s)))
+            return st;
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, q, lam, false, done, s));
-        if (m > 0)
-            LAUNCH(ctx, TOMO_K_ADJOINT, s,
-                   run_adjoint(ctx, rays, prm, frames, ptgd, t, mask_dev, q, cube, 1, img,
-                               tl, done, s));
+        if (m > 0 &&
+            (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, done, s)))
+            return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, n, partials, counter,
                                        S, report, grid, s));

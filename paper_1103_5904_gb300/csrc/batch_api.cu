@@ -192,7 +192,7 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_frames((const tomo_pointing *)P->ptg.p + P->img_off[i],
                              p.img.n_img, p.img.nu, p.img.nv, 1, fr, tu, tv, pr,
-                             s));
+                             nullptr, s));
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_ray_setup(fr, tu, tv, cube_dev(&p.cube), p.img.n_img,
                                 p.img.nu, p.img.nv,

@@ -37,6 +37,7 @@ struct tomo_ctx {
     char err[512] = { 0 };
     bool ray_cache = true;
     int adjoint_mode = 0;  // 0: float atomics; 1: bundle window; 2: tiles
+    int plane_sync = 1;  // bit 0: P^T, bit 1: P walk plane-synchronously
     tomo::Tiling tiling = { 32, 8, 8 };
     // geometry cache
     bool key_valid = false;
@@ -44,6 +45,10 @@ struct tomo_ctx {
     cudaEvent_t setup_done = nullptr;
     // per-geometry buffers
     tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
+    // bit L set: some image of the cached geometry walks in layout L
+    tomo::host::DevBuf layout_used;
+    // cube copies (forward) / accumulators (transpose) in layouts 1 and 2
+    tomo::host::DevBuf lay1, lay2;
     // solver workspace
     tomo::host::DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
     // tuned tile shapes per problem size, and the cached batch plan
@@ -87,6 +92,22 @@ cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
                         const tomo_cube_geom *c, int32_t n_frames,
                         const tomo_image_geom *g, Tiling t, const double *done,
                         cudaStream_t s);
+// Single-problem P and P^T with the context's walk: plane-synchronous
+// (layout copies + plane kernels) when enabled and supported, else the
+// per-ray kernels.  ensure_plane must have succeeded for the problem first.
+bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
+               bool forward);
+tomo_status ensure_plane(tomo_ctx *ctx, const tomo_cube_geom *c,
+                         int32_t n_frames, Tiling t);
+tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
+                        int32_t n_frames, const uint8_t *mask, float *out,
+                        const tomo_cube_geom *c, const tomo_image_geom *g,
+                        Tiling t, const double *done, cudaStream_t s);
+tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
+                        const uint8_t *mask, float *cube,
+                        const tomo_cube_geom *c, int32_t n_frames,
+                        const tomo_image_geom *g, Tiling t,
+                        const double *done, cudaStream_t s);
 // Builds (or reuses) the context's ray records for one geometry on `s`.
 tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          int32_t n_frames, const tomo_image_geom *g,

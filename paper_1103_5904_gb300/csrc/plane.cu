@@ -1,0 +1,552 @@
+// Plane-synchronous Siddon walk: P and P^T with the 32 rays of a warp
+// crossing the cube one plane of the image's major axis at a time, on a copy
+// of the cube stored with the image's lateral axis fastest.
+//
+// The operator is the one of siddon.cu (Section 3.3.1, Eq. lo: pixel k
+// receives g sum_j P_{k,j} x_j, P_{k,j} the length of its line of sight in
+// voxel j; P^T spreads g y_k back with the same lengths).  Only the order in
+// which the lanes of a warp visit their segments differs.
+//
+// Why: in the per-ray walk the lanes of a warp advance one segment per
+// iteration.  Neighbouring rays cross the planes of the two minor axes at
+// different iterations, so after a few voxels they sit at different depths
+// along the line of sight and their voxels fall in different 32-byte
+// sectors.  L2 float reductions are processed per sector (a warp reducing
+// into eight consecutive floats per sector runs about six times faster on
+// GB300 than one reducing into scattered floats), and L1 serves gathers one
+// sector per wavefront, so both directions of the projector pay per sector.
+//
+// Here the lanes of a warp hold one row of pixels of one image.  The warp
+// walks all its rays through the same plane of the image's major axis M (the
+// axis along which the central line of sight advances fastest) in the same
+// iteration: iteration i handles, for every lane, the slab between the
+// (i-1)-th and i-th M planes counted from the warp's first plane.  Inside a
+// slab a ray whose M component is strictly the largest crosses each minor
+// axis at most once, so a slab holds one to three segments, handled
+// branch-free.  At a fixed M plane, neighbouring pixels of a row sit at
+// neighbouring voxels along one lateral axis L; with the cube copied so that
+// L is the fastest axis, the 32 segments of a warp iteration fall in two or
+// three sectors.
+//
+// Exactness: every crossing parameter is computed as in the per-ray walk,
+// fmaf(k, |dt_a|, t0_a), and ends at the chord the setup kernel capped to
+// the last in-cube plane of every axis; each segment is the difference of
+// two consecutive crossings, so segment lengths equal the per-ray walk's.
+// Only a zero-length segment at an exact tie may be charged to an adjacent
+// voxel, which changes no sum.  Rays that do not fit the scheme take the
+// per-ray walk on the native layout: rays of an image without a plane hint,
+// rays whose M direction differs from the image's, and rays for which a
+// minor axis is as steep as M within rounding (two of its crossings could
+// then fall in one slab).
+//
+// Cube layouts (index of voxel (x, y, z); n? = voxel counts):
+//   0  x fastest (native):  x + nx (y + ny z)
+//   1  y fastest:           y + ny (x + nx z)
+//   2  z fastest:           z + nz (x + nx y)
+#include <limits.h>
+#include <math.h>
+
+#include "walk.cuh"
+
+namespace tomo {
+
+namespace {
+
+// One ray, re-expressed for the plane walk: M first, then the two minor
+// axes, a1 the one with the smaller crossing spacing (crossed more often).
+struct PlaneRay {
+    float t0M, t01, t02;  // first crossings
+    float AM, A1, A2;     // crossing spacings
+    float chord;
+    int sM, s1, s2;       // signed strides in the image's layout
+    int idx;              // entry voxel in the image's layout
+    int key;              // entry M coordinate, signed by the M direction
+};
+
+__device__ __forceinline__ void layout_strides(int L, int nx, int ny, int nz,
+                                               int &stx, int &sty, int &stz)
+{
+    if (L == 1) {
+        stx = ny;
+        sty = 1;
+        stz = nx * ny;
+    } else if (L == 2) {
+        stx = nz;
+        sty = nx * nz;
+        stz = 1;
+    } else {
+        stx = 1;
+        sty = nx;
+        stz = nx * ny;
+    }
+}
+
+// Fills p and returns true when the ray fits the plane walk of its image.
+__device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
+                                          int ny, int nz, PlaneRay &p)
+{
+    if (!(hint & kPlaneHintValid)) return false;
+    const int M = hint & 3, L = (hint >> 2) & 3;
+    const bool neg = (hint >> 4) & 1;
+    const int cx = r.idx0 % nx;
+    const int rest = r.idx0 / nx;
+    const int cy = rest % ny, cz = rest / ny;
+    int stx, sty, stz;
+    layout_strides(L, nx, ny, nz, stx, sty, stz);
+    const int gx = signbit(r.dtx) ? -stx : stx;
+    const int gy = signbit(r.dty) ? -sty : sty;
+    const int gz = signbit(r.dtz) ? -stz : stz;
+    const float dM = M == 0 ? r.dtx : (M == 1 ? r.dty : r.dtz);
+    p.t0M = M == 0 ? r.t0x : (M == 1 ? r.t0y : r.t0z);
+    p.t01 = M == 0 ? r.t0y : r.t0x;
+    p.t02 = M == 2 ? r.t0y : r.t0z;
+    p.AM = fabsf(dM);
+    p.A1 = fabsf(M == 0 ? r.dty : r.dtx);
+    p.A2 = fabsf(M == 2 ? r.dty : r.dtz);
+    p.sM = M == 0 ? gx : (M == 1 ? gy : gz);
+    p.s1 = M == 0 ? gy : gx;
+    p.s2 = M == 2 ? gy : gz;
+    // a1 = the minor axis crossed more often (spacing 0: never crossed)
+    if (p.A2 != 0.0f && (p.A1 == 0.0f || p.A2 < p.A1)) {
+        float f = p.t01;
+        p.t01 = p.t02;
+        p.t02 = f;
+        f = p.A1;
+        p.A1 = p.A2;
+        p.A2 = f;
+        const int g = p.s1;
+        p.s1 = p.s2;
+        p.s2 = g;
+    }
+    p.chord = r.chord;
+    p.idx = cx * stx + cy * sty + cz * stz;
+    const int cM = M == 0 ? cx : (M == 1 ? cy : cz);
+    p.key = neg ? -cM : cM;
+    // Two crossings of a minor axis in one slab need its crossing spacing,
+    // less rounding of two crossing parameters (each <= 2^-24 of a value of
+    // at most chord + spacing), below the slab length plus the same: the
+    // margin below is eight times that bound.
+    const float margin = ldexpf(p.chord + fmaxf(p.A1, p.A2) + p.AM, -19);
+    const bool ok1 = p.A1 == 0.0f || p.A1 > p.AM + margin;
+    const bool ok2 = p.A2 == 0.0f || p.A2 > p.AM + margin;
+    return p.AM > 0.0f && (signbit(dM) != 0) == neg && ok1 && ok2;
+}
+
+// Walks the regular lanes of the warp plane by plane; op(idx, len) is called
+// for every segment (len may be 0 at ties).  Every lane of the warp must call
+// this (it uses warp-wide votes); lanes with regular == false only vote.
+//
+// Most slabs hold no crossing of the less steep minor axis a2 (for a view
+// near the ecliptic, a2 is z and is crossed every few tens of slabs): when
+// no lane of the warp crosses a2 in the current slab, the warp takes a fast
+// path with at most one crossing (of a1); otherwise every lane takes the
+// general three-segment body.  Both give the same segments.
+template <class Op>
+__device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
+                                           Op &op)
+{
+    const unsigned full = 0xffffffffu;
+    const int kmin = __reduce_min_sync(full, regular ? p.key : INT_MAX);
+    int wait = regular ? p.key - kmin : 0;
+    bool pending = regular;
+    float t = 0.0f, kM = 0.0f, k1 = 0.0f, k2 = 0.0f;
+    float t1 = p.t01, t2 = p.t02;
+    int idx = p.idx;
+    while (__any_sync(full, pending)) {
+        const bool go = pending && wait <= 0;
+        --wait;
+        const float te = fminf(fmaf(kM, p.AM, p.t0M), p.chord);
+        if (__any_sync(full, go && t2 < te)) {
+            if (go) {
+                const bool first1 = t1 <= t2;
+                const float ta = first1 ? t1 : t2;
+                const float tb = first1 ? t2 : t1;
+                const int sa = first1 ? p.s1 : p.s2;
+                op(idx, fminf(ta, te) - t);
+                if (ta < te) op(idx + sa, fminf(tb, te) - ta);
+                if (tb < te) op(idx + p.s1 + p.s2, te - tb);
+                if (t1 < te) {
+                    k1 += 1.0f;
+                    t1 = fmaf(k1, p.A1, p.t01);
+                    idx += p.s1;
+                }
+                if (t2 < te) {
+                    k2 += 1.0f;
+                    t2 = fmaf(k2, p.A2, p.t02);
+                    idx += p.s2;
+                }
+            }
+        } else if (go) {
+            op(idx, fminf(t1, te) - t);
+            if (t1 < te) {
+                op(idx + p.s1, te - t1);
+                k1 += 1.0f;
+                t1 = fmaf(k1, p.A1, p.t01);
+                idx += p.s1;
+            }
+        }
+        if (go) {
+            if (te < p.chord) {
+                kM += 1.0f;
+                idx += p.sM;
+                t = te;
+            } else {
+                pending = false;
+            }
+        }
+    }
+}
+
+struct PlaneScatterOp {
+    float *c;
+    float y;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        if (len > 0.0f) atomicAdd(c + idx, len * y);
+    }
+};
+
+struct PlaneScatterTimeOp {
+    float *c0;
+    float *c1;
+    float y0, y1;
+    __device__ __forceinline__ void operator()(int idx, float len)
+    {
+        if (len > 0.0f) {
+            atomicAdd(c0 + idx, len * y0);
+            atomicAdd(c1 + idx, len * y1);
+        }
+    }
+};
+
+template <typename CubeT, bool kTime>
+__global__ void __launch_bounds__(256)
+k_forward_plane(const RayRec *__restrict__ rays,
+                const ImgParam *__restrict__ prm, PlaneCubes cubes,
+                int64_t frame_stride, const uint8_t *__restrict__ mask,
+                float *__restrict__ out, int nu, int nv, int nx, int ny,
+                int nz, Tiling tl, const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    int iu, iv;
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
+    const int img = blockIdx.z;
+    const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
+    const ImgParam q = prm[img];
+    RayRec r;
+    r.chord = -1.0f;
+    if (in_img && (mask == nullptr || mask[id] == 0)) r = load_ray(rays + id);
+    const bool live = r.chord > 0.0f;
+    PlaneRay p;
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const int L = (q.pad >> 2) & 3;
+    const CubeT *native = static_cast<const CubeT *>(cubes.c[0]);
+    const CubeT *lay = static_cast<const CubeT *>(
+        L == 1 ? cubes.c[1] : (L == 2 ? cubes.c[2] : cubes.c[0]));
+    const int64_t f0 = kTime ? (int64_t)q.frame * frame_stride : 0;
+    float acc = 0.0f;
+    if (kTime) {
+        GatherTimeOp<CubeT> op;
+        op.c0 = lay + f0;
+        op.c1 = op.c0 + frame_stride;
+        op.w0 = 1.0f - q.w;
+        op.w1 = q.w;
+        op.acc = 0.0f;
+        plane_walk(p, regular, op);
+        if (live && !regular) {
+            op.c0 = native + f0;
+            op.c1 = op.c0 + frame_stride;
+            siddon_walk(r, nx, nx * ny, op);
+        }
+        acc = op.acc;
+    } else {
+        GatherOp<CubeT> op;
+        op.c = lay;
+        op.acc = 0.0f;
+        plane_walk(p, regular, op);
+        if (live && !regular) {
+            op.c = native;
+            siddon_walk(r, nx, nx * ny, op);
+        }
+        acc = op.acc;
+    }
+    if (in_img) out[id] = q.gain * acc;
+}
+
+template <bool kTime>
+__global__ void __launch_bounds__(256)
+k_adjoint_plane(const RayRec *__restrict__ rays,
+                const ImgParam *__restrict__ prm,
+                const float *__restrict__ images,
+                const uint8_t *__restrict__ mask, PlaneAcc acc,
+                int64_t frame_stride, int nu, int nv, int nx, int ny, int nz,
+                Tiling tl, const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    int iu, iv;
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
+    const int img = blockIdx.z;
+    const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
+    const ImgParam q = prm[img];
+    RayRec r;
+    r.chord = -1.0f;
+    float yv = 0.0f;
+    if (in_img && (mask == nullptr || mask[id] == 0)) {
+        yv = q.gain * images[id];
+        if (yv != 0.0f) r = load_ray(rays + id);
+    }
+    const bool live = r.chord > 0.0f;
+    PlaneRay p;
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const int L = (q.pad >> 2) & 3;
+    float *lay = L == 1 ? acc.c[1] : (L == 2 ? acc.c[2] : acc.c[0]);
+    const int64_t f0 = kTime ? (int64_t)q.frame * frame_stride : 0;
+    if (kTime) {
+        PlaneScatterTimeOp op;
+        op.c0 = lay + f0;
+        op.c1 = op.c0 + frame_stride;
+        op.y0 = yv * (1.0f - q.w);
+        op.y1 = yv * q.w;
+        plane_walk(p, regular, op);
+        if (live && !regular) {
+            ScatterTimeOp op2;
+            op2.c0 = acc.c[0] + f0;
+            op2.c1 = op2.c0 + frame_stride;
+            op2.y0 = op.y0;
+            op2.y1 = op.y1;
+            siddon_walk(r, nx, nx * ny, op2);
+        }
+    } else {
+        PlaneScatterOp op;
+        op.c = lay;
+        op.y = yv;
+        plane_walk(p, regular, op);
+        if (live && !regular) {
+            ScatterOp op2;
+            op2.c = acc.c[0];
+            op2.y = yv;
+            siddon_walk(r, nx, nx * ny, op2);
+        }
+    }
+}
+
+// Layout copies.  Layout L (1 or 2) makes axis b (y or z) the fastest; c is
+// the remaining axis (z or y).  Native index: x + sb b + sc c; layout index:
+// b + nb (x + nx c).  One CTA moves a 32 x 32 (x, b) tile through shared
+// memory so that both the native reads (along x) and the layout writes
+// (along b) are coalesced.
+struct LayoutMap {
+    int nx, nb, nc;
+    int64_t sb, sc;
+};
+
+LayoutMap layout_map(int L, int nx, int ny, int nz)
+{
+    LayoutMap m;
+    m.nx = nx;
+    if (L == 1) {
+        m.nb = ny;
+        m.nc = nz;
+        m.sb = nx;
+        m.sc = (int64_t)nx * ny;
+    } else {
+        m.nb = nz;
+        m.nc = ny;
+        m.sb = (int64_t)nx * ny;
+        m.sc = nx;
+    }
+    return m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_to_layout(const T *__restrict__ in, T *__restrict__ out, LayoutMap m,
+            int n_frames, int64_t fstride, const unsigned *__restrict__ used,
+            unsigned bit, const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    if (!(*used & bit)) return;
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, b0 = blockIdx.y * 32, c = blockIdx.z;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int f = 0; f < n_frames; ++f) {
+        const T *src = in + f * fstride;
+        T *dst = out + f * fstride;
+        for (int k = ty; k < 32; k += 8) {
+            const int b = b0 + k, x = x0 + tx;
+            if (b < m.nb && x < m.nx) tile[k][tx] = src[x + m.sb * b + m.sc * c];
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += 8) {
+            const int x = x0 + k, b = b0 + tx;
+            if (b < m.nb && x < m.nx)
+                dst[b + (int64_t)m.nb * (x + (int64_t)m.nx * c)] = tile[tx][k];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_add_from_layout(const float *__restrict__ acc, float *__restrict__ out,
+                  LayoutMap m, int n_frames, int64_t fstride,
+                  const unsigned *__restrict__ used, unsigned bit,
+                  const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    if (!(*used & bit)) return;
+    __shared__ float tile[32][33];
+    const int x0 = blockIdx.x * 32, b0 = blockIdx.y * 32, c = blockIdx.z;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int f = 0; f < n_frames; ++f) {
+        const float *src = acc + f * fstride;
+        float *dst = out + f * fstride;
+        for (int k = ty; k < 32; k += 8) {
+            const int x = x0 + k, b = b0 + tx;
+            if (b < m.nb && x < m.nx)
+                tile[tx][k] = src[b + (int64_t)m.nb * (x + (int64_t)m.nx * c)];
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += 8) {
+            const int b = b0 + k, x = x0 + tx;
+            if (b < m.nb && x < m.nx) dst[x + m.sb * b + m.sc * c] += tile[k][tx];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_zero_layout(float *__restrict__ p, int64_t n, const unsigned *__restrict__ used,
+              unsigned bit, const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    if (!(*used & bit)) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        p[i] = 0.0f;
+}
+
+// 32 x 8 pixels per CTA, one row of 32 pixels per warp
+constexpr Tiling kPlaneTiling = { 32, 8, 32 };
+
+dim3 plane_grid(int nu, int nv, int n_img)
+{
+    const Tiling t = kPlaneTiling;
+    return dim3((unsigned)((nu + t.tile_u - 1) / t.tile_u),
+                (unsigned)((nv + t.tile_v - 1) / t.tile_v), (unsigned)n_img);
+}
+
+dim3 layout_grid(const LayoutMap &m)
+{
+    return dim3((unsigned)((m.nx + 31) / 32), (unsigned)((m.nb + 31) / 32),
+                (unsigned)m.nc);
+}
+
+}  // namespace
+
+bool plane_supported(const tomo_cube_geom *c)
+{
+    // layout copies index (x, b) tiles with a grid of at most 65535 in y and z
+    return c->nx <= kPlaneMaxSide && c->ny <= kPlaneMaxSide &&
+           c->nz <= kPlaneMaxSide;
+}
+
+cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
+                             int L, const tomo_cube_geom *c, int32_t n_frames,
+                             const unsigned *used, const double *done,
+                             cudaStream_t s)
+{
+    const LayoutMap m = layout_map(L, c->nx, c->ny, c->nz);
+    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+    if (dtype == TOMO_BF16)
+        k_to_layout<uint16_t><<<layout_grid(m), 256, 0, s>>>(
+            static_cast<const uint16_t *>(cube), static_cast<uint16_t *>(out),
+            m, n_frames, fstride, used, 1u << L, done);
+    else
+        k_to_layout<float><<<layout_grid(m), 256, 0, s>>>(
+            static_cast<const float *>(cube), static_cast<float *>(out), m,
+            n_frames, fstride, used, 1u << L, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_from_layout(const float *acc, float *cube, int L,
+                                   const tomo_cube_geom *c, int32_t n_frames,
+                                   const unsigned *used, const double *done,
+                                   cudaStream_t s)
+{
+    const LayoutMap m = layout_map(L, c->nx, c->ny, c->nz);
+    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+    k_add_from_layout<<<layout_grid(m), 256, 0, s>>>(acc, cube, m, n_frames,
+                                                     fstride, used, 1u << L,
+                                                     done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_layout(float *acc, int L, int64_t n,
+                               const unsigned *used, const double *done,
+                               int num_sms, cudaStream_t s)
+{
+    int64_t g = (n + 255) / 256;
+    const int64_t cap = 8LL * (num_sms > 0 ? num_sms : 152);
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    k_zero_layout<<<(unsigned)g, 256, 0, s>>>(acc, n, used, 1u << L, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
+                                 PlaneCubes cubes, tomo_dtype dtype,
+                                 int64_t frame_stride, bool time_interp,
+                                 const uint8_t *mask, float *out,
+                                 int32_t n_img, int32_t nu, int32_t nv,
+                                 const tomo_cube_geom *c, const double *done,
+                                 cudaStream_t s)
+{
+    if (n_img <= 0) return cudaSuccess;
+    const Tiling t = kPlaneTiling;
+    const dim3 grid = plane_grid(nu, nv, n_img);
+    const int block = t.tile_u * t.tile_v;
+    if (dtype == TOMO_BF16) {
+        if (time_interp)
+            k_forward_plane<uint16_t, true><<<grid, block, 0, s>>>(
+                rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
+                c->ny, c->nz, t, done);
+        else
+            k_forward_plane<uint16_t, false><<<grid, block, 0, s>>>(
+                rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
+                c->ny, c->nz, t, done);
+    } else {
+        if (time_interp)
+            k_forward_plane<float, true><<<grid, block, 0, s>>>(
+                rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
+                c->ny, c->nz, t, done);
+        else
+            k_forward_plane<float, false><<<grid, block, 0, s>>>(
+                rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
+                c->ny, c->nz, t, done);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_plane(const RayRec *rays, const ImgParam *prm,
+                                 const float *images, const uint8_t *mask,
+                                 PlaneAcc acc, int64_t frame_stride,
+                                 bool time_interp, int32_t n_img, int32_t nu,
+                                 int32_t nv, const tomo_cube_geom *c,
+                                 const double *done, cudaStream_t s)
+{
+    if (n_img <= 0) return cudaSuccess;
+    const Tiling t = kPlaneTiling;
+    const dim3 grid = plane_grid(nu, nv, n_img);
+    const int block = t.tile_u * t.tile_v;
+    if (time_interp)
+        k_adjoint_plane<true><<<grid, block, 0, s>>>(
+            rays, prm, images, mask, acc, frame_stride, nu, nv, c->nx, c->ny,
+            c->nz, t, done);
+    else
+        k_adjoint_plane<false><<<grid, block, 0, s>>>(
+            rays, prm, images, mask, acc, frame_stride, nu, nv, c->nx, c->ny,
+            c->nz, t, done);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

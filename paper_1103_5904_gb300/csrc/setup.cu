@@ -21,11 +21,41 @@ namespace tomo {
 
 namespace {
 
+// Hint for the plane-synchronous walk of one image: M = the axis along
+// which the line of sight of the image centre advances fastest, its
+// direction, and L = the axis (other than M) along which neighbouring pixels
+// of a row move at a fixed M plane.  Moving along the row turns the
+// direction by ~e1; at a fixed M plane the ray through u + e1 d is displaced
+// along e1 - u e1_M / u_M.  Only the walk's speed depends on the hint.
+__device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
+                              int nv)
+{
+    const double tu = tan((0.5 * (nu - 1) - p.crpix_u) * p.cdelt_u + p.crval_u);
+    const double tv = tan((0.5 * (nv - 1) - p.crpix_v) * p.cdelt_v + p.crval_v);
+    double u[3];
+    for (int a = 0; a < 3; ++a) u[a] = f.w[a] + tu * f.e1[a] + tv * f.e2[a];
+    int M = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(u[a]) > fabs(u[M])) M = a;
+    int L = -1;
+    double best = -1.0;
+    for (int a = 0; a < 3; ++a) {
+        if (a == M) continue;
+        const double lat = fabs(f.e1[a] - u[a] * f.e1[M] / u[M]);
+        if (lat > best) {
+            best = lat;
+            L = a;
+        }
+    }
+    return kPlaneHintValid | M | (L << 2) | ((u[M] < 0.0) ? 16 : 0);
+}
+
 // One block per image: the FP64 frame, the image parameters and the tangent
 // tables tan(theta_u), tan(theta_v) (one value per column / row).
 __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
                          int32_t nv, int32_t n_frames, Frame *frames,
-                         double *tan_u, double *tan_v, ImgParam *params)
+                         double *tan_u, double *tan_v, ImgParam *params,
+                         unsigned *layout_used)
 {
     const int img = blockIdx.x;
     const tomo_pointing p = ptg[img];
@@ -53,7 +83,8 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
         frames[img] = f;
         ImgParam q;
         q.gain = (float)p.gain;
-        q.pad = 0;
+        q.pad = plane_hint(p, f, nu, nv);
+        if (layout_used) atomicOr(layout_used, 1u << ((q.pad >> 2) & 3));
         if (n_frames > 1) {
             int k = (int)floor(p.time);
             if (k > n_frames - 2) k = n_frames - 2;
@@ -157,11 +188,12 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
-                          ImgParam *params, cudaStream_t s)
+                          ImgParam *params, unsigned *layout_used,
+                          cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
     k_frames<<<n_img, 128, 0, s>>>(ptg_dev, nu, nv, n_frames, frames, tan_u,
-                                   tan_v, params);
+                                   tan_v, params, layout_used);
     return cudaGetLastError();
 }
 

@@ -33,7 +33,21 @@ struct __align__(16) ImgParam {
     float gain;     // image gain g_n
     float w;        // weight of frame k + 1
     int32_t frame;  // k (0 when T == 1)
-    int32_t pad;
+    int32_t pad;    // plane-walk hint: bits 0-1 major axis M, bits 2-3
+                    // lateral axis L (the layout), bit 4 M direction < 0,
+                    // bit 5 set when the hint is valid
+};
+
+constexpr int32_t kPlaneHintValid = 32;
+constexpr int32_t kPlaneMaxSide = 16384;
+
+// Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
+// 2 = z-fastest) for the plane-synchronous walk (plane.cu).
+struct PlaneCubes {
+    const void *c[3];
+};
+struct PlaneAcc {
+    float *c[3];
 };
 
 struct Frame {
@@ -68,10 +82,13 @@ enum : int {
 constexpr int kMaxReduceBlocks = 2048;
 
 // ---- setup.cu
+// layout_used (may be NULL): bit L is or-ed in for every image whose plane
+// hint names layout L
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
-                          ImgParam *params, cudaStream_t s);
+                          ImgParam *params, unsigned *layout_used,
+                          cudaStream_t s);
 cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
                              const double *tan_v, CubeDev cube, int32_t n_img,
                              int32_t nu, int32_t nv, RayRec *rays,
@@ -107,6 +124,35 @@ cudaError_t launch_adjoint_tiled(const RayRec *rays, const ImgParam *prm,
                                  float *cube, CubeDev c, int32_t n_img,
                                  int32_t nu, int32_t nv, const double *done,
                                  cudaStream_t s);
+// plane.cu: plane-synchronous walk on lateral-axis-fastest cube copies.
+// The walk kernels use their own tiling: CTAs of 32 x 8 pixels, one image
+// row of 32 pixels per warp.  Layout kernels return at once unless bit L of
+// *used is set.
+bool plane_supported(const tomo_cube_geom *c);
+cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
+                             int L, const tomo_cube_geom *c, int32_t n_frames,
+                             const unsigned *used, const double *done,
+                             cudaStream_t s);
+cudaError_t launch_add_from_layout(const float *acc, float *cube, int L,
+                                   const tomo_cube_geom *c, int32_t n_frames,
+                                   const unsigned *used, const double *done,
+                                   cudaStream_t s);
+cudaError_t launch_zero_layout(float *acc, int L, int64_t n,
+                               const unsigned *used, const double *done,
+                               int num_sms, cudaStream_t s);
+cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
+                                 PlaneCubes cubes, tomo_dtype dtype,
+                                 int64_t frame_stride, bool time_interp,
+                                 const uint8_t *mask, float *out,
+                                 int32_t n_img, int32_t nu, int32_t nv,
+                                 const tomo_cube_geom *c, const double *done,
+                                 cudaStream_t s);
+cudaError_t launch_adjoint_plane(const RayRec *rays, const ImgParam *prm,
+                                 const float *images, const uint8_t *mask,
+                                 PlaneAcc acc, int64_t frame_stride,
+                                 bool time_interp, int32_t n_img, int32_t nu,
+                                 int32_t nv, const tomo_cube_geom *c,
+                                 const double *done, cudaStream_t s);
 cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
                          int32_t n_img, int32_t nu, int32_t nv, Tiling t,
                          unsigned long long *count, cudaStream_t s);

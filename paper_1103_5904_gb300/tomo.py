@@ -27,8 +27,9 @@ TOMO_ACCUMULATE, TOMO_SOLVE_X0, TOMO_SOLVE_BF16 = 1, 2, 4
 TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3, 4
 TOMO_OPT_PROFILE = 5
 TOMO_OPT_ADJOINT = 6
+TOMO_OPT_PLANE_SYNC = 7
 TOMO_BATCH_AUTOTUNE = 8
-KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector")
+KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector", "layout")
 
 STATUS = {0: "TOMO_OK", -1: "TOMO_ERR_ARG", -2: "TOMO_ERR_CUDA",
           -3: "TOMO_ERR_UNSUPPORTED", -4: "TOMO_ERR_OOM",
@@ -53,7 +54,8 @@ class Pointing(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5)]
+    _fields_ = [("launches", C.c_int64 * len(KERNEL_CLASSES)),
+                ("ms", C.c_double * len(KERNEL_CLASSES))]
 
 
 class Problem(C.Structure):

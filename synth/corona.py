@@ -13,11 +13,14 @@ Recipes (seeded; all in solar radii):
 * multiplicative uniform noise: ``x * (1 + f * U[-1, 1))``, which keeps the
   solar interior at zero.
 
-Cubes are produced in float64 slab by slab and returned rounded to float32,
-the precision the projector stores them in.
+Cubes are produced in float64 slab by slab (torch CPU operations, which run
+on every host core) and returned rounded to float32, the precision the
+projector stores them in.  ``radial_exp``, ``radial_power`` and
+``add_structures`` evaluate the same recipes on numpy arrays of points.
 """
 
 import numpy as np
+import torch
 
 from .geometry import voxel_centres
 
@@ -75,52 +78,75 @@ def uniform_noise(x, rng, frac):
     return x * (1.0 + frac * rng.uniform(-1.0, 1.0, size=x.shape))
 
 
-def corona_frames(geom, axes, width, amps, background="exp", slab=16):
+def _grid(geom, z0, z1):
+    """Broadcastable float64 voxel-centre coordinates of slab z0:z1."""
+    xs = torch.from_numpy(voxel_centres(geom, "x"))
+    ys = torch.from_numpy(voxel_centres(geom, "y"))
+    zs = torch.from_numpy(voxel_centres(geom, "z")[z0:z1])
+    return xs.view(1, 1, -1), ys.view(1, -1, 1), zs.view(-1, 1, 1)
+
+
+def _background(name, r):
+    one = torch.ones((), dtype=r.dtype)
+    if name == "exp":
+        val = torch.exp(-(r - 1.0) / 0.1)
+    else:
+        val = r.pow(-6) + 0.05 * r.pow(-2)
+    return torch.where(r >= one, val, torch.zeros((), dtype=r.dtype))
+
+
+def _profiles(px, py, pz, r2, bg, axes, width):
+    """One radial Gaussian cylinder profile (amplitude 1) per axis."""
+    out = []
+    for a in axes:
+        proj = px * float(a[0]) + py * float(a[1]) + pz * float(a[2])
+        d2 = torch.clamp(r2 - proj * proj, min=0.0)
+        prof = bg * torch.exp(d2 * (-0.5 / (width * width)))
+        out.append(torch.where(proj > 0.0, prof, torch.zeros((), dtype=prof.dtype)))
+    return out
+
+
+def corona_frames(geom, axes, width, amps, background="exp", slab=4):
     """Frames ``[T][nz][ny][nx]`` float32 of a background plus cylinders of
     one ``width`` whose amplitudes change from frame to frame: frame t holds
     ``n_bg + sum_s amps[t][s] * profile_s`` (see :func:`add_structures`)."""
-    bgf = _BACKGROUNDS[background]
     amps = np.asarray(amps, dtype=np.float64)
-    xs = voxel_centres(geom, "x")
-    ys = voxel_centres(geom, "y")
-    zs = voxel_centres(geom, "z")
     nz, ny, nx = geom["nz"], geom["ny"], geom["nx"]
     out = np.empty((amps.shape[0], nz, ny, nx), dtype=np.float32)
     for z0 in range(0, nz, slab):
-        pz, py, px = np.meshgrid(zs[z0:z0 + slab], ys, xs, indexing="ij")
-        bg = bgf(np.sqrt(px * px + py * py + pz * pz))
-        prof = [add_structures(px, py, pz, bg, [a], width, 1.0) for a in axes]
+        px, py, pz = _grid(geom, z0, min(z0 + slab, nz))
+        r2 = px * px + py * py + pz * pz
+        bg = _background(background, torch.sqrt(r2))
+        prof = _profiles(px, py, pz, r2, bg, axes, width)
         for t in range(amps.shape[0]):
-            val = bg.copy()
-            for s, p in enumerate(prof):
-                val += amps[t, s] * p
-            out[t, z0:z0 + slab] = val
+            val = bg.clone()
+            for s_, p_ in enumerate(prof):
+                val += float(amps[t, s_]) * p_
+            out[t, z0:z0 + slab] = val.numpy()
     return out
 
 
 def corona_cube(geom, background="exp", structures=(), noise_frac=0.0,
-                noise_rng=None, slab=16):
+                noise_rng=None, slab=4):
     """Density cube ``[nz][ny][nx]`` float32.
 
     ``structures`` is a sequence of ``(axes, width, amp)`` tuples.  The noise
     draws are taken in one call over the whole cube (C order) so that the
-    result does not depend on ``slab``.
+    result does not depend on ``slab``.  Evaluated in float64 with torch CPU
+    operations (multithreaded), slab by slab.
     """
-    bgf = _BACKGROUNDS[background]
-    xs = voxel_centres(geom, "x")
-    ys = voxel_centres(geom, "y")
-    zs = voxel_centres(geom, "z")
     nz, ny, nx = geom["nz"], geom["ny"], geom["nx"]
     out = np.empty((nz, ny, nx), dtype=np.float64)
     for z0 in range(0, nz, slab):
-        zz = zs[z0:z0 + slab]
-        pz, py, px = np.meshgrid(zz, ys, xs, indexing="ij")
-        r = np.sqrt(px * px + py * py + pz * pz)
-        bg = bgf(r)
-        val = bg.copy()
+        px, py, pz = _grid(geom, z0, min(z0 + slab, nz))
+        r2 = px * px + py * py + pz * pz
+        bg = _background(background, torch.sqrt(r2))
+        val = bg.clone()
         for axes, width, amp in structures:
-            val += add_structures(px, py, pz, bg, axes, width, amp)
-        out[z0:z0 + slab] = val
+            amps = np.broadcast_to(np.asarray(amp, dtype=np.float64), (len(axes),))
+            for am, prof in zip(amps, _profiles(px, py, pz, r2, bg, axes, width)):
+                val += float(am) * prof
+        out[z0:z0 + slab] = val.numpy()
     if noise_frac:
         out = uniform_noise(out, noise_rng, noise_frac)
     return out.astype(np.float32)
