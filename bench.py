@@ -68,6 +68,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--plane-sync", type=int, default=None,
+                    help="walk of P / P^T (TOMO_OPT_PLANE_SYNC bit mask: "
+                         "bit 0 P^T, bit 1 P plane-synchronous; library "
+                         "default 1)")
     ap.add_argument("--adjoint-mode", type=int, default=None,
                     help="transpose kernel (TOMO_OPT_ADJOINT): 0 float "
                          "atomics, 1 bundle window, 2 voxel tiles")
@@ -293,6 +297,8 @@ def run_gpu(args, rank, local_rank, world):
     ctx = T.Context(local_rank)
     if args.adjoint_mode is not None:
         ctx.set_option(T.tomo.TOMO_OPT_ADJOINT, args.adjoint_mode)
+    if args.plane_sync is not None:
+        ctx.set_option(T.tomo.TOMO_OPT_PLANE_SYNC, args.plane_sync)
     mask_h = c["mask"]
     mask = torch.from_numpy(mask_h).to(dev) if mask_h is not None else None
     x_true = torch.from_numpy(c["cube"]).to(dev)
@@ -364,11 +370,18 @@ def run_gpu(args, rank, local_rank, world):
                       "achieved_gbs": b / per_launch_s / 1e9,
                       "time_share": ms / sum(v[1] for v in prof.values())}
     dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    kern["layout"] = {"launches": prof["layout"][0], "ms": prof["layout"][1],
+                      "what": "cube layout copies of the plane-synchronous "
+                              "walk (most return at once when no image "
+                              "uses their layout)"}
     peak, peak_src = peak_hbm()
-    kname = {"forward": "k_forward<float,false>",
-             "adjoint": {None: "k_adjoint<false>", 0: "k_adjoint<false>",
-                         1: "k_adjoint_window",
-                         2: "k_adjoint_tiled"}[args.adjoint_mode]}
+    plane = 1 if args.plane_sync is None else args.plane_sync
+    mode = args.adjoint_mode or 0
+    kname = {"forward": ("k_forward_plane<float,false>" if plane & 2
+                         else "k_forward<float,false>"),
+             "adjoint": ("k_adjoint_plane<false>" if mode == 0 and plane & 1
+                         else {0: "k_adjoint<false>", 1: "k_adjoint_window",
+                               2: "k_adjoint_tiled"}[mode])}
     roofline = {"bound": "hbm", "kernel": kname[dom],
                 "achieved": kern[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,

@@ -208,6 +208,7 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          g->nv, n_frames, (Frame *)ctx->frames.p,
                          (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
                          (ImgParam *)ctx->params.p,
+                         make_double3(c->dx, c->dy, c->dz),
                          (unsigned *)ctx->layout_used.p, s));
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_ray_setup((const Frame *)ctx->frames.p,

@@ -21,7 +21,28 @@ struct WalkDesc {
     int32_t nu, nv, nx, nxny;
     int32_t tiles_u, tiles_v;
     Tiling tl;
-    int32_t pad;
+    int32_t ny, nz;
+    // plane-synchronous transpose: accumulators of layouts 1 and 2 (zero
+    // between transposes; k_add_from_layout_batched adds them to dst and
+    // zeroes them again)
+    float *lay1, *lay2;
+};
+
+// Plane-synchronous batched transpose tiles: 32 x 8 pixels, one image row of
+// 32 pixels per warp.
+constexpr int kPlaneTileU = 32, kPlaneTileV = 8;
+
+// One layout accumulator of one problem, added into that problem's cube by
+// the batched combine kernel in 32 x 32 tiles of (x, b) per value of c
+// (layout L: b = y (L = 1) or z (L = 2), c = the remaining axis).
+struct LayoutJob {
+    float *acc;
+    float *cube;
+    const unsigned *used;  // bit L set: some image of the problem uses L
+    const double *done;    // may be NULL
+    int32_t L, nx, nb, nc;
+    int64_t sb, sc;        // native strides of b and c
+    int32_t tiles_x, tiles_b;
 };
 
 // One problem as seen by the batched vector kernels.
@@ -37,12 +58,24 @@ struct VecDesc {
 };
 
 int walk_batched_blocks_per_sm();
+int plane_batched_blocks_per_sm();
 // sched[c] = (problem, first tile) of chunk c: kSchedGroup consecutive
 // tiles of one problem (tiles past the problem's count are skipped)
 cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,
                                 const int64_t *prefix, const int2 *sched,
                                 int64_t n_chunks, unsigned long long *next_item,
                                 int grid, cudaStream_t s);
+// Plane-synchronous transpose of every problem (work list over plane
+// tiles, same schedule format as launch_walk_batched).
+cudaError_t launch_adjoint_plane_batched(const WalkDesc *descs,
+                                         const int64_t *prefix,
+                                         const int2 *sched, int64_t n_chunks,
+                                         unsigned long long *next_item,
+                                         int grid, cudaStream_t s);
+// cube += acc, acc = 0 for every job; prefix[j] = first tile item of job j
+cudaError_t launch_add_from_layout_batched(const LayoutJob *jobs,
+                                           const int64_t *prefix, int n_jobs,
+                                           int grid, cudaStream_t s);
 cudaError_t launch_vec_batched(int op, const VecDesc *descs,
                                const int64_t *prefix, int n_probs, bool warm,
                                double *partials, int grid, cudaStream_t s);

@@ -31,11 +31,20 @@ struct BatchPlan {
     std::vector<int64_t> tile_prefix;  // n + 1
     DevBuf tpre_dev, sched_dev;        // tile prefix, walk schedule
     int64_t n_chunks = 0;
+    // plane-synchronous transpose: plane-tile prefix and schedule, voxel
+    // offsets, per-problem layout masks, accumulators of layouts 1 and 2
+    // (2 x voxels per problem, zero between transposes), combine-job tile
+    // prefix (jobs: problem i, layout 1 / 2 at 2 i, 2 i + 1)
+    std::vector<int64_t> ptile_prefix, vox_off, job_prefix;
+    DevBuf ptpre_dev, psched_dev, lay, lay_used, jpre_dev;
+    int64_t pn_chunks = 0;
+    bool lay_dirty = false;
     cudaEvent_t ready = nullptr;
     // per-call descriptors of the projector / transpose entry points
-    DevBuf call_desc, call_counter;
+    DevBuf call_desc, call_counter, call_jobs;
     // solver workspace and graph
-    DevBuf vec, timg, S, partials, counters, walk_desc, vec_desc, prefixes;
+    DevBuf vec, timg, S, partials, counters, walk_desc, vec_desc, prefixes,
+        solve_jobs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_launches[TOMO_K_COUNT] = { 0 };
@@ -49,10 +58,11 @@ void free_plan(tomo_ctx *ctx)
     if (!p) return;
     DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
                        &p->rays, &p->tpre_dev, &p->sched_dev,
-                       &p->call_desc, &p->call_counter, &p->vec, &p->timg,
-                       &p->S,
+                       &p->ptpre_dev, &p->psched_dev, &p->lay, &p->lay_used,
+                       &p->jpre_dev, &p->call_desc, &p->call_counter,
+                       &p->call_jobs, &p->vec, &p->timg, &p->S,
                        &p->partials, &p->counters, &p->walk_desc,
-                       &p->vec_desc, &p->prefixes };
+                       &p->vec_desc, &p->prefixes, &p->solve_jobs };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -151,6 +161,9 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
     P->tu_off.assign(n + 1, 0);
     P->tv_off.assign(n + 1, 0);
     P->tile_prefix.assign(n + 1, 0);
+    P->ptile_prefix.assign(n + 1, 0);
+    P->vox_off.assign(n + 1, 0);
+    P->job_prefix.assign(2 * (size_t)n + 1, 0);
     P->tl.assign(n, kDefaultTiling);
     for (int32_t i = 0; i < n; ++i) {
         const tomo_image_geom &g = probs[i].img;
@@ -163,6 +176,18 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                               ((g.nu + P->tl[i].tile_u - 1) / P->tl[i].tile_u) *
                               ((g.nv + P->tl[i].tile_v - 1) / P->tl[i].tile_v);
         P->tile_prefix[i + 1] = P->tile_prefix[i] + tiles;
+        P->ptile_prefix[i + 1] =
+            P->ptile_prefix[i] + (int64_t)g.n_img *
+                                     ((g.nu + kPlaneTileU - 1) / kPlaneTileU) *
+                                     ((g.nv + kPlaneTileV - 1) / kPlaneTileV);
+        const tomo_cube_geom &c = probs[i].cube;
+        P->vox_off[i + 1] = P->vox_off[i] + (int64_t)c.nx * c.ny * c.nz;
+        for (int L = 1; L <= 2; ++L) {
+            const int64_t nb = L == 1 ? c.ny : c.nz, nc = L == 1 ? c.nz : c.ny;
+            const size_t j = 2 * (size_t)i + (L - 1);
+            P->job_prefix[j + 1] = P->job_prefix[j] + ((c.nx + 31) / 32) *
+                                                          ((nb + 31) / 32) * nc;
+        }
     }
     const int64_t n_img = P->img_off[n];
     tomo_status st;
@@ -171,8 +196,13 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         (st = ensure(ctx, P->params, sizeof(ImgParam) * n_img)) ||
         (st = ensure(ctx, P->tan_u, sizeof(double) * P->tu_off[n])) ||
         (st = ensure(ctx, P->tan_v, sizeof(double) * P->tv_off[n])) ||
-        (st = ensure(ctx, P->rays, sizeof(RayRec) * P->ray_off[n])))
+        (st = ensure(ctx, P->rays, sizeof(RayRec) * P->ray_off[n])) ||
+        (st = ensure(ctx, P->lay, sizeof(float) * 2 * (P->vox_off[n] > 0 ? P->vox_off[n] : 1))) ||
+        (st = ensure(ctx, P->lay_used, sizeof(unsigned) * n)))
         return st;
+    CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0, sizeof(float) * 2 * P->vox_off[n], s));
+    CUDA_TRY(ctx, cudaMemsetAsync(P->lay_used.p, 0, sizeof(unsigned) * n, s));
+    P->lay_dirty = false;
     std::vector<tomo_pointing> all((size_t)n_img);
     for (int32_t i = 0; i < n; ++i)
         if (probs[i].img.n_img > 0)
@@ -192,7 +222,8 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_frames((const tomo_pointing *)P->ptg.p + P->img_off[i],
                              p.img.n_img, p.img.nu, p.img.nv, 1, fr, tu, tv, pr,
-                             nullptr, s));
+                             make_double3(p.cube.dx, p.cube.dy, p.cube.dz),
+                             (unsigned *)P->lay_used.p + i, s));
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_ray_setup(fr, tu, tv, cube_dev(&p.cube), p.img.n_img,
                                 p.img.nu, p.img.nv,
@@ -213,10 +244,30 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         }
     }
     P->n_chunks = (int64_t)sched.size();
+    // the same for the plane tiles of the plane-synchronous transpose
+    std::vector<int2> psched;
+    next.assign(n, 0);
+    for (bool any = true; any;) {
+        any = false;
+        for (int32_t i = 0; i < n; ++i) {
+            if (next[i] < P->ptile_prefix[i + 1] - P->ptile_prefix[i]) {
+                psched.push_back(make_int2(i, (int)next[i]));
+                next[i] += kSchedGroup;
+                any = true;
+            }
+        }
+    }
+    P->pn_chunks = (int64_t)psched.size();
     if ((st = upload(ctx, P->tpre_dev, P->tile_prefix.data(),
                      sizeof(int64_t) * (n + 1), s)) ||
         (st = upload(ctx, P->sched_dev, sched.data(),
-                     sizeof(int2) * (sched.empty() ? 1 : sched.size()), s)))
+                     sizeof(int2) * (sched.empty() ? 1 : sched.size()), s)) ||
+        (st = upload(ctx, P->ptpre_dev, P->ptile_prefix.data(),
+                     sizeof(int64_t) * (n + 1), s)) ||
+        (st = upload(ctx, P->psched_dev, psched.data(),
+                     sizeof(int2) * (psched.empty() ? 1 : psched.size()), s)) ||
+        (st = upload(ctx, P->jpre_dev, P->job_prefix.data(),
+                     sizeof(int64_t) * P->job_prefix.size(), s)))
         return st;
     CUDA_TRY(ctx, cudaEventRecord(P->ready, s));
     P->geom_key = h;
@@ -240,8 +291,59 @@ WalkDesc walk_desc(const BatchPlan *P, const tomo_problem &p, int32_t i,
     d.tl = P->tl[i];
     d.tiles_u = (p.img.nu + d.tl.tile_u - 1) / d.tl.tile_u;
     d.tiles_v = (p.img.nv + d.tl.tile_v - 1) / d.tl.tile_v;
-    d.pad = 0;
+    d.ny = p.cube.ny;
+    d.nz = p.cube.nz;
+    d.lay1 = (float *)P->lay.p + 2 * P->vox_off[i];
+    d.lay2 = d.lay1 + (P->vox_off[i + 1] - P->vox_off[i]);
     return d;
+}
+
+// Combine jobs of every problem (layouts 1 and 2) into the cubes cube[i].
+std::vector<LayoutJob> layout_jobs(const BatchPlan *P, int32_t n,
+                                   const tomo_problem *probs,
+                                   float *const *cubes, const double *const *done)
+{
+    std::vector<LayoutJob> jobs(2 * (size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        const tomo_cube_geom &c = probs[i].cube;
+        float *lay1 = (float *)P->lay.p + 2 * P->vox_off[i];
+        for (int L = 1; L <= 2; ++L) {
+            LayoutJob &J = jobs[2 * (size_t)i + (L - 1)];
+            J.acc = L == 1 ? lay1 : lay1 + (P->vox_off[i + 1] - P->vox_off[i]);
+            J.cube = cubes[i];
+            J.used = (const unsigned *)P->lay_used.p + i;
+            J.done = done ? done[i] : nullptr;
+            J.L = L;
+            J.nx = c.nx;
+            J.nb = L == 1 ? c.ny : c.nz;
+            J.nc = L == 1 ? c.nz : c.ny;
+            J.sb = L == 1 ? (int64_t)c.nx : (int64_t)c.nx * c.ny;
+            J.sc = L == 1 ? (int64_t)c.nx * c.ny : (int64_t)c.nx;
+            J.tiles_x = (c.nx + 31) / 32;
+            J.tiles_b = (J.nb + 31) / 32;
+        }
+    }
+    return jobs;
+}
+
+// Plane-synchronous transposes for this batch: enabled for P^T, float
+// atomics mode, and every cube within the plane walk's limits.
+bool batch_plane(const tomo_ctx *ctx, int32_t n, const tomo_problem *probs)
+{
+    if (!(ctx->plane_sync & 1) || ctx->adjoint_mode != 0) return false;
+    for (int32_t i = 0; i < n; ++i)
+        if (!plane_supported(&probs[i].cube)) return false;
+    return true;
+}
+
+int plane_walk_grid(const tomo_ctx *ctx)
+{
+    return (ctx->num_sms > 0 ? ctx->num_sms : 152) * plane_batched_blocks_per_sm();
+}
+
+int combine_grid(const tomo_ctx *ctx)
+{
+    return 8 * (ctx->num_sms > 0 ? ctx->num_sms : 152);
 }
 
 int walk_grid(const tomo_ctx *ctx)
@@ -275,6 +377,30 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         return st;
     CUDA_TRY(ctx, cudaMemsetAsync(P->call_counter.p, 0,
                                   sizeof(unsigned long long), s));
+    if (adjoint && batch_plane(ctx, n, probs)) {
+        if (P->lay_dirty)
+            CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0,
+                                          sizeof(float) * 2 * P->vox_off[n], s));
+        std::vector<float *> cubes(n);
+        for (int32_t i = 0; i < n; ++i) cubes[i] = probs[i].cube_dev;
+        const std::vector<LayoutJob> jobs = layout_jobs(P, n, probs, cubes.data(), nullptr);
+        if ((st = upload(ctx, P->call_jobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
+            return st;
+        P->lay_dirty = true;
+        LAUNCH(ctx, TOMO_K_ADJOINT, s,
+               launch_adjoint_plane_batched((const WalkDesc *)P->call_desc.p,
+                                            (const int64_t *)P->ptpre_dev.p,
+                                            (const int2 *)P->psched_dev.p,
+                                            P->pn_chunks,
+                                            (unsigned long long *)P->call_counter.p,
+                                            plane_walk_grid(ctx), s));
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_add_from_layout_batched((const LayoutJob *)P->call_jobs.p,
+                                              (const int64_t *)P->jpre_dev.p,
+                                              2 * n, combine_grid(ctx), s));
+        P->lay_dirty = false;
+        return TOMO_OK;
+    }
     LAUNCH(ctx, adjoint ? TOMO_K_ADJOINT : TOMO_K_FORWARD, s,
            launch_walk_batched(adjoint, (const WalkDesc *)P->call_desc.p,
                                (const int64_t *)P->tpre_dev.p,
@@ -305,13 +431,13 @@ tomo_status time_tiling(tomo_ctx *ctx, const tomo_problem *p, Tiling t,
                                  p->img.nv, p->cube.nx,
                                  p->cube.nx * p->cube.ny, t, nullptr, s);
         if (err == cudaSuccess) err = cudaEventRecord(e[1], s);
-        if (err == cudaSuccess)
-            err = run_adjoint(ctx, (const RayRec *)ctx->rays.p,
-                              (const ImgParam *)ctx->params.p,
-                              (const Frame *)ctx->frames.p,
-                              (const tomo_pointing *)ctx->ptg.p, p->images_dev,
-                              p->mask_dev, cube_tmp, &p->cube, 1, &p->img, t,
-                              nullptr, s);
+        if (err == cudaSuccess) {
+            // the transpose the single-problem calls would run (the plane
+            // walk ignores t, the per-ray walk uses it)
+            st = adjoint_one(ctx, p->images_dev, p->mask_dev, cube_tmp, &p->cube,
+                             1, &p->img, t, nullptr, s);
+            if (st) break;
+        }
         if (err == cudaSuccess) err = cudaEventRecord(e[2], s);
         if (err == cudaSuccess) err = cudaEventSynchronize(e[2]);
         float f = 0, a = 0;
@@ -348,7 +474,8 @@ tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
     DeviceGuard guard(ctx->device);
     if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = prepare_rays(ctx, &prob->cube, 1, &prob->img,
+    if ((st = ensure_plane(ctx, &prob->cube, 1, kDefaultTiling)) ||
+        (st = prepare_rays(ctx, &prob->cube, 1, &prob->img,
                            prob->pointing_host, s)))
         return st;
     const int64_t nvox = (int64_t)prob->cube.nx * prob->cube.ny * prob->cube.nz;
@@ -463,6 +590,8 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
     }
     h = fnv1a(h, &n_iter, sizeof(n_iter));
     h = fnv1a(h, &flags, sizeof(flags));
+    const bool plane = batch_plane(ctx, n, probs);
+    h = fnv1a(h, &plane, sizeof(plane));
     const size_t stride = 2 * ((size_t)n_iter + 1);
 
     if (!(P->exec && P->graph_key == h)) {
@@ -527,6 +656,26 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             v.nz = p.cube.nz;
             v.lam = (float)p.lambda;
         }
+        // combine jobs of the plane-synchronous transposes: into b, into q,
+        // into q skipping problems that are done
+        std::vector<float *> bs(n), qs(n);
+        std::vector<const double *> dn(n);
+        for (int32_t i = 0; i < n; ++i) {
+            bs[i] = vb + voff[i];
+            qs[i] = vq + voff[i];
+            dn[i] = S + (size_t)i * S_NSLOTS + S_DONE;
+        }
+        std::vector<LayoutJob> jobs = layout_jobs(P, n, probs, bs.data(), nullptr);
+        const std::vector<LayoutJob> jq = layout_jobs(P, n, probs, qs.data(), nullptr);
+        const std::vector<LayoutJob> jqd = layout_jobs(P, n, probs, qs.data(), dn.data());
+        jobs.insert(jobs.end(), jq.begin(), jq.end());
+        jobs.insert(jobs.end(), jqd.begin(), jqd.end());
+        if ((st = upload(ctx, P->solve_jobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
+            return st;
+        if (P->lay_dirty)
+            CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0,
+                                          sizeof(float) * 2 * P->vox_off[n], s));
+        P->lay_dirty = false;
         std::vector<int64_t> pre;  // tile, voxel-item, pixel-item prefixes
         pre.insert(pre.end(), P->tile_prefix.begin(), P->tile_prefix.end());
         pre.insert(pre.end(), vitems.begin(), vitems.end());
@@ -564,6 +713,30 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         if (e == cudaSuccess) e = (call);                                    \
         counts[kind] += 1;                                                   \
     } while (0)
+        // transpose of walk-descriptor set `ws` (combine-job set `js` for
+        // the plane-synchronous walk)
+        const LayoutJob *JB = (const LayoutJob *)P->solve_jobs.p;
+        const int64_t *jpre = (const int64_t *)P->jpre_dev.p;
+        const int64_t *ptile_pre = (const int64_t *)P->ptpre_dev.p;
+        const int2 *psch = (const int2 *)P->psched_dev.p;
+        const int cgrid = combine_grid(ctx);
+        const int pgrid = plane_walk_grid(ctx);
+#define CAP_ADJ(ws, js)                                                      \
+    do {                                                                     \
+        if (plane) {                                                         \
+            CAP(TOMO_K_ADJOINT,                                              \
+                launch_adjoint_plane_batched(W + (ws) * n, ptile_pre, psch,  \
+                                             P->pn_chunks, ctr + next_ctr++, \
+                                             pgrid, c));                     \
+            CAP(TOMO_K_LAYOUT,                                               \
+                launch_add_from_layout_batched(JB + (js) * 2 * n, jpre,      \
+                                               2 * n, cgrid, c));            \
+        } else {                                                             \
+            CAP(TOMO_K_ADJOINT,                                              \
+                launch_walk_batched(true, W + (ws) * n, tile_pre, sch, nch,  \
+                                    ctr + next_ctr++, wgrid, c));            \
+        }                                                                    \
+    } while (0)
         e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * n_walks, c);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(S, 0, sizeof(double) * n * S_NSLOTS, c);
@@ -574,15 +747,13 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                                                    part, c));
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_ZERO, V, vox_pre, n, warm, part,
                                               vgrid, c));
-        CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 0 * n, tile_pre, sch, nch,
-                                                ctr + next_ctr++, wgrid, c));
+        CAP_ADJ(0, 0);
         if (warm) {
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR_X, V, vox_pre, n, warm,
                                                  part, vgrid, c));
             CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, sch, nch,
                                                 ctr + next_ctr++, wgrid, c));
-            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 2 * n, tile_pre, sch, nch,
-                                                ctr + next_ctr++, wgrid, c));
+            CAP_ADJ(2, 1);
         }
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_INIT, V, vox_pre, n, warm, part,
                                               vgrid, c));
@@ -593,8 +764,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                                                 ctr + next_ctr++, wgrid, c));
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR, V, vox_pre, n, warm,
                                                  part, vgrid, c));
-            CAP(TOMO_K_ADJOINT, launch_walk_batched(true, W + 4 * n, tile_pre, sch, nch,
-                                                ctr + next_ctr++, wgrid, c));
+            CAP_ADJ(4, 2);
             CAP(TOMO_K_VECTOR, launch_vec_batched(BV_PQ, V, vox_pre, n, warm,
                                                   part, vgrid, c));
             CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_PQ, V, vox_pre, n, 0.0,
@@ -606,6 +776,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             CAP(TOMO_K_VECTOR, launch_vec_batched(BV_DIR, V, vox_pre, n, warm,
                                                   part, vgrid, c));
         }
+#undef CAP_ADJ
 #undef CAP
         cudaGraph_t g = nullptr;
         const cudaError_t e_end = cudaStreamEndCapture(c, &g);

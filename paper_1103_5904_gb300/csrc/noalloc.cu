@@ -99,7 +99,9 @@ tomo_project_noalloc(const tomo_cube_geom *cube, int32_t n_frames,
     if (cudaMemcpyAsync(ptg, pointing_host, sizeof(tomo_pointing) * n_img,
                         cudaMemcpyHostToDevice, s) != cudaSuccess ||
         launch_frames(ptg, img->n_img, img->nu, img->nv, n_frames, frames,
-                      tan_u, tan_v, params, nullptr, s) != cudaSuccess ||
+                      tan_u, tan_v, params,
+                      make_double3(cube->dx, cube->dy, cube->dz), nullptr,
+                      s) != cudaSuccess ||
         launch_ray_setup(frames, tan_u, tan_v, tomo::host::cube_dev(cube),
                          img->n_img,
                          img->nu, img->nv, rays, s) != cudaSuccess ||

@@ -43,181 +43,11 @@
 //   0  x fastest (native):  x + nx (y + ny z)
 //   1  y fastest:           y + ny (x + nx z)
 //   2  z fastest:           z + nz (x + nx y)
-#include <limits.h>
-#include <math.h>
-
-#include "walk.cuh"
+#include "plane.cuh"
 
 namespace tomo {
 
 namespace {
-
-// One ray, re-expressed for the plane walk: M first, then the two minor
-// axes, a1 the one with the smaller crossing spacing (crossed more often).
-struct PlaneRay {
-    float t0M, t01, t02;  // first crossings
-    float AM, A1, A2;     // crossing spacings
-    float chord;
-    int sM, s1, s2;       // signed strides in the image's layout
-    int idx;              // entry voxel in the image's layout
-    int key;              // entry M coordinate, signed by the M direction
-};
-
-__device__ __forceinline__ void layout_strides(int L, int nx, int ny, int nz,
-                                               int &stx, int &sty, int &stz)
-{
-    if (L == 1) {
-        stx = ny;
-        sty = 1;
-        stz = nx * ny;
-    } else if (L == 2) {
-        stx = nz;
-        sty = nx * nz;
-        stz = 1;
-    } else {
-        stx = 1;
-        sty = nx;
-        stz = nx * ny;
-    }
-}
-
-// Fills p and returns true when the ray fits the plane walk of its image.
-__device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
-                                          int ny, int nz, PlaneRay &p)
-{
-    if (!(hint & kPlaneHintValid)) return false;
-    const int M = hint & 3, L = (hint >> 2) & 3;
-    const bool neg = (hint >> 4) & 1;
-    const int cx = r.idx0 % nx;
-    const int rest = r.idx0 / nx;
-    const int cy = rest % ny, cz = rest / ny;
-    int stx, sty, stz;
-    layout_strides(L, nx, ny, nz, stx, sty, stz);
-    const int gx = signbit(r.dtx) ? -stx : stx;
-    const int gy = signbit(r.dty) ? -sty : sty;
-    const int gz = signbit(r.dtz) ? -stz : stz;
-    const float dM = M == 0 ? r.dtx : (M == 1 ? r.dty : r.dtz);
-    p.t0M = M == 0 ? r.t0x : (M == 1 ? r.t0y : r.t0z);
-    p.t01 = M == 0 ? r.t0y : r.t0x;
-    p.t02 = M == 2 ? r.t0y : r.t0z;
-    p.AM = fabsf(dM);
-    p.A1 = fabsf(M == 0 ? r.dty : r.dtx);
-    p.A2 = fabsf(M == 2 ? r.dty : r.dtz);
-    p.sM = M == 0 ? gx : (M == 1 ? gy : gz);
-    p.s1 = M == 0 ? gy : gx;
-    p.s2 = M == 2 ? gy : gz;
-    // a1 = the minor axis crossed more often (spacing 0: never crossed)
-    if (p.A2 != 0.0f && (p.A1 == 0.0f || p.A2 < p.A1)) {
-        float f = p.t01;
-        p.t01 = p.t02;
-        p.t02 = f;
-        f = p.A1;
-        p.A1 = p.A2;
-        p.A2 = f;
-        const int g = p.s1;
-        p.s1 = p.s2;
-        p.s2 = g;
-    }
-    p.chord = r.chord;
-    p.idx = cx * stx + cy * sty + cz * stz;
-    const int cM = M == 0 ? cx : (M == 1 ? cy : cz);
-    p.key = neg ? -cM : cM;
-    // Two crossings of a minor axis in one slab need its crossing spacing,
-    // less rounding of two crossing parameters (each <= 2^-24 of a value of
-    // at most chord + spacing), below the slab length plus the same: the
-    // margin below is eight times that bound.
-    const float margin = ldexpf(p.chord + fmaxf(p.A1, p.A2) + p.AM, -19);
-    const bool ok1 = p.A1 == 0.0f || p.A1 > p.AM + margin;
-    const bool ok2 = p.A2 == 0.0f || p.A2 > p.AM + margin;
-    return p.AM > 0.0f && (signbit(dM) != 0) == neg && ok1 && ok2;
-}
-
-// Walks the regular lanes of the warp plane by plane; op(idx, len) is called
-// for every segment (len may be 0 at ties).  Every lane of the warp must call
-// this (it uses warp-wide votes); lanes with regular == false only vote.
-//
-// Most slabs hold no crossing of the less steep minor axis a2 (for a view
-// near the ecliptic, a2 is z and is crossed every few tens of slabs): when
-// no lane of the warp crosses a2 in the current slab, the warp takes a fast
-// path with at most one crossing (of a1); otherwise every lane takes the
-// general three-segment body.  Both give the same segments.
-template <class Op>
-__device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
-                                           Op &op)
-{
-    const unsigned full = 0xffffffffu;
-    const int kmin = __reduce_min_sync(full, regular ? p.key : INT_MAX);
-    int wait = regular ? p.key - kmin : 0;
-    bool pending = regular;
-    float t = 0.0f, kM = 0.0f, k1 = 0.0f, k2 = 0.0f;
-    float t1 = p.t01, t2 = p.t02;
-    int idx = p.idx;
-    while (__any_sync(full, pending)) {
-        const bool go = pending && wait <= 0;
-        --wait;
-        const float te = fminf(fmaf(kM, p.AM, p.t0M), p.chord);
-        if (__any_sync(full, go && t2 < te)) {
-            if (go) {
-                const bool first1 = t1 <= t2;
-                const float ta = first1 ? t1 : t2;
-                const float tb = first1 ? t2 : t1;
-                const int sa = first1 ? p.s1 : p.s2;
-                op(idx, fminf(ta, te) - t);
-                if (ta < te) op(idx + sa, fminf(tb, te) - ta);
-                if (tb < te) op(idx + p.s1 + p.s2, te - tb);
-                if (t1 < te) {
-                    k1 += 1.0f;
-                    t1 = fmaf(k1, p.A1, p.t01);
-                    idx += p.s1;
-                }
-                if (t2 < te) {
-                    k2 += 1.0f;
-                    t2 = fmaf(k2, p.A2, p.t02);
-                    idx += p.s2;
-                }
-            }
-        } else if (go) {
-            op(idx, fminf(t1, te) - t);
-            if (t1 < te) {
-                op(idx + p.s1, te - t1);
-                k1 += 1.0f;
-                t1 = fmaf(k1, p.A1, p.t01);
-                idx += p.s1;
-            }
-        }
-        if (go) {
-            if (te < p.chord) {
-                kM += 1.0f;
-                idx += p.sM;
-                t = te;
-            } else {
-                pending = false;
-            }
-        }
-    }
-}
-
-struct PlaneScatterOp {
-    float *c;
-    float y;
-    __device__ __forceinline__ void operator()(int idx, float len)
-    {
-        if (len > 0.0f) atomicAdd(c + idx, len * y);
-    }
-};
-
-struct PlaneScatterTimeOp {
-    float *c0;
-    float *c1;
-    float y0, y1;
-    __device__ __forceinline__ void operator()(int idx, float len)
-    {
-        if (len > 0.0f) {
-            atomicAdd(c0 + idx, len * y0);
-            atomicAdd(c1 + idx, len * y1);
-        }
-    }
-};
 
 template <typename CubeT, bool kTime>
 __global__ void __launch_bounds__(256)
@@ -246,29 +76,37 @@ k_forward_plane(const RayRec *__restrict__ rays,
     const int64_t f0 = kTime ? (int64_t)q.frame * frame_stride : 0;
     float acc = 0.0f;
     if (kTime) {
-        GatherTimeOp<CubeT> op;
+        PlaneGatherTimeOp<CubeT> op;
         op.c0 = lay + f0;
         op.c1 = op.c0 + frame_stride;
         op.w0 = 1.0f - q.w;
         op.w1 = q.w;
         op.acc = 0.0f;
         plane_walk(p, regular, op);
-        if (live && !regular) {
-            op.c0 = native + f0;
-            op.c1 = op.c0 + frame_stride;
-            siddon_walk(r, nx, nx * ny, op);
-        }
         acc = op.acc;
+        if (live && !regular) {
+            GatherTimeOp<CubeT> op2;
+            op2.c0 = native + f0;
+            op2.c1 = op2.c0 + frame_stride;
+            op2.w0 = op.w0;
+            op2.w1 = op.w1;
+            op2.acc = 0.0f;
+            siddon_walk(r, nx, nx * ny, op2);
+            acc = op2.acc;
+        }
     } else {
-        GatherOp<CubeT> op;
+        PlaneGatherOp<CubeT> op;
         op.c = lay;
         op.acc = 0.0f;
         plane_walk(p, regular, op);
-        if (live && !regular) {
-            op.c = native;
-            siddon_walk(r, nx, nx * ny, op);
-        }
         acc = op.acc;
+        if (live && !regular) {
+            GatherOp<CubeT> op2;
+            op2.c = native;
+            op2.acc = 0.0f;
+            siddon_walk(r, nx, nx * ny, op2);
+            acc = op2.acc;
+        }
     }
     if (in_img) out[id] = q.gain * acc;
 }

@@ -1,0 +1,198 @@
+// Plane-synchronous Siddon walk: per-ray setup, the warp-wide walk and its
+// segment operations, shared by the single-problem kernels (plane.cu) and
+// the batched transpose (batch.cu).  The design and its exactness argument
+// are described at the top of plane.cu.
+#pragma once
+
+#include <limits.h>
+#include <math.h>
+
+#include "walk.cuh"
+
+namespace tomo {
+
+// One ray, re-expressed for the plane walk: M first, then the two minor
+// axes, a1 the one with the smaller crossing spacing (crossed more often).
+struct PlaneRay {
+    float t0M, t01, t02;  // first crossings
+    float AM, A1, A2;     // crossing spacings
+    float chord;
+    int sM, s1, s2;       // signed strides in the image's layout
+    int idx;              // entry voxel in the image's layout
+    int key;              // entry M coordinate, signed by the M direction
+};
+
+__device__ __forceinline__ void layout_strides(int L, int nx, int ny, int nz,
+                                               int &stx, int &sty, int &stz)
+{
+    if (L == 1) {
+        stx = ny;
+        sty = 1;
+        stz = nx * ny;
+    } else if (L == 2) {
+        stx = nz;
+        sty = nx * nz;
+        stz = 1;
+    } else {
+        stx = 1;
+        sty = nx;
+        stz = nx * ny;
+    }
+}
+
+// Fills p and returns true when the ray fits the plane walk of its image.
+__device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
+                                          int ny, int nz, PlaneRay &p)
+{
+    if (!(hint & kPlaneHintValid)) return false;
+    const int M = hint & 3, L = (hint >> 2) & 3;
+    const bool neg = (hint >> 4) & 1;
+    const int cx = r.idx0 % nx;
+    const int rest = r.idx0 / nx;
+    const int cy = rest % ny, cz = rest / ny;
+    int stx, sty, stz;
+    layout_strides(L, nx, ny, nz, stx, sty, stz);
+    const int gx = signbit(r.dtx) ? -stx : stx;
+    const int gy = signbit(r.dty) ? -sty : sty;
+    const int gz = signbit(r.dtz) ? -stz : stz;
+    const float dM = M == 0 ? r.dtx : (M == 1 ? r.dty : r.dtz);
+    p.t0M = M == 0 ? r.t0x : (M == 1 ? r.t0y : r.t0z);
+    p.t01 = M == 0 ? r.t0y : r.t0x;
+    p.t02 = M == 2 ? r.t0y : r.t0z;
+    p.AM = fabsf(dM);
+    p.A1 = fabsf(M == 0 ? r.dty : r.dtx);
+    p.A2 = fabsf(M == 2 ? r.dty : r.dtz);
+    p.sM = M == 0 ? gx : (M == 1 ? gy : gz);
+    p.s1 = M == 0 ? gy : gx;
+    p.s2 = M == 2 ? gy : gz;
+    // a1 = the minor axis crossed more often (spacing 0: never crossed)
+    if (p.A2 != 0.0f && (p.A1 == 0.0f || p.A2 < p.A1)) {
+        float f = p.t01;
+        p.t01 = p.t02;
+        p.t02 = f;
+        f = p.A1;
+        p.A1 = p.A2;
+        p.A2 = f;
+        const int g = p.s1;
+        p.s1 = p.s2;
+        p.s2 = g;
+    }
+    p.chord = r.chord;
+    p.idx = cx * stx + cy * sty + cz * stz;
+    const int cM = M == 0 ? cx : (M == 1 ? cy : cz);
+    p.key = neg ? -cM : cM;
+    // Two crossings of a minor axis in one slab need its crossing spacing,
+    // less rounding of two crossing parameters (each <= 2^-24 of a value of
+    // at most chord + spacing), below the slab length plus the same: the
+    // margin below is eight times that bound.
+    const float margin = ldexpf(p.chord + fmaxf(p.A1, p.A2) + p.AM, -19);
+    const bool ok1 = p.A1 == 0.0f || p.A1 > p.AM + margin;
+    const bool ok2 = p.A2 == 0.0f || p.A2 > p.AM + margin;
+    return p.AM > 0.0f && (signbit(dM) != 0) == neg && ok1 && ok2;
+}
+
+// Walks the regular lanes of the warp plane by plane; op(on, idx, len) is
+// called for every segment with on == true (len may be 0 at ties, which adds
+// an exact zero) and, with on == false, for slots without a segment (idx
+// then may lie outside the cube and must not be touched).  Every lane of the
+// warp must call this (it uses warp-wide votes); lanes with regular == false
+// only vote.
+//
+// Each lane counts slabs in kM; a lane whose entry plane comes after the
+// warp's first one starts at kM = -(its offset) and waits until kM reaches 0.
+// Most slabs hold no crossing of the less steep minor axis a2 (for a view
+// near the ecliptic, a2 is z and is crossed every few tens of slabs): when
+// no lane of the warp crosses a2 in the current slab, the warp takes a fast
+// path with at most one crossing (of a1); otherwise every lane takes the
+// general three-segment body.  Both give the same segments.
+template <class Op>
+__device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
+                                           Op &op)
+{
+    const unsigned full = 0xffffffffu;
+    const int kmin = __reduce_min_sync(full, regular ? p.key : INT_MAX);
+    bool pending = regular;
+    float kM = regular ? (float)(kmin - p.key) : 0.0f;
+    float t = 0.0f, k1 = 0.0f, k2 = 0.0f;
+    float t1 = p.t01, t2 = p.t02;
+    int idx = p.idx;
+    while (__any_sync(full, pending)) {
+        const bool go = pending && kM >= 0.0f;
+        const float te = fminf(fmaf(kM, p.AM, p.t0M), p.chord);
+        if (__any_sync(full, go && t2 < te)) {
+            const bool first1 = t1 <= t2;
+            const float ta = first1 ? t1 : t2;
+            const float tb = first1 ? t2 : t1;
+            const int sa = first1 ? p.s1 : p.s2;
+            op(go, idx, fminf(ta, te) - t);
+            op(go && ta < te, idx + sa, fminf(tb, te) - ta);
+            op(go && tb < te, idx + p.s1 + p.s2, te - tb);
+            const bool c1 = go && t1 < te, c2 = go && t2 < te;
+            k1 = c1 ? k1 + 1.0f : k1;
+            k2 = c2 ? k2 + 1.0f : k2;
+            t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
+            t2 = c2 ? fmaf(k2, p.A2, p.t02) : t2;
+            idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0);
+        } else {
+            const bool c1 = go && t1 < te;
+            op(go, idx, fminf(t1, te) - t);
+            op(c1, idx + p.s1, te - t1);
+            k1 = c1 ? k1 + 1.0f : k1;
+            t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
+            idx += c1 ? p.s1 : 0;
+        }
+        const bool more = te < p.chord;
+        pending = pending && (!go || more);
+        idx += (go && more) ? p.sM : 0;
+        t = go ? te : t;
+        kM += 1.0f;
+    }
+}
+
+template <typename CubeT>
+struct PlaneGatherOp {
+    const CubeT *c;
+    float acc;
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        if (on) acc = fmaf(len, load_voxel(c, idx), acc);
+    }
+};
+
+template <typename CubeT>
+struct PlaneGatherTimeOp {
+    const CubeT *c0;
+    const CubeT *c1;
+    float w0, w1, acc;
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        if (on) {
+            const float v = fmaf(w0, load_voxel(c0, idx), w1 * load_voxel(c1, idx));
+            acc = fmaf(len, v, acc);
+        }
+    }
+};
+
+struct PlaneScatterOp {
+    float *c;
+    float y;
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        if (on) atomicAdd(c + idx, len * y);
+    }
+};
+
+struct PlaneScatterTimeOp {
+    float *c0;
+    float *c1;
+    float y0, y1;
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        if (on) {
+            atomicAdd(c0 + idx, len * y0);
+            atomicAdd(c1 + idx, len * y1);
+        }
+    }
+};
+
+}  // namespace tomo

@@ -26,9 +26,11 @@ namespace {
 // direction, and L = the axis (other than M) along which neighbouring pixels
 // of a row move at a fixed M plane.  Moving along the row turns the
 // direction by ~e1; at a fixed M plane the ray through u + e1 d is displaced
-// along e1 - u e1_M / u_M.  Only the walk's speed depends on the hint.
+// along e1 - u e1_M / u_M.  The hint is marked valid only when neighbouring
+// pixels are at least kPlaneMinPitch voxels of L apart at the distance of
+// Sun centre.  Only the walk's speed depends on the hint.
 __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
-                              int nv)
+                              int nv, double3 vox)
 {
     const double tu = tan((0.5 * (nu - 1) - p.crpix_u) * p.cdelt_u + p.crval_u);
     const double tv = tan((0.5 * (nv - 1) - p.crpix_v) * p.cdelt_v + p.crval_v);
@@ -47,7 +49,10 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
             L = a;
         }
     }
-    return kPlaneHintValid | M | (L << 2) | ((u[M] < 0.0) ? 16 : 0);
+    const double dL = L == 0 ? vox.x : (L == 1 ? vox.y : vox.z);
+    const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dL;
+    const bool valid = pitch >= kPlaneMinPitch;
+    return (valid ? kPlaneHintValid : 0) | M | (L << 2) | ((u[M] < 0.0) ? 16 : 0);
 }
 
 // One block per image: the FP64 frame, the image parameters and the tangent
@@ -55,7 +60,7 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
 __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
                          int32_t nv, int32_t n_frames, Frame *frames,
                          double *tan_u, double *tan_v, ImgParam *params,
-                         unsigned *layout_used)
+                         double3 vox, unsigned *layout_used)
 {
     const int img = blockIdx.x;
     const tomo_pointing p = ptg[img];
@@ -83,8 +88,9 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
         frames[img] = f;
         ImgParam q;
         q.gain = (float)p.gain;
-        q.pad = plane_hint(p, f, nu, nv);
-        if (layout_used) atomicOr(layout_used, 1u << ((q.pad >> 2) & 3));
+        q.pad = plane_hint(p, f, nu, nv, vox);
+        if (layout_used && (q.pad & kPlaneHintValid))
+            atomicOr(layout_used, 1u << ((q.pad >> 2) & 3));
         if (n_frames > 1) {
             int k = (int)floor(p.time);
             if (k > n_frames - 2) k = n_frames - 2;
@@ -188,12 +194,12 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
-                          ImgParam *params, unsigned *layout_used,
-                          cudaStream_t s)
+                          ImgParam *params, double3 vox,
+                          unsigned *layout_used, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
     k_frames<<<n_img, 128, 0, s>>>(ptg_dev, nu, nv, n_frames, frames, tan_u,
-                                   tan_v, params, layout_used);
+                                   tan_v, params, vox, layout_used);
     return cudaGetLastError();
 }
 

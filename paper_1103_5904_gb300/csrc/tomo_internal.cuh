@@ -40,6 +40,11 @@ struct __align__(16) ImgParam {
 
 constexpr int32_t kPlaneHintValid = 32;
 constexpr int32_t kPlaneMaxSide = 16384;
+// Below this pixel pitch (in voxels of the lateral axis, at the distance of
+// Sun centre) a row of 32 rays covers only a few voxels; the per-ray walk,
+// which sums the contributions of lanes in the same voxel before its float
+// atomic, is faster there (measured crossover between 0.13 and 0.20).
+constexpr double kPlaneMinPitch = 0.16;
 
 // Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
 // 2 = z-fastest) for the plane-synchronous walk (plane.cu).
@@ -82,12 +87,13 @@ enum : int {
 constexpr int kMaxReduceBlocks = 2048;
 
 // ---- setup.cu
+// vox: voxel size per axis (for the plane-walk hint's pixel-pitch test);
 // layout_used (may be NULL): bit L is or-ed in for every image whose plane
-// hint names layout L
+// hint is valid and names layout L
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
-                          ImgParam *params, unsigned *layout_used,
+                          ImgParam *params, double3 vox, unsigned *layout_used,
                           cudaStream_t s);
 cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
                              const double *tan_v, CubeDev cube, int32_t n_img,

@@ -93,6 +93,45 @@ def test_backproject_batched_matches_oracle(T):
         torch.testing.assert_close(d["cube"], 2 * b, rtol=1e-5, atol=1e-6)
 
 
+def test_backproject_batched_walks_every_layout(T):
+    """Rolled, polar and axis views (every cube layout of the plane-
+    synchronous transpose, and lanes that fall back to the per-ray walk):
+    the batched transpose with the plane walk (default) and with the per-ray
+    walk both meet the transpose bound against the oracle."""
+    rng = np.random.default_rng(9)
+    probs = []
+    for i, (lons, lats, roll) in enumerate([
+            ([0.0, 90.0, 180.0], [0.0, 0.0, 0.0], 0.0),
+            ([10.0, 100.0, 230.0], [5.0, -5.0, 10.0], np.pi / 2),
+            ([0.0, 45.0, 200.0], [89.0, -88.0, 75.0], 0.3),
+            ([45.0, 135.0, 314.8], [0.0, 2.0, -2.0], 0.0)]):
+        # odd sides: the exact axis views (lon 0 / 90 / 180, lat 0) must not
+        # run inside a voxel plane through the origin, where which voxel gets
+        # the segment is decided by 1e-16 perturbations of the input
+        side = 25 + 2 * i
+        g = synth.cube_geom(side, 1.5, ny=side + 2, nz=side + 4)
+        ptg = synth.pointing_table(lons, lats, 215.0, 37, 29, 3.4,
+                                   roll_deg=np.degrees(roll))
+        probs.append({"geom": g, "pointing": ptg, "nu": 37, "nv": 29,
+                      "cube_np": np.zeros((g["nz"], g["ny"], g["nx"]), np.float32),
+                      "mask_np": (rng.random((3, 29, 37)) < 0.1).astype(np.uint8),
+                      "lam": 0.0})
+    ims = [rng.random((3, 29, 37)).astype(np.float32) for _ in probs]
+    ray = T.Context()
+    ray.set_option(T.tomo.TOMO_OPT_PLANE_SYNC, 0)
+    for ctx in (None, ray):
+        dp = _dev_problems(probs, ims)
+        T.tomo_backproject_batched(dp, ctx=ctx)
+        for p, d, y in zip(probs, dp, ims):
+            want = siddon.backproject(p["geom"], y, p["pointing"], p["nu"],
+                                      p["nv"], p["mask_np"])
+            cw = siddon.crossing_weights(p["geom"], y, p["pointing"], p["nu"],
+                                         p["nv"], p["mask_np"])
+            assert_transpose_close(d["cube"].cpu().numpy(), want, cw,
+                                   p["geom"], "batched P^T layouts")
+    ray.close()
+
+
 def _cg_problems(seeds, max_side):
     out = []
     for s in seeds:

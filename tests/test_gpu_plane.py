@@ -10,6 +10,7 @@ fallback: views along x (layout 1: y fastest) and along y (layout 0), rolled
 views whose pixel rows run along z (layout 2), views from near the pole
 (major axis z), images whose field of view straddles a 45-degree diagonal
 (lanes whose major axis differs from the image's take the per-ray walk),
+images whose pixels are too dense for the plane walk (all lanes per-ray),
 an observer inside the cube, ragged and anisotropic cubes, masks, gains,
 time interpolation and bf16 storage.
 """
@@ -89,6 +90,11 @@ def _cases():
     out.append(("masked", g, p, mask, 37, 53))
     c = synth.make_config("single", scale=2)
     out.append(("single/2", c["geom"], c["pointing"], c["mask"], c["nu"], c["nv"]))
+    # dense pixels (0.13 voxel apart): the plane hint is not valid and every
+    # lane takes the per-ray walk inside the plane kernels
+    g4 = synth.cube_geom(33, 1.5)
+    p = synth.pointing_table([20.0, 110.0], [3.0, -3.0], 215.0, 250, 40, 3.2)
+    out.append(("dense", g4, p, None, 250, 40))
     return out
 
 
