@@ -70,8 +70,8 @@ def parse_args(argv=None):
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--plane-sync", type=int, default=None,
                     help="walk of P / P^T (TOMO_OPT_PLANE_SYNC bit mask: "
-                         "bit 0 P^T, bit 1 P plane-synchronous; library "
-                         "default 1)")
+                         "bit 0 P^T, bit 1 P on every image, bit 2 P on the "
+                         "images where it is faster; library default 5)")
     ap.add_argument("--adjoint-mode", type=int, default=None,
                     help="transpose kernel (TOMO_OPT_ADJOINT): 0 float "
                          "atomics, 1 bundle window, 2 voxel tiles")
@@ -357,28 +357,35 @@ def run_gpu(args, rank, local_rank, world):
 
     # roofline of the dominant Siddon kernel (launch-averaged device time)
     kern = {}
+    # projections per step: P once per CG iteration, P^T once more for b;
+    # a projection may take more than one launch (the forward runs the
+    # per-ray and the plane-synchronous kernels on their own images)
+    n_proj = {"forward": args.iters * args.steps,
+              "adjoint": (args.iters + 1) * args.steps}
     for kind in ("forward", "adjoint"):
         launches, ms = prof[kind]
         if launches == 0:
             continue
-        per_launch_s = ms / 1e3 / launches
+        per_launch_s = ms / 1e3 / n_proj[kind]
         b = algorithmic_bytes(n_rays, n_live, segments, kind)
-        kern[kind] = {"launches": launches, "ms_per_launch": 1e3 * per_launch_s,
+        kern[kind] = {"launches": launches, "projections": n_proj[kind],
+                      "ms_per_projection": 1e3 * per_launch_s,
                       "segments_per_s": segments / per_launch_s,
                       "rays_per_s": n_rays / per_launch_s,
                       "algorithmic_bytes": b,
                       "achieved_gbs": b / per_launch_s / 1e9,
                       "time_share": ms / sum(v[1] for v in prof.values())}
-    dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    dom = max(kern, key=lambda k: kern[k]["ms_per_projection"] * kern[k]["projections"])
     kern["layout"] = {"launches": prof["layout"][0], "ms": prof["layout"][1],
                       "what": "cube layout copies of the plane-synchronous "
                               "walk (most return at once when no image "
                               "uses their layout)"}
     peak, peak_src = peak_hbm()
-    plane = 1 if args.plane_sync is None else args.plane_sync
+    plane = 5 if args.plane_sync is None else args.plane_sync
     mode = args.adjoint_mode or 0
-    kname = {"forward": ("k_forward_plane<float,false>" if plane & 2
-                         else "k_forward<float,false>"),
+    kname = {"forward": ("k_forward_plane<float,false>" if plane & 2 else
+                         "k_forward<float,false>+k_forward_plane<float,false>"
+                         if plane & 4 else "k_forward<float,false>"),
              "adjoint": ("k_adjoint_plane<false>" if mode == 0 and plane & 1
                          else {0: "k_adjoint<false>", 1: "k_adjoint_window",
                                2: "k_adjoint_tiled"}[mode])}

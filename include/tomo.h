@@ -107,19 +107,24 @@ typedef struct tomo_ctx tomo_ctx;
                                   global atomics).  Time-interpolated
                                   transposes always use 0, and 1 needs tiles
                                   of 256 pixels. */
-#define TOMO_OPT_PLANE_SYNC 7  /* bit mask (default 1): bit 0 for P^T (with
-                                  TOMO_OPT_ADJOINT 0), bit 1 for P, of
-                                  single-problem calls.  A set bit makes the
-                                  rays of a warp walk the cube one plane of
-                                  the image's major axis at a time, on a copy
-                                  of the cube stored with the image's
-                                  lateral axis fastest, so the voxels a warp
-                                  touches at once fall in few 32-byte
+#define TOMO_OPT_PLANE_SYNC 7  /* bit mask (default 5) choosing the Siddon
+                                  walk of single-problem calls: bit 0 for
+                                  P^T (with TOMO_OPT_ADJOINT 0); bit 1 for P
+                                  on every image; bit 2 for P on the images
+                                  viewed more than ~31 degrees from a cube
+                                  axis (per ray on the others).  A set bit
+                                  makes the rays of a warp walk the cube one
+                                  plane of the image's major axis at a time,
+                                  on a copy of the cube stored with the
+                                  image's lateral axis fastest, so the voxels
+                                  a warp touches at once fall in few 32-byte
                                   sectors; a clear bit makes every lane walk
                                   its own ray one segment per step.  Same
                                   segments either way: P is bit-identical,
                                   P^T differs only by the order of float
-                                  additions.  The plane walk uses its own
+                                  additions.  Images whose pixels are less
+                                  than 0.16 voxel apart always take the
+                                  per-ray walk.  The plane walk uses its own
                                   tiling (32 x 8 pixels per CTA, one image
                                   row per warp) whatever the tile options
                                   say.  Needs cubes of at most 16384 voxels

@@ -268,10 +268,10 @@ cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
 bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
                bool forward)
 {
-    const int bit = forward ? 2 : 1;
+    const int bits = forward ? (2 | 4) : 1;
     if (!forward && ctx->adjoint_mode != 0) return false;
     (void)t;
-    return (ctx->plane_sync & bit) != 0 && plane_supported(c);
+    return (ctx->plane_sync & bits) != 0 && plane_supported(c);
 }
 
 tomo_status ensure_plane(tomo_ctx *ctx, const tomo_cube_geom *c,
@@ -304,10 +304,19 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                launch_to_layout(cube_dev, dtype, ctx->lay2.p, 2, c, n_frames,
                                 used, done, s));
         PlaneCubes pc = { { cube_dev, ctx->lay1.p, ctx->lay2.p } };
+        // bit 1: every image plane-synchronous; else (bit 2) the images whose
+        // hint marks the plane forward as faster, the rest per ray
+        const bool all = (ctx->plane_sync & 2) != 0;
+        if (!all)
+            LAUNCH(ctx, TOMO_K_FORWARD, s,
+                   launch_forward(rays, prm, cube_dev, dtype, fstride,
+                                  n_frames > 1, mask, out, g->n_img, g->nu,
+                                  g->nv, c->nx, c->nx * c->ny, t, done, s,
+                                  true));
         LAUNCH(ctx, TOMO_K_FORWARD, s,
                launch_forward_plane(rays, prm, pc, dtype, fstride, n_frames > 1,
                                     mask, out, g->n_img, g->nu, g->nv, c,
-                                    done, s));
+                                    done, s, !all));
         return TOMO_OK;
     }
     LAUNCH(ctx, TOMO_K_FORWARD, s,
@@ -462,7 +471,7 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
         ctx->adjoint_mode = (int)value;
         return TOMO_OK;
     case TOMO_OPT_PLANE_SYNC:
-        if (value < 0 || value > 3) break;
+        if (value < 0 || value > 7) break;
         ctx->plane_sync = (int)value;
         return TOMO_OK;
     default:

@@ -37,7 +37,10 @@ struct tomo_ctx {
     char err[512] = { 0 };
     bool ray_cache = true;
     int adjoint_mode = 0;  // 0: float atomics; 1: bundle window; 2: tiles
-    int plane_sync = 1;  // bit 0: P^T, bit 1: P walk plane-synchronously
+    // bit 0: P^T plane-synchronous; bit 1: P plane-synchronous for every
+    // image; bit 2: P plane-synchronous for the images whose hint marks it
+    // as the faster walk, per ray for the others
+    int plane_sync = 5;
     tomo::Tiling tiling = { 32, 8, 8 };
     // geometry cache
     bool key_valid = false;

@@ -50,19 +50,22 @@ namespace tomo {
 namespace {
 
 template <typename CubeT, bool kTime>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
 k_forward_plane(const RayRec *__restrict__ rays,
                 const ImgParam *__restrict__ prm, PlaneCubes cubes,
                 int64_t frame_stride, const uint8_t *__restrict__ mask,
                 float *__restrict__ out, int nu, int nv, int nx, int ny,
-                int nz, Tiling tl, const double *__restrict__ done)
+                int nz, Tiling tl, const double *__restrict__ done,
+                bool only_marked)
 {
     if (done != nullptr && *done != 0.0) return;
+    const int img = blockIdx.z;
+    const ImgParam q = prm[img];
+    // the whole CTA covers one image: this return is uniform
+    if (only_marked && !(q.pad & kPlaneFwdBit)) return;
     int iu, iv;
     const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
-    const int img = blockIdx.z;
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
-    const ImgParam q = prm[img];
     RayRec r;
     r.chord = -1.0f;
     if (in_img && (mask == nullptr || mask[id] == 0)) r = load_ray(rays + id);
@@ -337,30 +340,31 @@ cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
                                  const uint8_t *mask, float *out,
                                  int32_t n_img, int32_t nu, int32_t nv,
                                  const tomo_cube_geom *c, const double *done,
-                                 cudaStream_t s)
+                                 cudaStream_t s, bool only_marked)
 {
     if (n_img <= 0) return cudaSuccess;
     const Tiling t = kPlaneTiling;
     const dim3 grid = plane_grid(nu, nv, n_img);
     const int block = t.tile_u * t.tile_v;
+    const bool om = only_marked;
     if (dtype == TOMO_BF16) {
         if (time_interp)
             k_forward_plane<uint16_t, true><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done);
+                c->ny, c->nz, t, done, om);
         else
             k_forward_plane<uint16_t, false><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done);
+                c->ny, c->nz, t, done, om);
     } else {
         if (time_interp)
             k_forward_plane<float, true><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done);
+                c->ny, c->nz, t, done, om);
         else
             k_forward_plane<float, false><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done);
+                c->ny, c->nz, t, done, om);
     }
     return cudaGetLastError();
 }

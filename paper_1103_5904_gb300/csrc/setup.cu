@@ -52,7 +52,12 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
     const double dL = L == 0 ? vox.x : (L == 1 ? vox.y : vox.z);
     const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dL;
     const bool valid = pitch >= kPlaneMinPitch;
-    return (valid ? kPlaneHintValid : 0) | M | (L << 2) | ((u[M] < 0.0) ? 16 : 0);
+    double minor = 0.0;
+    for (int a = 0; a < 3; ++a)
+        if (a != M) minor = fmax(minor, fabs(u[a]));
+    const bool fwd = valid && minor >= kPlaneFwdMinRatio * fabs(u[M]);
+    return (valid ? kPlaneHintValid : 0) | (fwd ? kPlaneFwdBit : 0) | M |
+           (L << 2) | ((u[M] < 0.0) ? 16 : 0);
 }
 
 // One block per image: the FP64 frame, the image parameters and the tangent

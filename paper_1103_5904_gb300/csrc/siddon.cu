@@ -25,12 +25,14 @@ __global__ void __launch_bounds__(512)
 k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
           const CubeT *__restrict__ cube, int64_t frame_stride,
           const uint8_t *__restrict__ mask, float *__restrict__ out, int nu,
-          int nv, int nx, int nxny, Tiling tl, const double *__restrict__ done)
+          int nv, int nx, int nxny, Tiling tl, const double *__restrict__ done,
+          bool skip_plane_images)
 {
     if (done != nullptr && *done != 0.0) return;
+    const int img = blockIdx.z;
+    if (skip_plane_images && (prm[img].pad & kPlaneFwdBit)) return;
     int iu, iv;
     if (!pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv)) return;
-    const int img = blockIdx.z;
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     float y = 0.0f;
     if (mask == nullptr || mask[id] == 0) {
@@ -127,27 +129,29 @@ cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
                            int64_t frame_stride, bool time_interp,
                            const uint8_t *mask, float *out, int32_t n_img,
                            int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
-                           Tiling t, const double *done, cudaStream_t s)
+                           Tiling t, const double *done, cudaStream_t s,
+                           bool skip_plane_images)
 {
     if (n_img <= 0) return cudaSuccess;
     const dim3 grid = grid_of(nu, nv, n_img, t);
     const int block = t.tile_u * t.tile_v;
+    const bool sk = skip_plane_images;
     if (dtype == TOMO_BF16) {
         const uint16_t *c = static_cast<const uint16_t *>(cube);
         if (time_interp)
             k_forward<uint16_t, true><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done);
+                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
         else
             k_forward<uint16_t, false><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done);
+                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
     } else {
         const float *c = static_cast<const float *>(cube);
         if (time_interp)
             k_forward<float, true><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done);
+                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
         else
             k_forward<float, false><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done);
+                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
     }
     return cudaGetLastError();
 }

@@ -35,7 +35,8 @@ struct __align__(16) ImgParam {
     int32_t frame;  // k (0 when T == 1)
     int32_t pad;    // plane-walk hint: bits 0-1 major axis M, bits 2-3
                     // lateral axis L (the layout), bit 4 M direction < 0,
-                    // bit 5 set when the hint is valid
+                    // bit 5 set when the hint is valid, bit 6 set when the
+                    // plane forward is the faster one (kPlaneFwdBit)
 };
 
 constexpr int32_t kPlaneHintValid = 32;
@@ -45,6 +46,14 @@ constexpr int32_t kPlaneMaxSide = 16384;
 // which sums the contributions of lanes in the same voxel before its float
 // atomic, is faster there (measured crossover between 0.13 and 0.20).
 constexpr double kPlaneMinPitch = 0.16;
+// Hint bit: the plane-synchronous forward is the faster one for this image.
+// Measured on 512^2 views of a 256^3 cube: the plane forward wins once the
+// steeper minor component of the central line of sight is at least 0.6 of
+// the major one (views more than ~31 degrees from an axis: two segments per
+// slab amortise its per-slab work); nearer the axes the per-ray walk's
+// lanes stay in step and it wins.
+constexpr int32_t kPlaneFwdBit = 64;
+constexpr double kPlaneFwdMinRatio = 0.6;
 
 // Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
 // 2 = z-fastest) for the plane-synchronous walk (plane.cu).
@@ -101,12 +110,15 @@ cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
                              cudaStream_t s);
 
 // ---- siddon.cu
+// skip_plane_images: leave the images whose hint has kPlaneFwdBit to the
+// plane-synchronous forward (launched with only_marked)
 cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
                            const void *cube, tomo_dtype dtype,
                            int64_t frame_stride, bool time_interp,
                            const uint8_t *mask, float *out, int32_t n_img,
                            int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
-                           Tiling t, const double *done, cudaStream_t s);
+                           Tiling t, const double *done, cudaStream_t s,
+                           bool skip_plane_images = false);
 cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
                            const float *images, const uint8_t *mask,
                            float *cube, int64_t frame_stride,
@@ -152,7 +164,7 @@ cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
                                  const uint8_t *mask, float *out,
                                  int32_t n_img, int32_t nu, int32_t nv,
                                  const tomo_cube_geom *c, const double *done,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool only_marked = false);
 cudaError_t launch_adjoint_plane(const RayRec *rays, const ImgParam *prm,
                                  const float *images, const uint8_t *mask,
                                  PlaneAcc acc, int64_t frame_stride,

@@ -49,6 +49,15 @@ def ctxs(T):
     ray.close()
 
 
+@pytest.fixture(scope="module")
+def auto(T):
+    """The default: P^T plane-synchronous, P per image."""
+    ctx = T.Context()
+    ctx.set_option(T.tomo.TOMO_OPT_PLANE_SYNC, 5)
+    yield ctx
+    ctx.close()
+
+
 def _anisotropic():
     return {"nx": 29, "ny": 31, "nz": 33, "x0": -1.4, "y0": -1.55, "z0": -1.3,
             "dx": 2.8 / 29, "dy": 3.1 / 31, "dz": 2.7 / 33}
@@ -102,7 +111,7 @@ CASES = _cases()
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_forward_bit_identical_to_per_ray_walk(T, ctxs, case):
+def test_forward_bit_identical_to_per_ray_walk(T, ctxs, auto, case):
     name, g, ptg, mask, nu, nv = case
     plane, ray = ctxs
     rng = np.random.default_rng(5)
@@ -110,7 +119,9 @@ def test_forward_bit_identical_to_per_ray_walk(T, ctxs, case):
     md = mask_dev(mask)
     a = T.tomo_project(to_dev(cube), g, ptg, nu, nv, mask=md, ctx=plane)
     b = T.tomo_project(to_dev(cube), g, ptg, nu, nv, mask=md, ctx=ray)
+    c = T.tomo_project(to_dev(cube), g, ptg, nu, nv, mask=md, ctx=auto)
     assert torch.equal(a, b), name
+    assert torch.equal(c, b), name
     want = siddon.project(g, cube, ptg, nu, nv, mask)
     assert_close(a.cpu().numpy(), want, "P plane %s" % name)
 
@@ -167,6 +178,7 @@ def test_time_interpolation_and_bf16(T, ctxs):
         a = T.tomo_project(X, g, ptg, 37, 53, n_frames=4, ctx=plane)
         b = T.tomo_project(X, g, ptg, 37, 53, n_frames=4, ctx=ray)
         assert torch.equal(a, b), dt
+        assert torch.equal(T.tomo_project(X, g, ptg, 37, 53, n_frames=4), b), dt
     want = siddon.project(g, frames, ptg, 37, 53, n_frames=4)
     assert_close(T.tomo_project(to_dev(frames), g, ptg, 37, 53, n_frames=4,
                                 ctx=plane).cpu().numpy(), want, "P plane time")
