@@ -75,6 +75,10 @@ def parse_args(argv=None):
     ap.add_argument("--adjoint-mode", type=int, default=None,
                     help="transpose kernel (TOMO_OPT_ADJOINT): 0 float "
                          "atomics, 1 bundle window, 2 voxel tiles")
+    ap.add_argument("--sweep", action="store_true",
+                    help="measurement table instead of the benchmark line: "
+                         "P, P^T (f32 / bf16), CG s/iter and the oracle's "
+                         "rate on 1 and all host cores for every config")
     ap.add_argument("--images", type=int, default=0,
                     help="keep only this many images (evenly spaced) of the "
                          "workload: a reduced case for profiler captures")
@@ -239,9 +243,9 @@ def oracle_sample(c, seconds, seed=0):
         images[ids] = 0.0
         return ids.size, segs, dt
 
-    n, segs, dt = run(2e-4)  # calibrate
-    rate = 2 * segs / max(dt, 1e-6)
-    frac = min(1.0, 2e-4 * seconds / max(dt, 1e-6))
+    f_cal = min(2e-4, 4000.0 / live.size)
+    n, segs, dt = run(f_cal)  # calibrate
+    frac = min(1.0, f_cal * seconds / max(dt, 1e-6))
     n, segs, dt = run(frac)
     desc = ("FP64 oracle P then P^T over a seeded sample of %d unmasked rays "
             "(%.3f %% of %s, %d segments each way)"
@@ -555,6 +559,141 @@ def run_batched(args, rank, local_rank, world):
     return 0
 
 
+# ------------------------------------------------------- measurement table
+
+SWEEP = [
+    # name, CG iterations (0: none), bf16 variant
+    ("small", 0, False),
+    ("single", 20, False),
+    ("temporal", 0, True),
+    ("coronagraph", 50, True),
+    ("paper128", 0, False),
+    ("paper256", 0, False),
+    ("cg256", 20, True),
+]
+
+
+def run_sweep(args, local_rank):
+    """One JSON line per config: device time and segments/s of P and P^T
+    (median of repeated calls with the ray records cached, L2 flushed between
+    calls), the bf16-stored cube where the config has one, CG seconds per
+    iteration (ray setup excluded), bf16 against f32 CG at equal criterion,
+    the autograd form against the plain calls (time-varying config), and
+    the FP64 oracle's segments/s on one host core and on all of them."""
+    import torch
+    import synth
+    import paper_1103_5904_gb300 as T
+    from oracle import siddon
+    from paper_1103_5904_gb300 import build as lib_build
+
+    lib_build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    ctx = T.Context(local_rank)
+
+    def med_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for name, cg_iters, has_bf16 in SWEEP:
+        c = synth.make_config(name)
+        g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
+        T_frames = c["n_frames"]
+        mask = (torch.from_numpy(c["mask"]).to(dev)
+                if c["mask"] is not None else None)
+        X = torch.from_numpy(c["cube"]).to(dev)
+        segs = T.tomo_count_segments(g, ptg, nu, nv, mask=mask, ctx=ctx)
+        rays = ptg.shape[0] * nu * nv
+        reps = 10 if segs < 2e10 else 5
+        y = T.tomo_project(X, g, ptg, nu, nv, mask=mask, n_frames=T_frames,
+                           ctx=ctx)
+        out = torch.empty_like(X)
+        line = {"sweep": name, "segments": int(segs), "rays": int(rays)}
+        p_ms = med_ms(lambda: T.tomo_project(X, g, ptg, nu, nv, mask=mask,
+                                             n_frames=T_frames, out=y,
+                                             ctx=ctx), reps)
+        a_ms = med_ms(lambda: T.tomo_backproject(y, g, ptg, mask=mask,
+                                                 n_frames=T_frames, out=out,
+                                                 ctx=ctx), reps)
+        line.update({"P_ms": p_ms, "PT_ms": a_ms,
+                     "P_segments_per_s": segs / (p_ms / 1e3),
+                     "PT_segments_per_s": segs / (a_ms / 1e3),
+                     "P_rays_per_s": rays / (p_ms / 1e3)})
+        if has_bf16:
+            Xb = X.to(torch.bfloat16)
+            line["P_bf16_ms"] = med_ms(lambda: T.tomo_project(
+                Xb, g, ptg, nu, nv, mask=mask, n_frames=T_frames, out=y,
+                ctx=ctx), reps)
+            line["P_bf16_segments_per_s"] = segs / (line["P_bf16_ms"] / 1e3)
+            del Xb
+        if T_frames > 1:
+            # the projector as a torch.autograd.Function: forward + backward
+            # of 0.5 ||P X||^2 against the plain P and P^T calls
+            Xg = X.clone().requires_grad_(True)
+
+            def fwd_bwd():
+                Xg.grad = None
+                P = T.autograd.project(Xg, g, ptg, nu, nv, mask=mask,
+                                       n_frames=T_frames, ctx=ctx)
+                P.backward(P.detach())
+            line["autograd_fwd_bwd_ms"] = med_ms(fwd_bwd, reps)
+            line["plain_P_plus_PT_ms"] = p_ms + a_ms
+            del Xg
+        if cg_iters:
+            # data: the projection of the cube (noise-free here: the solver's
+            # speed does not depend on the noise)
+            yd = y if T_frames == 1 else None
+            x = torch.empty_like(X)
+            cg_ms = med_ms(lambda: T.tomo_solve(
+                yd, g, ptg, mask=mask, lam=c["lam"], max_iter=cg_iters,
+                out=x, report=False, ctx=ctx), 3)
+            line["cg_iters"] = cg_iters
+            line["cg_s_per_iter"] = cg_ms / 1e3 / cg_iters
+            if has_bf16:
+                _, i32 = T.tomo_solve(yd, g, ptg, mask=mask, lam=c["lam"],
+                                      max_iter=cg_iters, out=x, ctx=ctx)
+                _, i16 = T.tomo_solve(yd, g, ptg, mask=mask, lam=c["lam"],
+                                      max_iter=int(1.5 * cg_iters), out=x,
+                                      bf16=True, ctx=ctx)
+                target = i32["J"][cg_iters] * (1 + 1e-4)
+                hit = np.flatnonzero(i16["J"] <= target)
+                k16 = int(hit[0]) if hit.size else -1
+                line["bf16_iters_to_f32_criterion"] = k16
+                if k16 > 0:
+                    b_ms = med_ms(lambda: T.tomo_solve(
+                        yd, g, ptg, mask=mask, lam=c["lam"], max_iter=k16,
+                        out=x, bf16=True, report=False, ctx=ctx), 3)
+                    line["cg_bf16_s_to_f32_criterion"] = b_ms / 1e3
+                    line["cg_f32_s"] = cg_ms / 1e3
+            del x
+        # the oracle on one core and on all host cores (seeded ray sample)
+        c_host = dict(c)
+        nthreads = siddon.get_threads()
+        if T_frames == 1:
+            siddon.set_threads(1)
+            line["oracle_segments_per_s_1core"] = oracle_sample(c_host, 1.0, 7)[0]
+            siddon.set_threads(nthreads)
+            r, cores, _, _, _ = oracle_sample(c_host, 2.0, 8)
+            line["oracle_segments_per_s_all"] = r
+            line["oracle_cores"] = cores
+        print(json.dumps(line), flush=True)
+        del X, y, out
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, local_rank, world = dist_env()
@@ -565,6 +704,8 @@ def main(argv=None):
             return 2
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, local_rank) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist
