@@ -203,6 +203,14 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
                                   cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
+    // the device marks an image for the plane forward when its pixel pitch
+    // is >= kPlaneFwdMinPitch voxels of its lateral axis; with the smallest
+    // voxel side instead, this bound is never below the device's value
+    const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
+    ctx->fwd_plane_possible = false;
+    for (size_t i = 0; i < n_img; ++i)
+        if (ptg[i].d_obs * fabs(tan(ptg[i].cdelt_u)) / dmin >= kPlaneFwdMinPitch)
+            ctx->fwd_plane_possible = true;
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
                          g->nv, n_frames, (Frame *)ctx->frames.p,
@@ -295,18 +303,17 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
     const RayRec *rays = (const RayRec *)ctx->rays.p;
     const ImgParam *prm = (const ImgParam *)ctx->params.p;
     const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
-    if (use_plane(ctx, c, t, true)) {
+    // bit 1: every image plane-synchronous; else (bit 2) the images whose
+    // hint marks the plane forward as faster, the rest per ray
+    const bool all = (ctx->plane_sync & 2) != 0;
+    if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible)) {
         const unsigned *used = (const unsigned *)ctx->layout_used.p;
-        LAUNCH(ctx, TOMO_K_LAYOUT, s,
-               launch_to_layout(cube_dev, dtype, ctx->lay1.p, 1, c, n_frames,
-                                used, done, s));
-        LAUNCH(ctx, TOMO_K_LAYOUT, s,
-               launch_to_layout(cube_dev, dtype, ctx->lay2.p, 2, c, n_frames,
-                                used, done, s));
+        for (int L = 1; L <= 2; ++L)
+            LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                   launch_to_layout(cube_dev, dtype, L == 1 ? ctx->lay1.p : ctx->lay2.p,
+                                    L, c, n_frames, used,
+                                    all ? 1u << L : 1u << (8 + L), done, s));
         PlaneCubes pc = { { cube_dev, ctx->lay1.p, ctx->lay2.p } };
-        // bit 1: every image plane-synchronous; else (bit 2) the images whose
-        // hint marks the plane forward as faster, the rest per ray
-        const bool all = (ctx->plane_sync & 2) != 0;
         if (!all)
             LAUNCH(ctx, TOMO_K_FORWARD, s,
                    launch_forward(rays, prm, cube_dev, dtype, fstride,

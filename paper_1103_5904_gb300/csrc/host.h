@@ -39,7 +39,7 @@ struct tomo_ctx {
     int adjoint_mode = 0;  // 0: float atomics; 1: bundle window; 2: tiles
     // bit 0: P^T plane-synchronous; bit 1: P plane-synchronous for every
     // image; bit 2: P plane-synchronous for the images whose hint marks it
-    // as the faster walk, per ray for the others
+    // as the faster walk (coarse pixels), per ray for the others
     int plane_sync = 5;
     tomo::Tiling tiling = { 32, 8, 8 };
     // geometry cache
@@ -50,6 +50,9 @@ struct tomo_ctx {
     tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
     // bit L set: some image of the cached geometry walks in layout L
     tomo::host::DevBuf layout_used;
+    // some image of the cached geometry may select the plane forward (a
+    // host-side upper bound of the device's per-image pixel-pitch test)
+    bool fwd_plane_possible = true;
     // cube copies (forward) / accumulators (transpose) in layouts 1 and 2
     tomo::host::DevBuf lay1, lay2;
     // solver workspace

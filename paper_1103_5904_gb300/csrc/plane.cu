@@ -293,19 +293,19 @@ bool plane_supported(const tomo_cube_geom *c)
 
 cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
                              int L, const tomo_cube_geom *c, int32_t n_frames,
-                             const unsigned *used, const double *done,
-                             cudaStream_t s)
+                             const unsigned *used, unsigned bit,
+                             const double *done, cudaStream_t s)
 {
     const LayoutMap m = layout_map(L, c->nx, c->ny, c->nz);
     const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
     if (dtype == TOMO_BF16)
         k_to_layout<uint16_t><<<layout_grid(m), 256, 0, s>>>(
             static_cast<const uint16_t *>(cube), static_cast<uint16_t *>(out),
-            m, n_frames, fstride, used, 1u << L, done);
+            m, n_frames, fstride, used, bit, done);
     else
         k_to_layout<float><<<layout_grid(m), 256, 0, s>>>(
             static_cast<const float *>(cube), static_cast<float *>(out), m,
-            n_frames, fstride, used, 1u << L, done);
+            n_frames, fstride, used, bit, done);
     return cudaGetLastError();
 }
 

@@ -52,10 +52,7 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
     const double dL = L == 0 ? vox.x : (L == 1 ? vox.y : vox.z);
     const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dL;
     const bool valid = pitch >= kPlaneMinPitch;
-    double minor = 0.0;
-    for (int a = 0; a < 3; ++a)
-        if (a != M) minor = fmax(minor, fabs(u[a]));
-    const bool fwd = valid && minor >= kPlaneFwdMinRatio * fabs(u[M]);
+    const bool fwd = valid && pitch >= kPlaneFwdMinPitch;
     return (valid ? kPlaneHintValid : 0) | (fwd ? kPlaneFwdBit : 0) | M |
            (L << 2) | ((u[M] < 0.0) ? 16 : 0);
 }
@@ -94,8 +91,13 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
         ImgParam q;
         q.gain = (float)p.gain;
         q.pad = plane_hint(p, f, nu, nv, vox);
-        if (layout_used && (q.pad & kPlaneHintValid))
-            atomicOr(layout_used, 1u << ((q.pad >> 2) & 3));
+        if (layout_used && (q.pad & kPlaneHintValid)) {
+            // bit L: a plane transpose uses layout L; bit 8 + L: so does a
+            // plane forward
+            const int L = (q.pad >> 2) & 3;
+            atomicOr(layout_used, (1u << L) |
+                                      ((q.pad & kPlaneFwdBit) ? 1u << (8 + L) : 0u));
+        }
         if (n_frames > 1) {
             int k = (int)floor(p.time);
             if (k > n_frames - 2) k = n_frames - 2;

@@ -47,13 +47,14 @@ constexpr int32_t kPlaneMaxSide = 16384;
 // atomic, is faster there (measured crossover between 0.13 and 0.20).
 constexpr double kPlaneMinPitch = 0.16;
 // Hint bit: the plane-synchronous forward is the faster one for this image.
-// Measured on 512^2 views of a 256^3 cube: the plane forward wins once the
-// steeper minor component of the central line of sight is at least 0.6 of
-// the major one (views more than ~31 degrees from an axis: two segments per
-// slab amortise its per-slab work); nearer the axes the per-ray walk's
-// lanes stay in step and it wins.
+// The per-ray forward relies on the 32 rays of a warp (8 x 4 pixels) sharing
+// L1 lines; with pixels about a voxel apart they share few, and the plane
+// forward (coalesced gathers along a row) wins: measured 1.62 against
+// 2.23 ms at 1.07 voxel (64 x 256^2 views of a 256^3 cube), while at 0.5
+// voxel the per-ray forward is as fast or faster on every configuration
+// measured (128^3 to 512^3 cubes).
 constexpr int32_t kPlaneFwdBit = 64;
-constexpr double kPlaneFwdMinRatio = 0.6;
+constexpr double kPlaneFwdMinPitch = 0.75;
 
 // Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
 // 2 = z-fastest) for the plane-synchronous walk (plane.cu).
@@ -98,7 +99,8 @@ constexpr int kMaxReduceBlocks = 2048;
 // ---- setup.cu
 // vox: voxel size per axis (for the plane-walk hint's pixel-pitch test);
 // layout_used (may be NULL): bit L is or-ed in for every image whose plane
-// hint is valid and names layout L
+// hint is valid and names layout L, bit 8 + L if its hint also selects the
+// plane forward
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
@@ -147,10 +149,11 @@ cudaError_t launch_adjoint_tiled(const RayRec *rays, const ImgParam *prm,
 // row of 32 pixels per warp.  Layout kernels return at once unless bit L of
 // *used is set.
 bool plane_supported(const tomo_cube_geom *c);
+// (copies for the forward: runs when bit `bit` of *used is set)
 cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
                              int L, const tomo_cube_geom *c, int32_t n_frames,
-                             const unsigned *used, const double *done,
-                             cudaStream_t s);
+                             const unsigned *used, unsigned bit,
+                             const double *done, cudaStream_t s);
 cudaError_t launch_add_from_layout(const float *acc, float *cube, int L,
                                    const tomo_cube_geom *c, int32_t n_frames,
                                    const unsigned *used, const double *done,
