@@ -111,8 +111,10 @@ typedef struct tomo_ctx tomo_ctx;
                                   walk of single-problem calls: bit 0 for
                                   P^T (with TOMO_OPT_ADJOINT 0); bit 1 for P
                                   on every image; bit 2 for P on the images
-                                  whose pixels are at least 0.75 voxel apart
-                                  (per ray on the others).  A set bit
+                                  where it measured faster: views within
+                                  ~1 degree of a cube-axis plane, or pixels
+                                  at least 0.75 voxel apart (per ray on the
+                                  others).  A set bit
                                   makes the rays of a warp walk the cube one
                                   plane of the image's major axis at a time,
                                   on a copy of the cube stored with the

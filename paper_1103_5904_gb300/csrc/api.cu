@@ -203,14 +203,22 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
                                   cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
-    // the device marks an image for the plane forward when its pixel pitch
-    // is >= kPlaneFwdMinPitch voxels of its lateral axis; with the smallest
-    // voxel side instead, this bound is never below the device's value
+    // whether any image may take the plane forward: the device's rule
+    // (setup.cu) evaluated from the boresight with a margin.  Only speed
+    // depends on this estimate: when it says no, the per-ray forward runs
+    // on every image.
     const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
     ctx->fwd_plane_possible = false;
-    for (size_t i = 0; i < n_img; ++i)
-        if (ptg[i].d_obs * fabs(tan(ptg[i].cdelt_u)) / dmin >= kPlaneFwdMinPitch)
+    for (size_t i = 0; i < n_img; ++i) {
+        const double cl = cos(ptg[i].lat);
+        const double w[3] = { fabs(cl * cos(ptg[i].lon)), fabs(cl * sin(ptg[i].lon)),
+                              fabs(sin(ptg[i].lat)) };
+        const double hi = fmax(w[0], fmax(w[1], w[2]));
+        const double lo = fmin(w[0], fmin(w[1], w[2])) / hi;
+        const double pitch = ptg[i].d_obs * fabs(tan(ptg[i].cdelt_u)) / dmin;
+        if (pitch >= 0.9 * kPlaneFwdMinPitch || lo < 1.5 * kPlaneFwdMaxRatio)
             ctx->fwd_plane_possible = true;
+    }
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
                          g->nv, n_frames, (Frame *)ctx->frames.p,

@@ -179,7 +179,7 @@ k_adjoint_plane_batched(const WalkDesc *__restrict__ descs,
                 PlaneScatterOp op;
                 op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.dst);
                 op.y = yv;
-                plane_walk(pr, regular, op);
+                plane_walk_for(q.pad, pr, regular, op);
                 if (live && !regular) {
                     ScatterOp op2;
                     op2.c = d.dst;

@@ -85,7 +85,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
         op.w0 = 1.0f - q.w;
         op.w1 = q.w;
         op.acc = 0.0f;
-        plane_walk(p, regular, op);
+        plane_walk_for(q.pad, p, regular, op);
         acc = op.acc;
         if (live && !regular) {
             GatherTimeOp<CubeT> op2;
@@ -101,7 +101,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
         PlaneGatherOp<CubeT> op;
         op.c = lay;
         op.acc = 0.0f;
-        plane_walk(p, regular, op);
+        plane_walk_for(q.pad, p, regular, op);
         acc = op.acc;
         if (live && !regular) {
             GatherOp<CubeT> op2;
@@ -148,7 +148,7 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
         op.c1 = op.c0 + frame_stride;
         op.y0 = yv * (1.0f - q.w);
         op.y1 = yv * q.w;
-        plane_walk(p, regular, op);
+        plane_walk_for(q.pad, p, regular, op);
         if (live && !regular) {
             ScatterTimeOp op2;
             op2.c0 = acc.c[0] + f0;
@@ -161,7 +161,7 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
         PlaneScatterOp op;
         op.c = lay;
         op.y = yv;
-        plane_walk(p, regular, op);
+        plane_walk_for(q.pad, p, regular, op);
         if (live && !regular) {
             ScatterOp op2;
             op2.c = acc.c[0];

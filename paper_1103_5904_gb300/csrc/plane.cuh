@@ -91,35 +91,68 @@ __device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
     return p.AM > 0.0f && (signbit(dM) != 0) == neg && ok1 && ok2;
 }
 
+// First slab j >= 0 whose far plane fmaf(j, AM, t0M) lies beyond x (at or
+// beyond x when `reach`).  The far planes are the walk's own float values,
+// so the answer agrees with every comparison the walk makes; the quotient
+// only gives the starting point, the two loops make it exact.
+__device__ __forceinline__ int slab_past(float AM, float t0M, float x, bool reach)
+{
+    int j = (int)fmaxf(ceilf((x - t0M) / AM), 0.0f);
+    for (;;) {
+        if (j == 0) break;
+        const float f = fmaf((float)(j - 1), AM, t0M);
+        if (reach ? f < x : f <= x) break;
+        --j;
+    }
+    for (;;) {
+        const float f = fmaf((float)j, AM, t0M);
+        if (reach ? f >= x : f > x) break;
+        ++j;
+    }
+    return j;
+}
+
 // Walks the regular lanes of the warp plane by plane; op(on, idx, len) is
 // called for every segment with on == true (len may be 0 at ties, which adds
 // an exact zero) and, with on == false, for slots without a segment (idx
 // then may lie outside the cube and must not be touched).  Every lane of the
-// warp must call this (it uses warp-wide votes); lanes with regular == false
-// only vote.
+// warp must call this (it uses warp-wide reductions); lanes with regular ==
+// false only take part in those.
 //
-// Each lane counts slabs in kM; a lane whose entry plane comes after the
-// warp's first one starts at kM = -(its offset) and waits until kM reaches 0.
-// Most slabs hold no crossing of the less steep minor axis a2 (for a view
-// near the ecliptic, a2 is z and is crossed every few tens of slabs): when
-// no lane of the warp crosses a2 in the current slab, the warp takes a fast
-// path with at most one crossing (of a1); otherwise every lane takes the
-// general three-segment body.  Both give the same segments.
-template <class Op>
+// Warp iteration i handles slab j = i - j0 of every lane (j0: how many M
+// planes after the warp's first one the lane enters).  Each lane knows how
+// many slabs it walks (jend) and in which slab its next crossing of the less
+// steep minor axis a2 falls (j2); the warp runs a fast body, which allows at
+// most one crossing (of a1) per slab, in a counted loop up to the first slab
+// in which any lane crosses a2, runs the general three-segment body for that
+// slab, and recomputes the bound.  For views near the ecliptic a2 is z and
+// is crossed every few tens of slabs, so almost every slab takes the fast
+// body with no warp-wide vote.  Both bodies give the same segments.
+//
+// With kEveryGeneral, every slab takes the general body and nothing is
+// tracked: for views whose a2 component is large enough that some lane of
+// the warp crosses a2 in most slabs (the lanes' a2 crossings spread over
+// many slabs, since a row's rays differ slightly in slope and the observer
+// is ~200 cube widths away), the votes and bound updates would cost more
+// than they save.
+template <bool kEveryGeneral, class Op>
 __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
                                            Op &op)
 {
     const unsigned full = 0xffffffffu;
     const int kmin = __reduce_min_sync(full, regular ? p.key : INT_MAX);
-    bool pending = regular;
-    float kM = regular ? (float)(kmin - p.key) : 0.0f;
+    const int j0 = regular ? p.key - kmin : 0;
+    // the walk ends in the first slab whose far plane reaches the chord
+    const int jend = regular ? 1 + slab_past(p.AM, p.t0M, p.chord, true) : 0;
+    const int i_end = __reduce_max_sync(full, regular ? j0 + jend : 0);
     float t = 0.0f, k1 = 0.0f, k2 = 0.0f;
     float t1 = p.t01, t2 = p.t02;
     int idx = p.idx;
-    while (__any_sync(full, pending)) {
-        const bool go = pending && kM >= 0.0f;
-        const float te = fminf(fmaf(kM, p.AM, p.t0M), p.chord);
-        if (__any_sync(full, go && t2 < te)) {
+    if (kEveryGeneral) {
+        for (int i = 0; i < i_end; ++i) {
+            const int j = i - j0;
+            const bool go = (unsigned)j < (unsigned)jend;
+            const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
             const bool first1 = t1 <= t2;
             const float ta = first1 ? t1 : t2;
             const float tb = first1 ? t2 : t1;
@@ -132,21 +165,64 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
             k2 = c2 ? k2 + 1.0f : k2;
             t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
             t2 = c2 ? fmaf(k2, p.A2, p.t02) : t2;
-            idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0);
-        } else {
+            idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? p.sM : 0);
+            t = go ? te : t;
+        }
+        return;
+    }
+    // slab of the next a2 crossing (the first whose far plane lies beyond it)
+    int j2 = (regular && t2 < p.chord) ? slab_past(p.AM, p.t0M, t2, false) : INT_MAX;
+    int next = __reduce_min_sync(full, j2 < jend ? j0 + j2 : INT_MAX);
+    int i = 0;
+    while (i < i_end) {
+        const int stop = next < i_end ? next : i_end;
+        for (; i < stop; ++i) {
+            const int j = i - j0;
+            const bool go = (unsigned)j < (unsigned)jend;
+            const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
             const bool c1 = go && t1 < te;
             op(go, idx, fminf(t1, te) - t);
             op(c1, idx + p.s1, te - t1);
             k1 = c1 ? k1 + 1.0f : k1;
             t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
-            idx += c1 ? p.s1 : 0;
+            idx += (c1 ? p.s1 : 0) + (go ? p.sM : 0);
+            t = go ? te : t;
         }
-        const bool more = te < p.chord;
-        pending = pending && (!go || more);
-        idx += (go && more) ? p.sM : 0;
+        if (i >= i_end) break;
+        // slab i holds a crossing of a2 for at least one lane
+        const int j = i - j0;
+        const bool go = (unsigned)j < (unsigned)jend;
+        const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
+        const bool first1 = t1 <= t2;
+        const float ta = first1 ? t1 : t2;
+        const float tb = first1 ? t2 : t1;
+        const int sa = first1 ? p.s1 : p.s2;
+        op(go, idx, fminf(ta, te) - t);
+        op(go && ta < te, idx + sa, fminf(tb, te) - ta);
+        op(go && tb < te, idx + p.s1 + p.s2, te - tb);
+        const bool c1 = go && t1 < te, c2 = go && t2 < te;
+        k1 = c1 ? k1 + 1.0f : k1;
+        k2 = c2 ? k2 + 1.0f : k2;
+        t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
+        t2 = c2 ? fmaf(k2, p.A2, p.t02) : t2;
+        idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? p.sM : 0);
         t = go ? te : t;
-        kM += 1.0f;
+        if (c2) j2 = t2 < p.chord ? slab_past(p.AM, p.t0M, t2, false) : INT_MAX;
+        ++i;
+        next = __reduce_min_sync(full, j2 < jend ? j0 + j2 : INT_MAX);
     }
+}
+
+// The walk variant the image's hint selects (the hint is the same for the
+// whole CTA, so every lane of a warp takes the same branch).
+template <class Op>
+__device__ __forceinline__ void plane_walk_for(int hint, const PlaneRay &p,
+                                               bool regular, Op &op)
+{
+    if (hint & kPlaneGeneralBit)
+        plane_walk<true>(p, regular, op);
+    else
+        plane_walk<false>(p, regular, op);
 }
 
 template <typename CubeT>

@@ -28,7 +28,8 @@ namespace {
 // direction by ~e1; at a fixed M plane the ray through u + e1 d is displaced
 // along e1 - u e1_M / u_M.  The hint is marked valid only when neighbouring
 // pixels are at least kPlaneMinPitch voxels of L apart at the distance of
-// Sun centre.  Only the walk's speed depends on the hint.
+// Sun centre; the forward and walk-variant bits follow the measured rules
+// in tomo_internal.cuh.  Only the walks' speed depends on the hint.
 __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
                               int nv, double3 vox)
 {
@@ -52,9 +53,15 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
     const double dL = L == 0 ? vox.x : (L == 1 ? vox.y : vox.z);
     const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dL;
     const bool valid = pitch >= kPlaneMinPitch;
-    const bool fwd = valid && pitch >= kPlaneFwdMinPitch;
-    return (valid ? kPlaneHintValid : 0) | (fwd ? kPlaneFwdBit : 0) | M |
-           (L << 2) | ((u[M] < 0.0) ? 16 : 0);
+    double lo = INFINITY;  // the less steep minor component
+    for (int a = 0; a < 3; ++a)
+        if (a != M) lo = fmin(lo, fabs(u[a]));
+    lo /= fabs(u[M]);
+    const bool general = lo >= kPlaneGeneralRatio;
+    const bool fwd = valid && (pitch >= kPlaneFwdMinPitch || lo < kPlaneFwdMaxRatio);
+    return (valid ? kPlaneHintValid : 0) | (fwd ? kPlaneFwdBit : 0) |
+           (general ? kPlaneGeneralBit : 0) | M | (L << 2) |
+           ((u[M] < 0.0) ? 16 : 0);
 }
 
 // One block per image: the FP64 frame, the image parameters and the tangent

@@ -46,15 +46,27 @@ constexpr int32_t kPlaneMaxSide = 16384;
 // which sums the contributions of lanes in the same voxel before its float
 // atomic, is faster there (measured crossover between 0.13 and 0.20).
 constexpr double kPlaneMinPitch = 0.16;
-// Hint bit: the plane-synchronous forward is the faster one for this image.
-// The per-ray forward relies on the 32 rays of a warp (8 x 4 pixels) sharing
-// L1 lines; with pixels about a voxel apart they share few, and the plane
-// forward (coalesced gathers along a row) wins: measured 1.62 against
-// 2.23 ms at 1.07 voxel (64 x 256^2 views of a 256^3 cube), while at 0.5
-// voxel the per-ray forward is as fast or faster on every configuration
-// measured (128^3 to 512^3 cubes).
+// Hint bits chosen by measurement (GB300, 24 views of 512^2 around a 256^3
+// cube, latitude 0-25 degrees; 64 views of 256^2 for the pixel pitch).
+// "lo" is the less steep minor direction component of the image's central
+// line of sight over the major one.
+//  * kPlaneGeneralBit (lo >= kPlaneGeneralRatio): the plane walks take the
+//    general three-segment body on every slab.  The lanes of a warp cross
+//    the a2 planes in different slabs once lo is more than about 0.02 (a
+//    row's rays differ slightly in slope, and the observer is ~200 cube
+//    widths away), so the counted fast loop keeps stopping; the transpose
+//    with the counted loop takes 0.46x the per-ray time at lo = 0 and 0.63x
+//    at lo = 0.035, where the every-slab variant takes 0.63x.
+//  * kPlaneFwdBit: the plane forward is the faster one: with the counted
+//    loop when lo < kPlaneFwdMaxRatio (0.81x the per-ray forward at lo = 0,
+//    0.94x at 0.017, 1.04x at 0.026), and whenever the pixels are at least
+//    kPlaneFwdMinPitch voxels apart, where the per-ray warps share few L1
+//    lines (1.22 against 2.14 ms at 1.07 voxel).
 constexpr int32_t kPlaneFwdBit = 64;
 constexpr double kPlaneFwdMinPitch = 0.75;
+constexpr double kPlaneFwdMaxRatio = 0.02;
+constexpr int32_t kPlaneGeneralBit = 128;
+constexpr double kPlaneGeneralRatio = 0.035;
 
 // Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
 // 2 = z-fastest) for the plane-synchronous walk (plane.cu).
