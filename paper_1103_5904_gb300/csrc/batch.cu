@@ -209,7 +209,7 @@ k_add_from_layout_batched(const LayoutJob *__restrict__ jobs,
         const int j = owner(prefix, n_jobs, item);
         const LayoutJob J = jobs[j];
         // the same for every thread of the CTA
-        if (!(*J.used & (1u << J.L)) || (J.done != nullptr && *J.done != 0.0))
+        if (!(*J.used & J.bit) || (J.done != nullptr && *J.done != 0.0))
             continue;
         const int64_t k = item - prefix[j];
         const int x0 = (int)(k % J.tiles_x) * 32;
@@ -230,6 +230,120 @@ k_add_from_layout_batched(const LayoutJob *__restrict__ jobs,
             if (b < J.nb && x < J.nx) J.cube[x + J.sb * b + J.sc * c] += tile[i][tx];
         }
         __syncthreads();
+    }
+}
+
+// The problems' cubes into their layout copies (the inverse tile move of
+// k_add_from_layout_batched: read along x, write along b).
+__global__ void __launch_bounds__(kThreads)
+k_to_layout_batched(const LayoutJob *__restrict__ jobs,
+                    const int64_t *__restrict__ prefix, int n_jobs)
+{
+    __shared__ float tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t n_items = prefix[n_jobs];
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int j = owner(prefix, n_jobs, item);
+        const LayoutJob J = jobs[j];
+        // the same for every thread of the CTA
+        if (!(*J.used & J.bit) || (J.done != nullptr && *J.done != 0.0))
+            continue;
+        const int64_t k = item - prefix[j];
+        const int x0 = (int)(k % J.tiles_x) * 32;
+        const int64_t r = k / J.tiles_x;
+        const int b0 = (int)(r % J.tiles_b) * 32;
+        const int c = (int)(r / J.tiles_b);
+        for (int i = ty; i < 32; i += 8) {
+            const int b = b0 + i, x = x0 + tx;
+            if (b < J.nb && x < J.nx) tile[i][tx] = J.cube[x + J.sb * b + J.sc * c];
+        }
+        __syncthreads();
+        for (int i = ty; i < 32; i += 8) {
+            const int x = x0 + i, b = b0 + tx;
+            if (b < J.nb && x < J.nx)
+                J.acc[b + (int64_t)J.nb * (x + (int64_t)J.nx * c)] = tile[tx][i];
+        }
+        __syncthreads();
+    }
+}
+
+// Forward projection over the plane tiles of every problem, with the work
+// queue of k_walk_batched.  A CTA covers one image; when its hint selects
+// the plane forward the warps walk plane by plane on the layout copies
+// (irregular lanes per ray on the native cube), otherwise every lane walks
+// its own ray.  All lanes of a warp take part in the plane walk's votes.
+__global__ void __launch_bounds__(kThreads, 5)
+k_forward_plane_batched(const WalkDesc *__restrict__ descs,
+                        const int64_t *__restrict__ prefix,
+                        const int2 *__restrict__ sched, int64_t n_chunks,
+                        unsigned long long *next_item)
+{
+    __shared__ long long s_item;
+    const int lane = threadIdx.x & 31;
+    const int wt = threadIdx.x >> 5;  // image row of the tile
+    const int64_t n_items = n_chunks * kSchedGroup;
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(next_item, 1ull);
+    __syncthreads();
+    int64_t item = s_item;
+    while (item < n_items) {
+        unsigned long long ahead = 0;
+        if (threadIdx.x == 0) ahead = atomicAdd(next_item, 1ull);
+        const int2 ch = sched[item / kSchedGroup];
+        const int p = ch.x;
+        const int t = ch.y + (int)(item % kSchedGroup);
+        // t, p, the done flag and the image hint are the same for every
+        // thread of the CTA
+        if (t < (int)(prefix[p + 1] - prefix[p])) {
+            const WalkDesc d = descs[p];
+            if (d.done == nullptr || *d.done == 0.0) {
+                const int tiles_u = (d.nu + kPlaneTileU - 1) / kPlaneTileU;
+                const int tiles_v = (d.nv + kPlaneTileV - 1) / kPlaneTileV;
+                const int tu = t % tiles_u;
+                const int rest = t / tiles_u;
+                const int tv = rest % tiles_v;
+                const int img = rest / tiles_v;
+                const int iu = tu * kPlaneTileU + lane;
+                const int iv = tv * kPlaneTileV + wt;
+                const bool in_img = iu < d.nu && iv < d.nv;
+                const int64_t id = ((int64_t)img * d.nv + iv) * d.nu + iu;
+                const ImgParam q = d.prm[img];
+                RayRec r;
+                r.chord = -1.0f;
+                if (in_img && (d.mask == nullptr || d.mask[id] == 0))
+                    r = load_ray(d.rays + id);
+                const bool live = r.chord > 0.0f;
+                float acc = 0.0f;
+                if (q.pad & kPlaneFwdBit) {
+                    PlaneRay pr;
+                    const bool regular =
+                        live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr);
+                    const int L = (q.pad >> 2) & 3;
+                    PlaneGatherOp<float> op;
+                    op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.src);
+                    op.acc = 0.0f;
+                    plane_walk_for(q.pad, pr, regular, op);
+                    acc = op.acc;
+                    if (live && !regular) {
+                        GatherOp<float> op2;
+                        op2.c = d.src;
+                        op2.acc = 0.0f;
+                        siddon_walk(r, d.nx, d.nxny, op2);
+                        acc = op2.acc;
+                    }
+                } else if (live) {
+                    GatherOp<float> op2;
+                    op2.c = d.src;
+                    op2.acc = 0.0f;
+                    siddon_walk(r, d.nx, d.nxny, op2);
+                    acc = op2.acc;
+                }
+                if (in_img) d.dst[id] = q.gain * acc;
+            }
+        }
+        __syncthreads();  // every thread has read s_item
+        if (threadIdx.x == 0) s_item = (long long)ahead;
+        __syncthreads();
+        item = s_item;
     }
 }
 
@@ -367,10 +481,13 @@ int walk_batched_blocks_per_sm()
 
 int plane_batched_blocks_per_sm()
 {
-    int q = 0;
+    int q = 0, f = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &q, k_adjoint_plane_batched, kThreads, 0) != cudaSuccess)
+            &q, k_adjoint_plane_batched, kThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &f, k_forward_plane_batched, kThreads, 0) != cudaSuccess)
         return 1;
+    q = q < f ? q : f;
     return q > 0 ? q : 1;
 }
 
@@ -405,6 +522,26 @@ cudaError_t launch_add_from_layout_batched(const LayoutJob *jobs,
 {
     if (n_jobs <= 0) return cudaSuccess;
     k_add_from_layout_batched<<<grid, kThreads, 0, s>>>(jobs, prefix, n_jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_layout_batched(const LayoutJob *jobs,
+                                     const int64_t *prefix, int n_jobs,
+                                     int grid, cudaStream_t s)
+{
+    if (n_jobs <= 0) return cudaSuccess;
+    k_to_layout_batched<<<grid, kThreads, 0, s>>>(jobs, prefix, n_jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_plane_batched(const WalkDesc *descs,
+                                         const int64_t *prefix,
+                                         const int2 *sched, int64_t n_chunks,
+                                         unsigned long long *next_item,
+                                         int grid, cudaStream_t s)
+{
+    k_forward_plane_batched<<<grid, kThreads, 0, s>>>(descs, prefix, sched,
+                                                      n_chunks, next_item);
     return cudaGetLastError();
 }
 

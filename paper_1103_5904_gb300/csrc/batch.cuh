@@ -32,17 +32,21 @@ struct WalkDesc {
 // 32 pixels per warp.
 constexpr int kPlaneTileU = 32, kPlaneTileV = 8;
 
-// One layout accumulator of one problem, added into that problem's cube by
-// the batched combine kernel in 32 x 32 tiles of (x, b) per value of c
-// (layout L: b = y (L = 1) or z (L = 2), c = the remaining axis).
+// One layout buffer of one problem and that problem's native cube, moved in
+// 32 x 32 tiles of (x, b) per value of c (layout L: b = y (L = 1) or z
+// (L = 2), c = the remaining axis): added into the cube by the batched
+// combine kernel (transpose accumulators), or copied from the cube by the
+// batched layout-copy kernel (forward).
 struct LayoutJob {
     float *acc;
     float *cube;
-    const unsigned *used;  // bit L set: some image of the problem uses L
+    const unsigned *used;  // the job runs when (*used & bit) != 0
     const double *done;    // may be NULL
     int32_t L, nx, nb, nc;
     int64_t sb, sc;        // native strides of b and c
     int32_t tiles_x, tiles_b;
+    unsigned bit;
+    int32_t pad;
 };
 
 // One problem as seen by the batched vector kernels.
@@ -76,6 +80,19 @@ cudaError_t launch_adjoint_plane_batched(const WalkDesc *descs,
 cudaError_t launch_add_from_layout_batched(const LayoutJob *jobs,
                                            const int64_t *prefix, int n_jobs,
                                            int grid, cudaStream_t s);
+// acc = the cube in layout L, for every job
+cudaError_t launch_to_layout_batched(const LayoutJob *jobs,
+                                     const int64_t *prefix, int n_jobs,
+                                     int grid, cudaStream_t s);
+// Forward projection of every problem over the plane tiles: images whose
+// hint selects the plane forward walk plane-synchronously (on the layout
+// copies in descs[p].lay1 / lay2, made by launch_to_layout_batched), the
+// others per ray.
+cudaError_t launch_forward_plane_batched(const WalkDesc *descs,
+                                         const int64_t *prefix,
+                                         const int2 *sched, int64_t n_chunks,
+                                         unsigned long long *next_item,
+                                         int grid, cudaStream_t s);
 cudaError_t launch_vec_batched(int op, const VecDesc *descs,
                                const int64_t *prefix, int n_probs, bool warm,
                                double *partials, int grid, cudaStream_t s);

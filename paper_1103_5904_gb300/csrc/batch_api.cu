@@ -37,14 +37,15 @@ struct BatchPlan {
     // prefix (jobs: problem i, layout 1 / 2 at 2 i, 2 i + 1)
     std::vector<int64_t> ptile_prefix, vox_off, job_prefix;
     DevBuf ptpre_dev, psched_dev, lay, lay_used, jpre_dev;
+    DevBuf flay;  // layout copies of the forward's source cubes (2 x voxels)
     int64_t pn_chunks = 0;
     bool lay_dirty = false;
     cudaEvent_t ready = nullptr;
     // per-call descriptors of the projector / transpose entry points
-    DevBuf call_desc, call_counter, call_jobs;
+    DevBuf call_desc, call_counter, call_jobs, call_fjobs;
     // solver workspace and graph
     DevBuf vec, timg, S, partials, counters, walk_desc, vec_desc, prefixes,
-        solve_jobs;
+        solve_jobs, solve_fjobs;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t graph_launches[TOMO_K_COUNT] = { 0 };
@@ -59,10 +60,11 @@ void free_plan(tomo_ctx *ctx)
     DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
                        &p->rays, &p->tpre_dev, &p->sched_dev,
                        &p->ptpre_dev, &p->psched_dev, &p->lay, &p->lay_used,
-                       &p->jpre_dev, &p->call_desc, &p->call_counter,
-                       &p->call_jobs, &p->vec, &p->timg, &p->S,
-                       &p->partials, &p->counters, &p->walk_desc,
-                       &p->vec_desc, &p->prefixes, &p->solve_jobs };
+                       &p->jpre_dev, &p->flay, &p->call_desc,
+                       &p->call_counter, &p->call_jobs, &p->call_fjobs,
+                       &p->vec, &p->timg, &p->S, &p->partials, &p->counters,
+                       &p->walk_desc, &p->vec_desc, &p->prefixes,
+                       &p->solve_jobs, &p->solve_fjobs };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -198,6 +200,7 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         (st = ensure(ctx, P->tan_v, sizeof(double) * P->tv_off[n])) ||
         (st = ensure(ctx, P->rays, sizeof(RayRec) * P->ray_off[n])) ||
         (st = ensure(ctx, P->lay, sizeof(float) * 2 * (P->vox_off[n] > 0 ? P->vox_off[n] : 1))) ||
+        (st = ensure(ctx, P->flay, sizeof(float) * 2 * (P->vox_off[n] > 0 ? P->vox_off[n] : 1))) ||
         (st = ensure(ctx, P->lay_used, sizeof(unsigned) * n)))
         return st;
     CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0, sizeof(float) * 2 * P->vox_off[n], s));
@@ -274,8 +277,11 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
     return TOMO_OK;
 }
 
+// forward: the layout buffers are the forward's copies (flay), else the
+// transpose's accumulators (lay)
 WalkDesc walk_desc(const BatchPlan *P, const tomo_problem &p, int32_t i,
-                   const float *src, float *dst, const double *done)
+                   const float *src, float *dst, const double *done,
+                   bool forward)
 {
     WalkDesc d;
     d.rays = (const RayRec *)P->rays.p + P->ray_off[i];
@@ -293,20 +299,24 @@ WalkDesc walk_desc(const BatchPlan *P, const tomo_problem &p, int32_t i,
     d.tiles_v = (p.img.nv + d.tl.tile_v - 1) / d.tl.tile_v;
     d.ny = p.cube.ny;
     d.nz = p.cube.nz;
-    d.lay1 = (float *)P->lay.p + 2 * P->vox_off[i];
+    d.lay1 = (float *)(forward ? P->flay.p : P->lay.p) + 2 * P->vox_off[i];
     d.lay2 = d.lay1 + (P->vox_off[i + 1] - P->vox_off[i]);
     return d;
 }
 
 // Combine jobs of every problem (layouts 1 and 2) into the cubes cube[i].
+// forward: copy jobs into the forward's layout copies (run when some image
+// of the problem takes the plane forward in layout L), else combine jobs of
+// the transpose's accumulators (run when some image walks in layout L)
 std::vector<LayoutJob> layout_jobs(const BatchPlan *P, int32_t n,
                                    const tomo_problem *probs,
-                                   float *const *cubes, const double *const *done)
+                                   float *const *cubes, const double *const *done,
+                                   bool forward = false)
 {
     std::vector<LayoutJob> jobs(2 * (size_t)n);
     for (int32_t i = 0; i < n; ++i) {
         const tomo_cube_geom &c = probs[i].cube;
-        float *lay1 = (float *)P->lay.p + 2 * P->vox_off[i];
+        float *lay1 = (float *)(forward ? P->flay.p : P->lay.p) + 2 * P->vox_off[i];
         for (int L = 1; L <= 2; ++L) {
             LayoutJob &J = jobs[2 * (size_t)i + (L - 1)];
             J.acc = L == 1 ? lay1 : lay1 + (P->vox_off[i + 1] - P->vox_off[i]);
@@ -321,6 +331,8 @@ std::vector<LayoutJob> layout_jobs(const BatchPlan *P, int32_t n,
             J.sc = L == 1 ? (int64_t)c.nx * c.ny : (int64_t)c.nx;
             J.tiles_x = (c.nx + 31) / 32;
             J.tiles_b = (J.nb + 31) / 32;
+            J.bit = forward ? 1u << (8 + L) : 1u << L;
+            J.pad = 0;
         }
     }
     return jobs;
@@ -331,6 +343,17 @@ std::vector<LayoutJob> layout_jobs(const BatchPlan *P, int32_t n,
 bool batch_plane(const tomo_ctx *ctx, int32_t n, const tomo_problem *probs)
 {
     if (!(ctx->plane_sync & 1) || ctx->adjoint_mode != 0) return false;
+    for (int32_t i = 0; i < n; ++i)
+        if (!plane_supported(&probs[i].cube)) return false;
+    return true;
+}
+
+// Batched forward over plane tiles, each image taking the walk its hint
+// selects (TOMO_OPT_PLANE_SYNC bit 1 or 2; the batched path follows the
+// per-image choice in both cases).
+bool batch_plane_forward(const tomo_ctx *ctx, int32_t n, const tomo_problem *probs)
+{
+    if (!(ctx->plane_sync & (2 | 4))) return false;
     for (int32_t i = 0; i < n; ++i)
         if (!plane_supported(&probs[i].cube)) return false;
     return true;
@@ -362,9 +385,9 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
     std::vector<WalkDesc> d(n);
     for (int32_t i = 0; i < n; ++i)
         d[i] = adjoint ? walk_desc(P, probs[i], i, probs[i].images_dev,
-                                   probs[i].cube_dev, nullptr)
+                                   probs[i].cube_dev, nullptr, false)
                        : walk_desc(P, probs[i], i, probs[i].cube_dev,
-                                   probs[i].images_dev, nullptr);
+                                   probs[i].images_dev, nullptr, true);
     if (adjoint && !(flags & TOMO_ACCUMULATE))
         for (int32_t i = 0; i < n; ++i)
             CUDA_TRY(ctx, cudaMemsetAsync(probs[i].cube_dev, 0,
@@ -399,6 +422,26 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                               (const int64_t *)P->jpre_dev.p,
                                               2 * n, combine_grid(ctx), s));
         P->lay_dirty = false;
+        return TOMO_OK;
+    }
+    if (!adjoint && batch_plane_forward(ctx, n, probs)) {
+        std::vector<float *> cubes(n);
+        for (int32_t i = 0; i < n; ++i) cubes[i] = probs[i].cube_dev;
+        const std::vector<LayoutJob> jobs =
+            layout_jobs(P, n, probs, cubes.data(), nullptr, true);
+        if ((st = upload(ctx, P->call_fjobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
+            return st;
+        LAUNCH(ctx, TOMO_K_LAYOUT, s,
+               launch_to_layout_batched((const LayoutJob *)P->call_fjobs.p,
+                                        (const int64_t *)P->jpre_dev.p, 2 * n,
+                                        combine_grid(ctx), s));
+        LAUNCH(ctx, TOMO_K_FORWARD, s,
+               launch_forward_plane_batched((const WalkDesc *)P->call_desc.p,
+                                            (const int64_t *)P->ptpre_dev.p,
+                                            (const int2 *)P->psched_dev.p,
+                                            P->pn_chunks,
+                                            (unsigned long long *)P->call_counter.p,
+                                            plane_walk_grid(ctx), s));
         return TOMO_OK;
     }
     LAUNCH(ctx, adjoint ? TOMO_K_ADJOINT : TOMO_K_FORWARD, s,
@@ -591,7 +634,9 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
     h = fnv1a(h, &n_iter, sizeof(n_iter));
     h = fnv1a(h, &flags, sizeof(flags));
     const bool plane = batch_plane(ctx, n, probs);
+    const bool plane_fwd = batch_plane_forward(ctx, n, probs);
     h = fnv1a(h, &plane, sizeof(plane));
+    h = fnv1a(h, &plane_fwd, sizeof(plane_fwd));
     const size_t stride = 2 * ((size_t)n_iter + 1);
 
     if (!(P->exec && P->graph_key == h)) {
@@ -634,11 +679,11 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             const double *done = Si + S_DONE;
             float *bi = vb + voff[i], *ri = vr + voff[i], *pi = vp + voff[i],
                   *qi = vq + voff[i], *ti = tim + poff[i];
-            wd[0 * n + i] = walk_desc(P, p, i, p.images_dev, bi, nullptr);
-            wd[1 * n + i] = walk_desc(P, p, i, p.cube_dev, ti, nullptr);
-            wd[2 * n + i] = walk_desc(P, p, i, ti, qi, nullptr);
-            wd[3 * n + i] = walk_desc(P, p, i, pi, ti, done);
-            wd[4 * n + i] = walk_desc(P, p, i, ti, qi, done);
+            wd[0 * n + i] = walk_desc(P, p, i, p.images_dev, bi, nullptr, false);
+            wd[1 * n + i] = walk_desc(P, p, i, p.cube_dev, ti, nullptr, true);
+            wd[2 * n + i] = walk_desc(P, p, i, ti, qi, nullptr, false);
+            wd[3 * n + i] = walk_desc(P, p, i, pi, ti, done, true);
+            wd[4 * n + i] = walk_desc(P, p, i, ti, qi, done, false);
             VecDesc &v = vd[i];
             v.x = p.cube_dev;
             v.r = ri;
@@ -671,6 +716,17 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         jobs.insert(jobs.end(), jq.begin(), jq.end());
         jobs.insert(jobs.end(), jqd.begin(), jqd.end());
         if ((st = upload(ctx, P->solve_jobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
+            return st;
+        // copy jobs of the plane forwards: from x (warm start), from p
+        std::vector<float *> xs(n), ps(n);
+        for (int32_t i = 0; i < n; ++i) {
+            xs[i] = probs[i].cube_dev;
+            ps[i] = vp + voff[i];
+        }
+        std::vector<LayoutJob> fj = layout_jobs(P, n, probs, xs.data(), nullptr, true);
+        const std::vector<LayoutJob> fp = layout_jobs(P, n, probs, ps.data(), dn.data(), true);
+        fj.insert(fj.end(), fp.begin(), fp.end());
+        if ((st = upload(ctx, P->solve_fjobs, fj.data(), sizeof(LayoutJob) * fj.size(), s)))
             return st;
         if (P->lay_dirty)
             CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0,
@@ -721,6 +777,25 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int2 *psch = (const int2 *)P->psched_dev.p;
         const int cgrid = combine_grid(ctx);
         const int pgrid = plane_walk_grid(ctx);
+        const LayoutJob *FJ = (const LayoutJob *)P->solve_fjobs.p;
+        // forward of walk-descriptor set `ws` (copy-job set `js` for the
+        // plane forward)
+#define CAP_FWD(ws, js)                                                      \
+    do {                                                                     \
+        if (plane_fwd) {                                                     \
+            CAP(TOMO_K_LAYOUT,                                               \
+                launch_to_layout_batched(FJ + (js) * 2 * n, jpre, 2 * n,     \
+                                         cgrid, c));                         \
+            CAP(TOMO_K_FORWARD,                                              \
+                launch_forward_plane_batched(W + (ws) * n, ptile_pre, psch,  \
+                                             P->pn_chunks, ctr + next_ctr++, \
+                                             pgrid, c));                     \
+        } else {                                                             \
+            CAP(TOMO_K_FORWARD,                                              \
+                launch_walk_batched(false, W + (ws) * n, tile_pre, sch, nch, \
+                                    ctr + next_ctr++, wgrid, c));            \
+        }                                                                    \
+    } while (0)
 #define CAP_ADJ(ws, js)                                                      \
     do {                                                                     \
         if (plane) {                                                         \
@@ -751,8 +826,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         if (warm) {
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR_X, V, vox_pre, n, warm,
                                                  part, vgrid, c));
-            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 1 * n, tile_pre, sch, nch,
-                                                ctr + next_ctr++, wgrid, c));
+            CAP_FWD(1, 0);
             CAP_ADJ(2, 1);
         }
         CAP(TOMO_K_VECTOR, launch_vec_batched(BV_INIT, V, vox_pre, n, warm, part,
@@ -760,8 +834,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         CAP(TOMO_K_VECTOR, launch_finalize_batched(BV_INIT, V, vox_pre, n, 0.0,
                                                    part, c));
         for (int32_t k = 0; k < n_iter; ++k) {
-            CAP(TOMO_K_FORWARD, launch_walk_batched(false, W + 3 * n, tile_pre, sch, nch,
-                                                ctr + next_ctr++, wgrid, c));
+            CAP_FWD(3, 1);
             CAP(TOMO_K_PRIOR, launch_vec_batched(BV_PRIOR, V, vox_pre, n, warm,
                                                  part, vgrid, c));
             CAP_ADJ(4, 2);
@@ -777,6 +850,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                                                   part, vgrid, c));
         }
 #undef CAP_ADJ
+#undef CAP_FWD
 #undef CAP
         cudaGraph_t g = nullptr;
         const cudaError_t e_end = cudaStreamEndCapture(c, &g);
