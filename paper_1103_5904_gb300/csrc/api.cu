@@ -203,21 +203,11 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
                                   cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
-    // whether any image may take the plane forward: the device's rule
-    // (setup.cu) evaluated from the boresight with a margin.  Only speed
-    // depends on this estimate: when it says no, the per-ray forward runs
-    // on every image.
-    const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
     ctx->fwd_plane_possible = false;
+    ctx->plane_possible = false;
     for (size_t i = 0; i < n_img; ++i) {
-        const double cl = cos(ptg[i].lat);
-        const double w[3] = { fabs(cl * cos(ptg[i].lon)), fabs(cl * sin(ptg[i].lon)),
-                              fabs(sin(ptg[i].lat)) };
-        const double hi = fmax(w[0], fmax(w[1], w[2]));
-        const double lo = fmin(w[0], fmin(w[1], w[2])) / hi;
-        const double pitch = ptg[i].d_obs * fabs(tan(ptg[i].cdelt_u)) / dmin;
-        if (pitch >= 0.9 * kPlaneFwdMinPitch || lo < 1.5 * kPlaneFwdMaxRatio)
-            ctx->fwd_plane_possible = true;
+        ctx->plane_possible |= plane_estimate(ptg[i], c);
+        ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c);
     }
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
@@ -279,6 +269,27 @@ cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
     return launch_adjoint(rays, prm, images, mask, cube, fstride, n_frames > 1,
                           g->n_img, g->nu, g->nv, c->nx, c->nx * c->ny, t,
                           done, s);
+}
+
+// The device's rules (setup.cu) evaluated from the boresight, with margins
+// towards "may"; the pixel pitch with the smallest voxel side.
+bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c)
+{
+    const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
+    return p.d_obs * fabs(tan(p.cdelt_u)) / dmin >= 0.9 * kPlaneMinPitch;
+}
+
+bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c)
+{
+    if (!plane_estimate(p, c)) return false;
+    const double cl = cos(p.lat);
+    const double w[3] = { fabs(cl * cos(p.lon)), fabs(cl * sin(p.lon)),
+                          fabs(sin(p.lat)) };
+    const double hi = fmax(w[0], fmax(w[1], w[2]));
+    const double lo = fmin(w[0], fmin(w[1], w[2])) / hi;
+    const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
+    const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dmin;
+    return pitch >= 0.9 * kPlaneFwdMinPitch || lo < 1.5 * kPlaneFwdMaxRatio;
 }
 
 bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
@@ -349,7 +360,7 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
 {
     const RayRec *rays = (const RayRec *)ctx->rays.p;
     const ImgParam *prm = (const ImgParam *)ctx->params.p;
-    if (use_plane(ctx, c, t, false)) {
+    if (use_plane(ctx, c, t, false) && ctx->plane_possible) {
         const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
         const unsigned *used = (const unsigned *)ctx->layout_used.p;
         float *a1 = (float *)ctx->lay1.p, *a2 = (float *)ctx->lay2.p;

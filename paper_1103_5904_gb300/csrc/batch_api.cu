@@ -37,6 +37,12 @@ struct BatchPlan {
     // prefix (jobs: problem i, layout 1 / 2 at 2 i, 2 i + 1)
     std::vector<int64_t> ptile_prefix, vox_off, job_prefix;
     DevBuf ptpre_dev, psched_dev, lay, lay_used, jpre_dev;
+    // with the plane walks on, problems whose pixels are too dense for them
+    // (host estimate) walk per ray with their own tile shapes: tile prefix
+    // and schedule of those problems only (the plane prefix holds the rest)
+    std::vector<int64_t> rtile_prefix;
+    DevBuf rtpre_dev, rsched_dev;
+    int64_t rn_chunks = 0;
     DevBuf flay;  // layout copies of the forward's source cubes (2 x voxels)
     int64_t pn_chunks = 0;
     bool lay_dirty = false;
@@ -59,7 +65,8 @@ void free_plan(tomo_ctx *ctx)
     if (!p) return;
     DevBuf *bufs[] = { &p->ptg, &p->frames, &p->tan_u, &p->tan_v, &p->params,
                        &p->rays, &p->tpre_dev, &p->sched_dev,
-                       &p->ptpre_dev, &p->psched_dev, &p->lay, &p->lay_used,
+                       &p->ptpre_dev, &p->psched_dev, &p->rtpre_dev,
+                       &p->rsched_dev, &p->lay, &p->lay_used,
                        &p->jpre_dev, &p->flay, &p->call_desc,
                        &p->call_counter, &p->call_jobs, &p->call_fjobs,
                        &p->vec, &p->timg, &p->S, &p->partials, &p->counters,
@@ -164,6 +171,7 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
     P->tv_off.assign(n + 1, 0);
     P->tile_prefix.assign(n + 1, 0);
     P->ptile_prefix.assign(n + 1, 0);
+    P->rtile_prefix.assign(n + 1, 0);
     P->vox_off.assign(n + 1, 0);
     P->job_prefix.assign(2 * (size_t)n + 1, 0);
     P->tl.assign(n, kDefaultTiling);
@@ -178,10 +186,14 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                               ((g.nu + P->tl[i].tile_u - 1) / P->tl[i].tile_u) *
                               ((g.nv + P->tl[i].tile_v - 1) / P->tl[i].tile_v);
         P->tile_prefix[i + 1] = P->tile_prefix[i] + tiles;
+        bool plane_ok = false;
+        for (int32_t k = 0; k < g.n_img; ++k)
+            plane_ok |= plane_estimate(probs[i].pointing_host[k], &probs[i].cube);
         P->ptile_prefix[i + 1] =
-            P->ptile_prefix[i] + (int64_t)g.n_img *
+            P->ptile_prefix[i] + (plane_ok ? (int64_t)g.n_img *
                                      ((g.nu + kPlaneTileU - 1) / kPlaneTileU) *
-                                     ((g.nv + kPlaneTileV - 1) / kPlaneTileV);
+                                     ((g.nv + kPlaneTileV - 1) / kPlaneTileV) : 0);
+        P->rtile_prefix[i + 1] = P->rtile_prefix[i] + (plane_ok ? 0 : tiles);
         const tomo_cube_geom &c = probs[i].cube;
         P->vox_off[i + 1] = P->vox_off[i] + (int64_t)c.nx * c.ny * c.nz;
         for (int L = 1; L <= 2; ++L) {
@@ -232,43 +244,45 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                 p.img.nu, p.img.nv,
                                 (RayRec *)P->rays.p + P->ray_off[i], s));
     }
-    // walk schedule: groups of kSchedGroup tiles dealt round-robin over
-    // the problems
-    std::vector<int2> sched;
-    std::vector<int64_t> next(n, 0);
-    for (bool any = true; any;) {
-        any = false;
-        for (int32_t i = 0; i < n; ++i) {
-            if (next[i] < P->tile_prefix[i + 1] - P->tile_prefix[i]) {
-                sched.push_back(make_int2(i, (int)next[i]));
-                next[i] += kSchedGroup;
-                any = true;
+    // walk schedules: groups of kSchedGroup tiles of one problem, dealt
+    // round-robin over the problems (all problems per ray; the plane-walk
+    // problems in plane tiles; the others per ray)
+    auto deal = [n](const std::vector<int64_t> &pre) {
+        std::vector<int2> out;
+        std::vector<int64_t> next(n, 0);
+        for (bool any = true; any;) {
+            any = false;
+            for (int32_t i = 0; i < n; ++i) {
+                if (next[i] < pre[i + 1] - pre[i]) {
+                    out.push_back(make_int2(i, (int)next[i]));
+                    next[i] += kSchedGroup;
+                    any = true;
+                }
             }
         }
-    }
+        return out;
+    };
+    std::vector<int2> sched = deal(P->tile_prefix);
+    std::vector<int2> psched = deal(P->ptile_prefix);
+    std::vector<int2> rsched = deal(P->rtile_prefix);
     P->n_chunks = (int64_t)sched.size();
-    // the same for the plane tiles of the plane-synchronous transpose
-    std::vector<int2> psched;
-    next.assign(n, 0);
-    for (bool any = true; any;) {
-        any = false;
-        for (int32_t i = 0; i < n; ++i) {
-            if (next[i] < P->ptile_prefix[i + 1] - P->ptile_prefix[i]) {
-                psched.push_back(make_int2(i, (int)next[i]));
-                next[i] += kSchedGroup;
-                any = true;
-            }
-        }
-    }
     P->pn_chunks = (int64_t)psched.size();
+    P->rn_chunks = (int64_t)rsched.size();
+    // an empty schedule still gets a (never read) element to upload
+    for (std::vector<int2> *v : { &sched, &psched, &rsched })
+        if (v->empty()) v->push_back(make_int2(0, 0));
     if ((st = upload(ctx, P->tpre_dev, P->tile_prefix.data(),
                      sizeof(int64_t) * (n + 1), s)) ||
         (st = upload(ctx, P->sched_dev, sched.data(),
-                     sizeof(int2) * (sched.empty() ? 1 : sched.size()), s)) ||
+                     sizeof(int2) * sched.size(), s)) ||
         (st = upload(ctx, P->ptpre_dev, P->ptile_prefix.data(),
                      sizeof(int64_t) * (n + 1), s)) ||
         (st = upload(ctx, P->psched_dev, psched.data(),
-                     sizeof(int2) * (psched.empty() ? 1 : psched.size()), s)) ||
+                     sizeof(int2) * psched.size(), s)) ||
+        (st = upload(ctx, P->rtpre_dev, P->rtile_prefix.data(),
+                     sizeof(int64_t) * (n + 1), s)) ||
+        (st = upload(ctx, P->rsched_dev, rsched.data(),
+                     sizeof(int2) * rsched.size(), s)) ||
         (st = upload(ctx, P->jpre_dev, P->job_prefix.data(),
                      sizeof(int64_t) * P->job_prefix.size(), s)))
         return st;
@@ -395,11 +409,14 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                               probs[i].cube.ny * probs[i].cube.nz,
                                           s));
     if (P->tile_prefix[n] == 0) return TOMO_OK;
+    // two queue counters: the plane-tile walk and the per-ray walk of the
+    // problems too dense for it
     if ((st = upload(ctx, P->call_desc, d.data(), sizeof(WalkDesc) * n, s)) ||
-        (st = ensure(ctx, P->call_counter, sizeof(unsigned long long))))
+        (st = ensure(ctx, P->call_counter, 2 * sizeof(unsigned long long))))
         return st;
     CUDA_TRY(ctx, cudaMemsetAsync(P->call_counter.p, 0,
-                                  sizeof(unsigned long long), s));
+                                  2 * sizeof(unsigned long long), s));
+    unsigned long long *ctr2 = (unsigned long long *)P->call_counter.p;
     if (adjoint && batch_plane(ctx, n, probs)) {
         if (P->lay_dirty)
             CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0,
@@ -410,13 +427,19 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         if ((st = upload(ctx, P->call_jobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
             return st;
         P->lay_dirty = true;
-        LAUNCH(ctx, TOMO_K_ADJOINT, s,
-               launch_adjoint_plane_batched((const WalkDesc *)P->call_desc.p,
-                                            (const int64_t *)P->ptpre_dev.p,
-                                            (const int2 *)P->psched_dev.p,
-                                            P->pn_chunks,
-                                            (unsigned long long *)P->call_counter.p,
-                                            plane_walk_grid(ctx), s));
+        if (P->pn_chunks > 0)
+            LAUNCH(ctx, TOMO_K_ADJOINT, s,
+                   launch_adjoint_plane_batched((const WalkDesc *)P->call_desc.p,
+                                                (const int64_t *)P->ptpre_dev.p,
+                                                (const int2 *)P->psched_dev.p,
+                                                P->pn_chunks, ctr2,
+                                                plane_walk_grid(ctx), s));
+        if (P->rn_chunks > 0)
+            LAUNCH(ctx, TOMO_K_ADJOINT, s,
+                   launch_walk_batched(true, (const WalkDesc *)P->call_desc.p,
+                                       (const int64_t *)P->rtpre_dev.p,
+                                       (const int2 *)P->rsched_dev.p,
+                                       P->rn_chunks, ctr2 + 1, walk_grid(ctx), s));
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
                launch_add_from_layout_batched((const LayoutJob *)P->call_jobs.p,
                                               (const int64_t *)P->jpre_dev.p,
@@ -435,13 +458,19 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                launch_to_layout_batched((const LayoutJob *)P->call_fjobs.p,
                                         (const int64_t *)P->jpre_dev.p, 2 * n,
                                         combine_grid(ctx), s));
-        LAUNCH(ctx, TOMO_K_FORWARD, s,
-               launch_forward_plane_batched((const WalkDesc *)P->call_desc.p,
-                                            (const int64_t *)P->ptpre_dev.p,
-                                            (const int2 *)P->psched_dev.p,
-                                            P->pn_chunks,
-                                            (unsigned long long *)P->call_counter.p,
-                                            plane_walk_grid(ctx), s));
+        if (P->pn_chunks > 0)
+            LAUNCH(ctx, TOMO_K_FORWARD, s,
+                   launch_forward_plane_batched((const WalkDesc *)P->call_desc.p,
+                                                (const int64_t *)P->ptpre_dev.p,
+                                                (const int2 *)P->psched_dev.p,
+                                                P->pn_chunks, ctr2,
+                                                plane_walk_grid(ctx), s));
+        if (P->rn_chunks > 0)
+            LAUNCH(ctx, TOMO_K_FORWARD, s,
+                   launch_walk_batched(false, (const WalkDesc *)P->call_desc.p,
+                                       (const int64_t *)P->rtpre_dev.p,
+                                       (const int2 *)P->rsched_dev.p,
+                                       P->rn_chunks, ctr2 + 1, walk_grid(ctx), s));
         return TOMO_OK;
     }
     LAUNCH(ctx, adjoint ? TOMO_K_ADJOINT : TOMO_K_FORWARD, s,
@@ -659,7 +688,9 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         }
         const int64_t NV = voff[n];
         const int64_t max_items = vitems[n] > pitems[n] ? vitems[n] : pitems[n];
-        const int n_walks = 1 + (warm ? 2 : 0) + 2 * n_iter;  // queue counters
+        // queue counters: up to two walks (plane tiles, dense problems per
+        // ray) per projection
+        const int n_walks = 2 * (1 + (warm ? 2 : 0) + 2 * n_iter);
         if ((st = ensure(ctx, P->vec, sizeof(float) * 4 * NV)) ||
             (st = ensure(ctx, P->timg, sizeof(float) * (poff[n] > 0 ? poff[n] : 1))) ||
             (st = ensure(ctx, P->S, sizeof(double) * n * (S_NSLOTS + stride))) ||
@@ -778,18 +809,26 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int cgrid = combine_grid(ctx);
         const int pgrid = plane_walk_grid(ctx);
         const LayoutJob *FJ = (const LayoutJob *)P->solve_fjobs.p;
+        const int64_t *rtile_pre = (const int64_t *)P->rtpre_dev.p;
+        const int2 *rsch = (const int2 *)P->rsched_dev.p;
         // forward of walk-descriptor set `ws` (copy-job set `js` for the
-        // plane forward)
+        // plane forward; problems too dense for the plane walks per ray)
 #define CAP_FWD(ws, js)                                                      \
     do {                                                                     \
         if (plane_fwd) {                                                     \
             CAP(TOMO_K_LAYOUT,                                               \
                 launch_to_layout_batched(FJ + (js) * 2 * n, jpre, 2 * n,     \
                                          cgrid, c));                         \
-            CAP(TOMO_K_FORWARD,                                              \
-                launch_forward_plane_batched(W + (ws) * n, ptile_pre, psch,  \
-                                             P->pn_chunks, ctr + next_ctr++, \
-                                             pgrid, c));                     \
+            if (P->pn_chunks > 0)                                            \
+                CAP(TOMO_K_FORWARD,                                          \
+                    launch_forward_plane_batched(W + (ws) * n, ptile_pre,    \
+                                                 psch, P->pn_chunks,         \
+                                                 ctr + next_ctr++, pgrid, c)); \
+            if (P->rn_chunks > 0)                                            \
+                CAP(TOMO_K_FORWARD,                                          \
+                    launch_walk_batched(false, W + (ws) * n, rtile_pre, rsch, \
+                                        P->rn_chunks, ctr + next_ctr++,      \
+                                        wgrid, c));                          \
         } else {                                                             \
             CAP(TOMO_K_FORWARD,                                              \
                 launch_walk_batched(false, W + (ws) * n, tile_pre, sch, nch, \
@@ -799,10 +838,16 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
 #define CAP_ADJ(ws, js)                                                      \
     do {                                                                     \
         if (plane) {                                                         \
-            CAP(TOMO_K_ADJOINT,                                              \
-                launch_adjoint_plane_batched(W + (ws) * n, ptile_pre, psch,  \
-                                             P->pn_chunks, ctr + next_ctr++, \
-                                             pgrid, c));                     \
+            if (P->pn_chunks > 0)                                            \
+                CAP(TOMO_K_ADJOINT,                                          \
+                    launch_adjoint_plane_batched(W + (ws) * n, ptile_pre,    \
+                                                 psch, P->pn_chunks,         \
+                                                 ctr + next_ctr++, pgrid, c)); \
+            if (P->rn_chunks > 0)                                            \
+                CAP(TOMO_K_ADJOINT,                                          \
+                    launch_walk_batched(true, W + (ws) * n, rtile_pre, rsch, \
+                                        P->rn_chunks, ctr + next_ctr++,      \
+                                        wgrid, c));                          \
             CAP(TOMO_K_LAYOUT,                                               \
                 launch_add_from_layout_batched(JB + (js) * 2 * n, jpre,      \
                                                2 * n, cgrid, c));            \

@@ -53,6 +53,9 @@ struct tomo_ctx {
     // some image of the cached geometry may select the plane forward (a
     // host-side upper bound of the device's per-image pixel-pitch test)
     bool fwd_plane_possible = true;
+    // some image of the cached geometry may have a valid plane hint (the
+    // same kind of estimate; when false the per-ray transpose runs)
+    bool plane_possible = true;
     // cube copies (forward) / accumulators (transpose) in layouts 1 and 2
     tomo::host::DevBuf lay1, lay2;
     // solver workspace
@@ -115,6 +118,12 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                         const tomo_image_geom *g, Tiling t,
                         const double *done, cudaStream_t s);
 // Builds (or reuses) the context's ray records for one geometry on `s`.
+// Host estimates of the device's per-image plane-walk rules (setup.cu) from
+// the boresight: whether an image may get a valid hint, and whether it may
+// select the plane forward.  Only speed depends on them: the kernel that
+// runs when an estimate says no walks every ray per ray.
+bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c);
+bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c);
 tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          int32_t n_frames, const tomo_image_geom *g,
                          const tomo_pointing *ptg, cudaStream_t s);
