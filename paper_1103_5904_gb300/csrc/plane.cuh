@@ -254,7 +254,7 @@ struct PlaneScatterOp {
     float y;
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
-        if (on) atomicAdd(c + idx, len * y);
+        if (on) red_add(c + idx, len * y);
     }
 };
 
@@ -265,8 +265,8 @@ struct PlaneScatterTimeOp {
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
         if (on) {
-            atomicAdd(c0 + idx, len * y0);
-            atomicAdd(c1 + idx, len * y1);
+            red_add(c0 + idx, len * y0);
+            red_add(c1 + idx, len * y1);
         }
     }
 };

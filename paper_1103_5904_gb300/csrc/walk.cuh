@@ -82,6 +82,21 @@ __device__ __forceinline__ void siddon_walk(const RayRec &r, int nx, int nxny,
     }
 }
 
+// Fire-and-forget float addition into global memory (PTX red.global).
+// atomicAdd through a pointer whose address space the compiler cannot infer
+// (one read from a descriptor in global memory, as in the batched kernels)
+// compiles to a generic atomic that returns the old value; measured on
+// GB300 that made the batched transposes wait on every addition.  The
+// pointer must point to global memory (every caller passes a cube or
+// accumulator allocated with cudaMalloc).
+__device__ __forceinline__ void red_add(float *p, float v)
+{
+    asm volatile("red.global.add.f32 [%0], %1;"
+                 :
+                 : "l"(__cvta_generic_to_global(p)), "f"(v)
+                 : "memory");
+}
+
 __device__ __forceinline__ float load_voxel(const float *c, int idx)
 {
     return __ldg(c + idx);
@@ -147,7 +162,7 @@ struct ScatterOp {
                 }
             }
         }
-        if (v != 0.0f) atomicAdd(c + idx, v);
+        if (v != 0.0f) red_add(c + idx, v);
     }
 };
 
@@ -158,8 +173,8 @@ struct ScatterTimeOp {
     __device__ __forceinline__ void operator()(int idx, float len)
     {
         if (len > 0.0f) {
-            atomicAdd(c0 + idx, len * y0);
-            atomicAdd(c1 + idx, len * y1);
+            red_add(c0 + idx, len * y0);
+            red_add(c1 + idx, len * y1);
         }
     }
 };
