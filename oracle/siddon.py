@@ -18,14 +18,17 @@ _lib = None
 
 class _Cube(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("lo", C.c_double * 3),
-                ("d", C.c_double * 3)]
+                ("d", C.c_double * 3), ("r_obs", C.c_double)]
 
 
 def _cube(geom):
+    """Cube geometry; an optional ``geom["r_obs"]`` > 0 is the radius of the
+    opaque sphere at the origin where lines of sight end."""
     c = _Cube()
     c.n[:] = [geom["nx"], geom["ny"], geom["nz"]]
     c.lo[:] = [geom["x0"], geom["y0"], geom["z0"]]
     c.d[:] = [geom["dx"], geom["dy"], geom["dz"]]
+    c.r_obs = float(geom.get("r_obs", 0.0))
     return c
 
 

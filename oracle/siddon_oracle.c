@@ -50,11 +50,13 @@
 #endif
 
 /* Cube of identical voxels: counts (nx, ny, nz), minimum corner, voxel size.
- * Arrays are [nz][ny][nx], x fastest. */
+ * Arrays are [nz][ny][nx], x fastest.  r_obs > 0: radius of an opaque sphere
+ * centred at the frame origin (the photosphere); 0: no obstacle. */
 typedef struct {
     int32_t n[3];
     double lo[3];
     double d[3];
+    double r_obs;
 } orc_cube;
 
 /* Column order of one pointing record. */
@@ -134,6 +136,13 @@ int orc_ray(const double *p, int32_t iu, int32_t iv, double o[3], double u[3])
 /* Parameter interval [amin, amax] of the half-line o + a u, a >= 0, inside the
  * cube.  An axis with u_a = 0 is dropped; the ray then misses unless o_a lies
  * in [lo_a, lo_a + n_a d_a).  Returns 1 on a hit of positive length. */
+/* The part of the half-line o + a u (a >= 0, u a unit vector) that the line
+ * of sight integrates: the slab clip against the cube, ended where the ray
+ * first meets the opaque sphere if there is one.  The paper stops the
+ * integration "when the ray reaches the photosphere" (Section 4) and gives
+ * no formula; reading: the first root a of |o + a u| = r_obs ends the
+ * interval, a ray from an observer inside (or on) the sphere integrates
+ * nothing, and a ray that misses or only grazes the sphere is unchanged. */
 int orc_clip(const orc_cube *c, const double o[3], const double u[3],
              double *amin, double *amax)
 {
@@ -147,6 +156,26 @@ int orc_clip(const orc_cube *c, const double o[3], const double u[3],
         double a0 = (p0 - o[a]) / u[a], a1 = (p1 - o[a]) / u[a];
         lo = fmax(lo, fmin(a0, a1));
         hi = fmin(hi, fmax(a0, a1));
+    }
+    if (c->r_obs > 0.0) {
+        /* |o + a u|^2 = r^2.  With q = o - (o.u) u, the point of closest
+         * approach, the roots are a = -(o.u) -+ sqrt(r^2 - |q|^2); forming
+         * r^2 - |q|^2 from q avoids subtracting |o|^2 ~ (o.u)^2 from each
+         * other (the observer is ~200 radii away). */
+        double r2 = c->r_obs * c->r_obs;
+        double oo = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+        if (oo <= r2) return 0; /* observer inside the sphere */
+        double ou = o[0] * u[0] + o[1] * u[1] + o[2] * u[2];
+        double q2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double q = o[a] - ou * u[a];
+            q2 += q * q;
+        }
+        double disc = r2 - q2;
+        if (disc > 0.0) {
+            double first = -ou - sqrt(disc);
+            if (first > 0.0) hi = fmin(hi, first);
+        }
     }
     if (!(lo < hi)) return 0;
     *amin = lo;

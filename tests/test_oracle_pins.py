@@ -491,3 +491,93 @@ def test_crossing_weights():
     Pty = siddon.backproject(g, y, ptg, 10, 6, mask)
     diag = np.sqrt(sum((g["n" + a] * g["d" + a]) ** 2 for a in "xyz"))
     assert np.all(np.abs(Pty) <= Cy * min(diag, max(g["dx"], g["dy"], g["dz"]) * np.sqrt(3)) + 1e-12)
+
+
+# ------------------------------------------------------- opaque photosphere
+
+def _obs_geom(n, h, r):
+    g = synth.cube_geom(n, h)
+    g["r_obs"] = r
+    return g
+
+
+@pytest.mark.parametrize("b", [0.0, 0.31, 0.7, 0.999, 1.2, 1.4])
+def test_obstacle_axis_ray_closed_form(b):
+    """Ray along -x from (D, b, z) through the cube [-h, h]^3 (z = 0.013
+    keeps it off the voxel plane z = 0): its impact parameter is
+    p = sqrt(b^2 + z^2); it enters at x = h and, when p < 1, stops on the
+    unit sphere at x = sqrt(1 - p^2), so the segment lengths sum to
+    h - sqrt(1 - p^2); past the sphere (p > 1) the whole chord 2 h counts."""
+    h, D, z = 1.5, 215.0, 0.013
+    g = _obs_geom(30, h, 1.0)
+    idx, ln, a0, a1 = siddon.segments(g, [D, b, z], [-1.0, 0.0, 0.0])
+    p2 = b * b + z * z
+    want = h - math.sqrt(1.0 - p2) if p2 < 1.0 else 2 * h
+    assert float(np.sum(ln)) == pytest.approx(want, rel=1e-12, abs=1e-12)
+    # without the obstacle the same ray crosses the whole cube
+    g0 = _obs_geom(30, h, 0.0)
+    _, ln0, _, _ = siddon.segments(g0, [D, b, z], [-1.0, 0.0, 0.0])
+    assert float(np.sum(ln0)) == pytest.approx(2 * h, rel=1e-12)
+
+
+def test_obstacle_observer_inside_sphere_sees_nothing():
+    g = _obs_geom(10, 1.5, 1.0)
+    for o in ([0.2, 0.1, -0.3], [0.0, 0.0, 0.999]):
+        idx, ln, _, _ = siddon.segments(g, o, [0.6, 0.0, 0.8])
+        assert idx.size == 0
+
+
+def test_obstacle_brute_force_random_rays():
+    """Per-voxel slab clips ended where a scan-and-bisection search finds
+    the ray first reaching the sphere, against the oracle's closed-form
+    root, on rays aimed near the sphere (some hit it, some miss)."""
+    rng = np.random.default_rng(71)
+    g = _obs_geom(6, 1.0, 0.55)
+    for _ in range(30):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        o = rng.uniform(-0.5, 0.5, 3) - 4.0 * u
+        s_end = checks.first_hit(o, u, 0.55, 8.0)
+        want = checks.brute_force_ray(g, o, u,
+                                      np.inf if s_end is None else s_end)
+        np.testing.assert_allclose(_dense(g, o, u), want, rtol=0,
+                                   atol=1e-12)
+
+
+def test_obstacle_fine_sampling_converges():
+    rng = np.random.default_rng(72)
+    g = _obs_geom(8, 1.0, 0.6)
+    x = rng.random((8, 8, 8))
+    flat = x.reshape(-1)
+    for _ in range(4):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        o = rng.uniform(-0.3, 0.3, 3) - 5.0 * u
+        idx, ln, _, _ = siddon.segments(g, o, u)
+        exact = float(np.sum(ln * flat[idx]))
+        approx = checks.sampled_ray(g, x, o, u, 1e-4, 5.0 + 2 * np.sqrt(3),
+                                    r_obs=0.6)
+        assert abs(approx - exact) <= (len(idx) + 3) * 1e-4 * x.max()
+
+
+def test_obstacle_adjoint_identity_and_blocking_fp64():
+    """With the photosphere, <P x, y> = <x, P^T y> to FP64 rounding, no
+    voxel whose every point lies inside the sphere receives anything, and
+    the projection never exceeds the obstacle-free one for a non-negative
+    map."""
+    rng = np.random.default_rng(73)
+    g = _obs_geom(12, 1.5, 1.0)
+    ptg = synth.pointing_table([0.0, 70.0, 200.0], [5.0, -10.0, 30.0], 215.0,
+                               17, 13, 3.4)
+    x = rng.random((12, 12, 12))
+    y = rng.random((3, 13, 17))
+    Px = siddon.project(g, x, ptg, 17, 13)
+    Pty = siddon.backproject(g, y, ptg, 17, 13)
+    assert float(np.sum(Px * y)) == pytest.approx(float(np.sum(x * Pty)),
+                                                  rel=1e-12)
+    c = np.array([(i + 0.5) * g["dx"] + g["x0"] for i in range(12)])
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    far = np.sqrt(xx ** 2 + yy ** 2 + zz ** 2) + np.sqrt(3) * g["dx"] / 2
+    assert np.all(Pty[far < 1.0] == 0.0)
+    g0 = dict(g, r_obs=0.0)
+    assert np.all(Px <= siddon.project(g0, x, ptg, 17, 13) + 1e-12)
