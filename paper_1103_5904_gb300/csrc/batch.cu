@@ -197,7 +197,8 @@ k_adjoint_plane_batched(const WalkDesc *__restrict__ descs,
 
 // Layout accumulators back into the native cubes: one CTA per 32 x 32 tile
 // of (x, b) at one c, reading the accumulator along b and adding into the
-// cube along x (both coalesced); the accumulator is zeroed as it is read.
+// cube along x (both coalesced, the additions atomic); the accumulator is
+// zeroed as it is read.
 __global__ void __launch_bounds__(kThreads)
 k_add_from_layout_batched(const LayoutJob *__restrict__ jobs,
                           const int64_t *__restrict__ prefix, int n_jobs)
@@ -225,9 +226,11 @@ k_add_from_layout_batched(const LayoutJob *__restrict__ jobs,
             }
         }
         __syncthreads();
+        // the jobs of layouts 1 and 2 of one problem run in this same launch
+        // and add into the same cube: the additions must be atomic
         for (int i = ty; i < 32; i += 8) {
             const int b = b0 + i, x = x0 + tx;
-            if (b < J.nb && x < J.nx) J.cube[x + J.sb * b + J.sc * c] += tile[i][tx];
+            if (b < J.nb && x < J.nx) red_add(J.cube + x + J.sb * b + J.sc * c, tile[i][tx]);
         }
         __syncthreads();
     }

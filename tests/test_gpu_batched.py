@@ -247,3 +247,27 @@ def test_batched_mixes_plane_and_dense_problems(T):
         rel = float(torch.linalg.norm(d["cube"] - x_seq) /
                     torch.linalg.norm(x_seq))
         assert rel <= 1e-3, rel
+
+
+def test_backproject_batched_layouts_1_and_2_in_one_problem(T):
+    """One problem whose images walk in layout 1 (views along x) and in
+    layout 2 (rolled views whose pixel rows run along z): both layouts'
+    accumulators are added into the same cube in one combine launch."""
+    rng = np.random.default_rng(12)
+    g = synth.cube_geom(25, 1.5, ny=27, nz=29)
+    ptg = synth.pointing_table([0.0, 180.0, 10.0, 190.0], [0.0, 0.0, 5.0, -5.0],
+                               215.0, 37, 41, 3.4)
+    ptg[2:, 3] = np.pi / 2
+    probs = [{"geom": g, "pointing": ptg, "nu": 37, "nv": 41,
+              "cube_np": np.zeros((29, 27, 25), np.float32), "mask_np": None,
+              "lam": 0.0}]
+    y = rng.random((4, 41, 37)).astype(np.float32)
+    dp = _dev_problems(probs, [y])
+    T.tomo_backproject_batched(dp)
+    single = T.tomo_backproject(to_dev(y), g, ptg)
+    torch.testing.assert_close(dp[0]["cube"], single, rtol=1e-5,
+                               atol=1e-6 * float(single.abs().max()))
+    want = siddon.backproject(g, y, ptg, 37, 41)
+    cw = siddon.crossing_weights(g, y, ptg, 37, 41)
+    assert_transpose_close(dp[0]["cube"].cpu().numpy(), want, cw, g,
+                           "batched P^T layouts 1 + 2")
