@@ -71,6 +71,13 @@ typedef struct {
     int32_t nx, ny, nz, reserved;
     double x0, y0, z0;
     double dx, dy, dz;
+    /* Radius of an opaque sphere centred at the frame origin (the
+     * photosphere, in the cube's units), or 0 for none.  Lines of sight end
+     * where they first reach it (the paper stops the integration "when the
+     * ray reaches the photosphere", Section 4); a line of sight from an
+     * observer inside the sphere integrates nothing.  Must be finite and
+     * >= 0. */
+    double r_obs;
 } tomo_cube_geom;
 
 /* Image stack geometry: n_img images of nv rows by nu columns. */

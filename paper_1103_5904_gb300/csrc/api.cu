@@ -67,10 +67,12 @@ tomo_status check_cube(tomo_ctx *ctx, const tomo_cube_geom *c, int32_t n_frames)
                     c->nx, c->ny, c->nz);
     if (c->reserved != 0)
         return fail(ctx, TOMO_ERR_ARG, "cube geometry: reserved must be 0");
-    const double v[6] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz };
-    if (!finite_all(v, 6) || !(c->dx > 0) || !(c->dy > 0) || !(c->dz > 0))
-        return fail(ctx, TOMO_ERR_ARG, "cube corner/voxel size must be finite, "
-                                       "voxel size > 0");
+    const double v[7] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz, c->r_obs };
+    if (!finite_all(v, 7) || !(c->dx > 0) || !(c->dy > 0) || !(c->dz > 0))
+        return fail(ctx, TOMO_ERR_ARG, "cube corner/voxel size/r_obs must be "
+                                       "finite, voxel size > 0");
+    if (c->r_obs < 0)
+        return fail(ctx, TOMO_ERR_ARG, "r_obs must be >= 0");
     const int64_t nvox = (int64_t)c->nx * c->ny * c->nz;
     if (nvox > INT32_MAX)
         return fail(ctx, TOMO_ERR_UNSUPPORTED,
@@ -164,6 +166,7 @@ CubeDev cube_dev(const tomo_cube_geom *c)
     d.lo[0] = c->x0;
     d.lo[1] = c->y0;
     d.lo[2] = c->z0;
+    d.r_obs = c->r_obs;
     d.d[0] = c->dx;
     d.d[1] = c->dy;
     d.d[2] = c->dz;
@@ -179,7 +182,7 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
 {
     uint64_t h = 1469598103934665603ull;
     const int32_t cn[4] = { c->nx, c->ny, c->nz, n_frames };
-    const double cv[6] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz };
+    const double cv[7] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz, c->r_obs };
     h = fnv1a(h, cn, sizeof(cn));
     h = fnv1a(h, cv, sizeof(cv));
     h = fnv1a(h, g, sizeof(*g));

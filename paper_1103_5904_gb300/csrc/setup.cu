@@ -160,6 +160,29 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
             amax = fmin(amax, fmax(a0, a1));
         }
     }
+    // Opaque sphere of radius r_obs at the origin (the photosphere): the
+    // line of sight ends at its first point on the sphere (the paper stops
+    // the integration there, Section 4).  Roots of |o + a u| = r: with p the
+    // point of closest approach to the origin, a = -(o.u) -+ sqrt(r^2 -
+    // |p|^2); |p|^2 is summed from p's components, which keeps the ~200-radii
+    // observer distance out of the difference.  An observer inside the
+    // sphere sees nothing.
+    if (hit && c.r_obs > 0.0) {
+        const double r2 = c.r_obs * c.r_obs;
+        const double ou = f.o[0] * u[0] + f.o[1] * u[1] + f.o[2] * u[2];
+        double oo = 0.0, pp = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            oo += f.o[a] * f.o[a];
+            const double pa = f.o[a] - ou * u[a];
+            pp += pa * pa;
+        }
+        if (oo <= r2) {
+            hit = false;
+        } else if (pp < r2) {
+            const double first = -ou - sqrt(r2 - pp);
+            if (first > 0.0) amax = fmin(amax, first);
+        }
+    }
     RayRec r;
     r.t0x = r.t0y = r.t0z = 0.0f;
     r.dtx = r.dty = r.dtz = 0.0f;

@@ -85,6 +85,7 @@ struct CubeDev {
     int32_t nx, ny, nz;
     double lo[3], d[3];
     double inv_d[3];  // 1 / d
+    double r_obs;     // opaque sphere at the origin (0: none)
 };
 
 struct Tiling {

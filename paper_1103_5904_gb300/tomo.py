@@ -40,7 +40,7 @@ class CubeGeom(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("reserved", C.c_int32), ("x0", C.c_double),
                 ("y0", C.c_double), ("z0", C.c_double), ("dx", C.c_double),
-                ("dy", C.c_double), ("dz", C.c_double)]
+                ("dy", C.c_double), ("dz", C.c_double), ("r_obs", C.c_double)]
 
 
 class ImageGeom(C.Structure):
@@ -71,8 +71,8 @@ class TilingResult(C.Structure):
                 ("adj_ms", C.c_float)]
 
 
-assert C.sizeof(CubeGeom) == 64 and C.sizeof(Pointing) == 96
-assert C.sizeof(Problem) == 120
+assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
+assert C.sizeof(Problem) == 128
 
 
 class TomoError(RuntimeError):
@@ -219,9 +219,12 @@ def default_context(device=None):
 # -------------------------------------------------------------- marshalling
 
 def cube_geom_struct(geom):
+    """``geom``: nx, ny, nz, x0, y0, z0, dx, dy, dz and optionally r_obs
+    (radius of the opaque sphere at the origin; 0 or absent: none)."""
     return CubeGeom(int(geom["nx"]), int(geom["ny"]), int(geom["nz"]), 0,
                     float(geom["x0"]), float(geom["y0"]), float(geom["z0"]),
-                    float(geom["dx"]), float(geom["dy"]), float(geom["dz"]))
+                    float(geom["dx"]), float(geom["dy"]), float(geom["dz"]),
+                    float(geom.get("r_obs", 0.0)))
 
 
 def pointing_array(pointing):

@@ -58,8 +58,9 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "tomo.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tomo_cube_geom),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tomo_cube_geom),
          offsetof(tomo_cube_geom, x0), offsetof(tomo_cube_geom, dz),
+         offsetof(tomo_cube_geom, r_obs),
          sizeof(tomo_image_geom), sizeof(tomo_pointing), sizeof(tomo_profile));
   return 0;
 }''')
@@ -68,7 +69,8 @@ int main(void) {
                            "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(tomo.CubeGeom), tomo.CubeGeom.x0.offset,
-            tomo.CubeGeom.dz.offset, C.sizeof(tomo.ImageGeom),
+            tomo.CubeGeom.dz.offset, tomo.CubeGeom.r_obs.offset,
+            C.sizeof(tomo.ImageGeom),
             C.sizeof(tomo.Pointing), C.sizeof(tomo.Profile)]
     assert got == want
 
