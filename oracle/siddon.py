@@ -132,12 +132,21 @@ def segments(geom, o, u):
     return idx[:n].copy(), ln[:n].copy(), a0.value, a1.value
 
 
+def _keep(map_mask):
+    """1 on the voxels that are unknowns, 0 on those a map mask excludes."""
+    return (np.asarray(map_mask) == 0).astype(np.float64)
+
+
 def project(geom, cube, pointing, nu, nv, mask=None, n_frames=1,
-            ray_ids=None):
+            ray_ids=None, map_mask=None):
     """FP64 ``y = P x``; returns ``[n_img][nv][nu]`` or, with ``ray_ids``, the
-    values of those rays."""
+    values of those rays.  ``map_mask`` ([nz][ny][nx], nonzero = voxel
+    excluded from the map, the counterpart of the pixel mask that Section 4
+    names for the map): the excluded voxels are read as 0, in every frame."""
     c = _cube(geom)
     cube = _f64(cube)
+    if map_mask is not None:
+        cube = _f64(cube * _keep(map_mask))
     ptg = _f64(pointing)
     n_img = ptg.shape[0]
     m, mp = _mask_ptr(mask)
@@ -151,9 +160,10 @@ def project(geom, cube, pointing, nu, nv, mask=None, n_frames=1,
 
 
 def backproject(geom, images, pointing, nu, nv, mask=None, n_frames=1,
-                ray_ids=None):
+                ray_ids=None, map_mask=None):
     """FP64 ``x = P^T y``; ``images`` is a full ``[n_img][nv][nu]`` stack
-    (with ``ray_ids``, only those pixels are used)."""
+    (with ``ray_ids``, only those pixels are used).  With ``map_mask`` the
+    excluded voxels receive 0 (the transpose of reading them as 0)."""
     c = _cube(geom)
     ptg = _f64(pointing)
     n_img = ptg.shape[0]
@@ -170,6 +180,8 @@ def backproject(geom, images, pointing, nu, nv, mask=None, n_frames=1,
                                _dp(out))
     if rc != 0:
         raise ValueError("invalid pointing or time stamp")
+    if map_mask is not None:
+        out = out * _keep(map_mask)
     return out
 
 

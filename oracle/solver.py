@@ -13,6 +13,12 @@ with A = M P (the masked projector: masked pixels are not projected, Section
 differences ``x[i+1] - x[i]`` along x, y and z, without wrap-around (N - 1
 differences per line), the same lambda on every axis (as in Table hypers).
 
+A map mask (nonzero = voxel excluded from the map) restricts the unknowns
+to the other voxels; reading: the excluded voxels are zero in the map that P
+and D see, so with K = diag(1 - mask) the criterion is
+||M (y - P K x)||^2 + lambda ||D K x||^2 over x = K x, whose normal
+equations are K (P^T M P + lambda D^T D) K x = K P^T M y.
+
 The solver is the textbook (Hestenes-Stiefel) conjugate-gradient method on
 the normal equations, started from x0 (zero unless given), run for a fixed
 number of iterations (the paper uses CG throughout, Sections 3.1 and 5.1; it
@@ -62,21 +68,28 @@ def prior_energy(x):
 class Problem:
     """One static reconstruction: cube geometry, pointing, mask, data, lambda."""
 
-    def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0):
+    def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0,
+                 map_mask=None):
         self.geom, self.pointing = geom, np.asarray(pointing, np.float64)
         self.nu, self.nv = int(nu), int(nv)
         self.mask = mask
         self.y = np.asarray(y, dtype=np.float64)
         self.lam = float(lam)
         self.shape = (geom["nz"], geom["ny"], geom["nx"])
+        self.keep = (None if map_mask is None else
+                     (np.asarray(map_mask) == 0).astype(np.float64))
+
+    def K(self, x):
+        """The map mask: excluded voxels set to 0."""
+        return x if self.keep is None else x * self.keep
 
     def P(self, x):
-        return siddon.project(self.geom, x, self.pointing, self.nu, self.nv,
-                              self.mask)
+        return siddon.project(self.geom, self.K(x), self.pointing, self.nu,
+                              self.nv, self.mask)
 
     def Pt(self, y):
-        return siddon.backproject(self.geom, y, self.pointing, self.nu,
-                                  self.nv, self.mask)
+        return self.K(siddon.backproject(self.geom, y, self.pointing, self.nu,
+                                         self.nv, self.mask))
 
     def masked(self, y):
         if self.mask is None:
@@ -88,13 +101,13 @@ class Problem:
         return self.Pt(self.masked(self.y))
 
     def normal(self, v):
-        """(P^T M P + lambda D^T D) v."""
-        return self.Pt(self.P(v)) + self.lam * DtD(v)
+        """K (P^T M P + lambda D^T D) K v (K = identity without map mask)."""
+        return self.Pt(self.P(v)) + self.lam * self.K(DtD(self.K(v)))
 
     def J(self, x):
-        """Eq. criterion: ||M (y - P x)||^2 + lambda ||D x||^2."""
+        """Eq. criterion: ||M (y - P K x)||^2 + lambda ||D K x||^2."""
         r = self.masked(self.y - self.P(x))
-        return float(np.sum(r * r)) + self.lam * prior_energy(x)
+        return float(np.sum(r * r)) + self.lam * prior_energy(self.K(x))
 
 
 def cg(problem, n_iter, x0=None, track_J=True):
@@ -105,7 +118,8 @@ def cg(problem, n_iter, x0=None, track_J=True):
     recursively updated residual).
     """
     b = problem.rhs()
-    x = np.zeros(problem.shape) if x0 is None else np.array(x0, np.float64)
+    x = (np.zeros(problem.shape) if x0 is None else
+         problem.K(np.array(x0, np.float64)))
     r = b - problem.normal(x) if x0 is not None else b.copy()
     p = r.copy()
     rr = float(np.sum(r * r))

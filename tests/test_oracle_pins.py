@@ -417,11 +417,9 @@ def _dense_problem():
     return solver.Problem(g, ptg, 8, 8, y, mask, lam=0.3)
 
 
-def test_cg_matches_direct_solve():
-    """CG on the normal equations reaches the direct solution of
-    (A^T A + lambda B^T B) x = A^T y (Eq. criterion) built from dense
-    brute-force rows and dense difference matrices."""
-    pb = _dense_problem()
+def _dense_AB(pb):
+    """Dense A = M P (brute-force rows, masked pixels zero) and the dense
+    forward-difference matrix B of the 5 x 4 x 4 problem."""
     g = pb.geom
     nvox = 80
     A = np.zeros((6 * 64, nvox))
@@ -441,7 +439,15 @@ def test_cg_matches_direct_solve():
                     row[((k + dk) * 4 + j + dj) * 5 + i + di] += 1
                     row[(k * 4 + j) * 5 + i] -= 1
                     rows.append(row)
-    B = np.array(rows)
+    return A, np.array(rows)
+
+
+def test_cg_matches_direct_solve():
+    """CG on the normal equations reaches the direct solution of
+    (A^T A + lambda B^T B) x = A^T y (Eq. criterion) built from dense
+    brute-force rows and dense difference matrices."""
+    pb = _dense_problem()
+    A, B = _dense_AB(pb)
     ym = np.where(pb.mask == 0, pb.y, 0.0).reshape(-1)
     x_direct = np.linalg.solve(A.T @ A + pb.lam * B.T @ B, A.T @ ym)
     x_cg, rep = solver.cg(pb, 400)
@@ -466,6 +472,78 @@ def test_cg_warm_start_and_J_identity():
                                      rel=1e-10)
     x_more, rep_more = solver.cg(pb, 30, x0=x5)
     assert rep_more["J"][-1] <= rep5["J"][-1]
+
+
+def _map_mask_problem(n_excluded, seed=4):
+    pb = _dense_problem()
+    rng = np.random.default_rng(seed)
+    mm = np.zeros(80, np.uint8)
+    mm[rng.choice(80, n_excluded, replace=False)] = 1 + rng.integers(0, 255,
+                                                                     n_excluded)
+    mm = mm.reshape(4, 4, 5)
+    return solver.Problem(pb.geom, pb.pointing, 8, 8, pb.y, pb.mask, pb.lam,
+                          map_mask=mm), mm
+
+
+def test_map_mask_solves_the_reduced_system():
+    """With a map mask the unknowns are the other voxels: the solution is the
+    direct solve of the least-squares problem whose dense matrices have the
+    excluded voxels' columns deleted (the excluded voxels stay 0)."""
+    pb, mm = _map_mask_problem(23)
+    A, B = _dense_AB(pb)
+    keep = mm.reshape(-1) == 0
+    Ak, Bk = A[:, keep], B[:, keep]
+    ym = np.where(pb.mask == 0, pb.y, 0.0).reshape(-1)
+    xk = np.linalg.solve(Ak.T @ Ak + pb.lam * Bk.T @ Bk, Ak.T @ ym)
+    x_cg, rep = solver.cg(pb, 400, x0=np.ones((4, 4, 5)))
+    x_cg = x_cg.reshape(-1)
+    assert np.all(x_cg[~keep] == 0.0)
+    np.testing.assert_allclose(x_cg[keep], xk, rtol=0,
+                               atol=1e-9 * np.abs(xk).max())
+    Jmin = float(np.sum((ym - Ak @ xk) ** 2) + pb.lam * np.sum((Bk @ xk) ** 2))
+    assert rep["J"][-1] == pytest.approx(Jmin, rel=1e-10)
+    # J identity of the device solver holds on the restricted system
+    x5, _ = solver.cg(pb, 5)
+    b = pb.rhs()
+    r = b - pb.normal(x5)
+    assert np.all(r.reshape(-1)[~keep] == 0.0)
+    yy = pb.masked(pb.y)
+    assert pb.J(x5) == pytest.approx(float(np.sum(yy * yy) - np.sum(x5 * (r + b))),
+                                     rel=1e-10)
+
+
+def test_map_mask_projection_special_cases():
+    """P with a map mask against brute-force rows times the kept voxels; the
+    adjoint identity in FP64; an all-excluded map projects, back-projects and
+    reconstructs to 0; an all-kept map changes nothing."""
+    g, ptg, mask, rng = _small_scene()
+    shape = (g["nz"], g["ny"], g["nx"])
+    x = rng.random(shape)
+    mm = (rng.random(shape) < 0.3).astype(np.uint8) * 7
+    got = siddon.project(g, x, ptg, 10, 6, mask, map_mask=mm)
+    keep = (mm == 0).reshape(-1)
+    for r in rng.choice(5 * 60, 40, replace=False):
+        n, iv, iu = r // 60, (r // 10) % 6, r % 10
+        o, u = siddon.ray(ptg[n], iu, iv)
+        want = 0.0 if mask[n, iv, iu] else float(
+            np.sum(checks.brute_force_ray(g, o, u) * keep * x.reshape(-1)) *
+            ptg[n, 10])
+        assert got[n, iv, iu] == pytest.approx(want, rel=1e-12, abs=1e-14)
+    y = rng.random((5, 6, 10))
+    Pty = siddon.backproject(g, y, ptg, 10, 6, mask, map_mask=mm)
+    assert np.all(Pty[mm != 0] == 0.0)
+    lhs = float(np.sum(np.where(mask == 0, y, 0) * got))
+    assert lhs == pytest.approx(float(np.sum(x * Pty)), rel=1e-12)
+    full = np.ones(shape, np.uint8)
+    assert not np.any(siddon.project(g, x, ptg, 10, 6, mask, map_mask=full))
+    assert not np.any(siddon.backproject(g, y, ptg, 10, 6, mask,
+                                         map_mask=full))
+    zero = np.zeros(shape, np.uint8)
+    assert np.array_equal(siddon.project(g, x, ptg, 10, 6, mask, map_mask=zero),
+                          siddon.project(g, x, ptg, 10, 6, mask))
+    pb, _ = _map_mask_problem(80)
+    x_all, rep = solver.cg(pb, 5, x0=np.ones((4, 4, 5)))
+    assert not np.any(x_all)
 
 
 def test_crossing_weights():
