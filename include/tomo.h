@@ -25,6 +25,12 @@
  *    a face is charged to the voxel above it.
  *  - Masks: uint8 [n_img][nv][nu], nonzero = excluded (Section 4: masked
  *    pixels are not projected).  P writes 0 there, P^T ignores them.
+ *  - Map masks: uint8 [nz][ny][nx], nonzero = voxel excluded from the map
+ *    (Section 4 names masks of the data and of the map; the paper gives no
+ *    formula).  Reading: an excluded voxel is not an unknown.  P reads it as
+ *    0 (P K x, K = diag(1 - map mask)), P^T leaves it 0 (K P^T y), and the
+ *    solver works on the system restricted to the other voxels.  With
+ *    T > 1 frames the one mask applies to every frame.  Always nullable.
  *  - Gains: each image is scaled by its record's gain (Eq. two_spacecraft,
  *    Eq. lin2space).
  *  - Time (Section 3.3.3, a parameterised temporal evolution): with T > 1
@@ -195,6 +201,9 @@ tomo_status tomo_profile_read(tomo_ctx *ctx, tomo_profile *out, int32_t reset);
  *   img:           image stack geometry
  *   pointing_host: n_img records (copied during the call)
  *   mask_dev:      nullable; nonzero pixels are written as 0
+ *   map_mask_dev:  nullable; excluded voxels are read as 0 (the call copies
+ *                  the masked cube into context workspace; cube_dev is not
+ *                  modified)
  *   images_dev:    [n_img][nv][nu] float32, overwritten
  * Ray records are computed in FP64 by a setup kernel and cached in the
  * context, keyed by (cube, img, pointing) contents. */
@@ -202,21 +211,25 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
                          int32_t n_frames, const void *cube_dev,
                          tomo_dtype dtype, const tomo_image_geom *img,
                          const tomo_pointing *pointing_host,
-                         const uint8_t *mask_dev, float *images_dev,
-                         void *stream);
+                         const uint8_t *mask_dev, const uint8_t *map_mask_dev,
+                         float *images_dev, void *stream);
 
 /* Backprojection x = P^T y: the exact transpose of tomo_project with the
  * same arguments (same segments, lengths, mask, gains and time weights).
- *   images_dev: [n_img][nv][nu] float32 input
- *   cube_dev:   [T][nz][ny][nx] float32 output; overwritten unless
- *               flags has TOMO_ACCUMULATE
+ *   images_dev:   [n_img][nv][nu] float32 input
+ *   map_mask_dev: nullable; excluded voxels receive 0 (with
+ *                 TOMO_ACCUMULATE they keep their value)
+ *   cube_dev:     [T][nz][ny][nx] float32 output; overwritten unless
+ *                 flags has TOMO_ACCUMULATE
  * Results are accumulated with float32 atomics, so the summation order and
  * the last bits vary from run to run. */
 tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
                              int32_t n_frames, const tomo_image_geom *img,
                              const tomo_pointing *pointing_host,
-                             const uint8_t *mask_dev, const float *images_dev,
-                             float *cube_dev, uint32_t flags, void *stream);
+                             const uint8_t *mask_dev,
+                             const uint8_t *map_mask_dev,
+                             const float *images_dev, float *cube_dev,
+                             uint32_t flags, void *stream);
 
 /* Regularised least squares (Eq. criterion with A = M P, B = D):
  *     x = argmin ||M (y - P x)||^2 + lambda ||D x||^2 ,
@@ -225,6 +238,11 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
  * (P^T M P + lambda D^T D) x = P^T M y, one static frame, FP32 vectors and
  * FP64 scalars (alpha, beta, residual norms, J).
  *   y_dev:       [n_img][nv][nu] float32 data
+ *   map_mask_dev: nullable; restricts the unknowns to the other voxels:
+ *                the criterion becomes ||M (y - P K x)||^2 +
+ *                lambda ||D K x||^2 and CG runs on K (P^T M P +
+ *                lambda D^T D) K x = K P^T M y; the excluded voxels of the
+ *                result (and of the initial guess, in place) are 0
  *   x_dev:       [nz][ny][nx] float32; initial guess if flags has
  *                TOMO_SOLVE_X0 (else start from 0); receives the result
  *   lambda:      >= 0
@@ -240,10 +258,11 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
 tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                        const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
-                       const uint8_t *mask_dev, const float *y_dev,
-                       float *x_dev, double lambda, int32_t max_iter,
-                       double tol, uint32_t flags, double *report_host,
-                       int32_t *iters_host, void *stream);
+                       const uint8_t *mask_dev, const uint8_t *map_mask_dev,
+                       const float *y_dev, float *x_dev, double lambda,
+                       int32_t max_iter, double tol, uint32_t flags,
+                       double *report_host, int32_t *iters_host,
+                       void *stream);
 
 /* q = lambda D^T D x (+ q if flags has TOMO_ACCUMULATE), the gradient of the
  * prior term lambda ||D x||^2 / 2 (Section 3.3.1); x, q: [nz][ny][nx] f32. */
@@ -281,6 +300,10 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
  *                             TOMO_SOLVE_X0)
  *   lambda                    solve: prior weight (>= 0)
  *   reserved                  must be 0
+ *   map_mask_dev              nullable; the map mask of the single-problem
+ *                             calls (project: excluded voxels read as 0;
+ *                             backproject: they receive 0; solve: the
+ *                             restricted system)
  */
 typedef struct {
     tomo_cube_geom cube;
@@ -291,6 +314,7 @@ typedef struct {
     float *images_dev;
     float *cube_dev;
     double lambda;
+    const uint8_t *map_mask_dev;
 } tomo_problem;
 
 /* A tile shape and its measured times (tomo_autotune). */
@@ -367,8 +391,9 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
  * (cudaGetSymbolAddress, with that device current) and remembers it; make
  * that first call before any stream capture.
  *
- * Arguments are those of tomo_project without the context: the current
- * device is used, the stream is a cudaStream_t passed as void* (NULL = the
+ * Arguments are those of tomo_project without the context and without the
+ * map mask (a masked copy of the cube would need cube-sized scratch; apply
+ * the mask to the cube before the call): the current device is used, the stream is a cudaStream_t passed as void* (NULL = the
  * legacy default stream), and the call is asynchronous on it.  The
  * pointing table is copied during the call.  No cudaMalloc, cudaFree or
  * other allocating routine is called. */

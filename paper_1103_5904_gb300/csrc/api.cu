@@ -461,7 +461,7 @@ void tomo_destroy(tomo_ctx *ctx)
                        &ctx->params, &ctx->rays, &ctx->b, &ctx->r, &ctx->p,
                        &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
                        &ctx->counter, &ctx->count64, &ctx->layout_used,
-                       &ctx->lay1, &ctx->lay2 };
+                       &ctx->lay1, &ctx->lay2, &ctx->mcube };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     free_plan(ctx);
@@ -555,8 +555,8 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
                          int32_t n_frames, const void *cube_dev,
                          tomo_dtype dtype, const tomo_image_geom *img,
                          const tomo_pointing *pointing_host,
-                         const uint8_t *mask_dev, float *images_dev,
-                         void *stream)
+                         const uint8_t *mask_dev, const uint8_t *map_mask_dev,
+                         float *images_dev, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
@@ -576,6 +576,16 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
         (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
         return st;
+    if (map_mask_dev) {
+        // P K x: the walks read a copy with the excluded voxels at 0
+        const int64_t nvox = (int64_t)cube->nx * cube->ny * cube->nz;
+        const size_t esz = dtype == TOMO_F32 ? 4 : 2;
+        if ((st = ensure(ctx, ctx->mcube, esz * nvox * n_frames))) return st;
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_map_keep_copy(cube_dev, ctx->mcube.p, dtype == TOMO_BF16,
+                                    map_mask_dev, nvox, n_frames, s));
+        cube_dev = ctx->mcube.p;
+    }
     return forward_one(ctx, cube_dev, dtype, n_frames, mask_dev, images_dev,
                        cube, img, tl, nullptr, s);
 }
@@ -583,8 +593,10 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
 tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
                              int32_t n_frames, const tomo_image_geom *img,
                              const tomo_pointing *pointing_host,
-                             const uint8_t *mask_dev, const float *images_dev,
-                             float *cube_dev, uint32_t flags, void *stream)
+                             const uint8_t *mask_dev,
+                             const uint8_t *map_mask_dev,
+                             const float *images_dev, float *cube_dev,
+                             uint32_t flags, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
@@ -609,8 +621,27 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
         (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
         return st;
-    return adjoint_one(ctx, images_dev, mask_dev, cube_dev, cube, n_frames,
-                       img, tl, nullptr, s);
+    if (map_mask_dev && (flags & TOMO_ACCUMULATE)) {
+        // cube += K P^T y: transpose into scratch, add the kept voxels
+        const size_t bytes = sizeof(float) * fstride * n_frames;
+        if ((st = ensure(ctx, ctx->mcube, bytes))) return st;
+        float *tmp = (float *)ctx->mcube.p;
+        CUDA_TRY(ctx, cudaMemsetAsync(tmp, 0, bytes, s));
+        if ((st = adjoint_one(ctx, images_dev, mask_dev, tmp, cube, n_frames,
+                              img, tl, nullptr, s)))
+            return st;
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_map_keep_add(cube_dev, tmp, map_mask_dev, fstride,
+                                   n_frames, s));
+        return TOMO_OK;
+    }
+    if ((st = adjoint_one(ctx, images_dev, mask_dev, cube_dev, cube, n_frames,
+                          img, tl, nullptr, s)))
+        return st;
+    if (map_mask_dev)  // cube = K P^T y
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_map_zero(cube_dev, map_mask_dev, fstride, n_frames, s));
+    return TOMO_OK;
 }
 
 tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
@@ -669,10 +700,10 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
 tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                        const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
-                       const uint8_t *mask_dev, const float *y_dev,
-                       float *x_dev, double lambda, int32_t max_iter,
-                       double tol, uint32_t flags, double *report_host,
-                       int32_t *iters_host, void *stream)
+                       const uint8_t *mask_dev, const uint8_t *map_mask_dev,
+                       const float *y_dev, float *x_dev, double lambda,
+                       int32_t max_iter, double tol, uint32_t flags,
+                       double *report_host, int32_t *iters_host, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
@@ -744,19 +775,25 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if (m > 0 &&
         (st = adjoint_one(ctx, y_dev, mask_dev, b, cube, 1, img, tl, nullptr, s)))
         return st;
+    // with a map mask, b, r and p are restricted by the init and update
+    // kernels, and x0 here, so every iterate has 0 on the excluded voxels
+    // and the forward walks of p need no masked copy
+    const uint8_t *mm = map_mask_dev;
     if (flags & TOMO_SOLVE_X0) {
         // r0 = b - (P^T M P + lambda D^T D) x0
+        if (mm)
+            LAUNCH(ctx, TOMO_K_VECTOR, s, launch_map_zero(x_dev, mm, n, 1, s));
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, q, lam, false, nullptr, s));
         if (m > 0 &&
             ((st = forward_one(ctx, x_dev, TOMO_F32, 1, mask_dev, t, cube, img,
                                tl, nullptr, s)) ||
              (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, nullptr, s))))
             return st;
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, n, tol * tol,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, mm, n, tol * tol,
                                      partials, counter, S, report, grid, s));
     } else {
         CUDA_TRY(ctx, cudaMemsetAsync(x_dev, 0, sizeof(float) * n, s));
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, nullptr, nullptr, r, p, p16, n,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, nullptr, nullptr, r, p, p16, mm, n,
                                      tol * tol, partials, counter, S, report,
                                      grid, s));
     }
@@ -773,7 +810,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
             (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, done, s)))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, n, partials, counter,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, mm, n, partials, counter,
                                        S, report, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_direction(r, p, p16, n, S, grid, s));
     }

@@ -381,12 +381,16 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
         } else if (op == V_ZERO) {
             for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
                 d.b[i] = 0.0f;
-                if (!warm) d.x[i] = 0.0f;
+                if (!warm || (d.mm != nullptr && d.mm[i] != 0)) d.x[i] = 0.0f;
             }
         } else if (op == V_INIT) {
+            // map mask: b, r, p are 0 on the excluded voxels, so every
+            // iterate stays in the restricted space
             for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
-                const float bi = d.b[i];
-                const float ri = warm ? bi - d.q[i] : bi;
+                const bool out = d.mm != nullptr && d.mm[i] != 0;
+                if (out) d.b[i] = 0.0f;
+                const float bi = out ? 0.0f : d.b[i];
+                const float ri = out ? 0.0f : (warm ? bi - d.q[i] : bi);
                 d.r[i] = ri;
                 d.p[i] = ri;
                 s0 += (double)ri * ri;
@@ -412,7 +416,9 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
                 const float alpha = (float)d.S[S_ALPHA];
                 for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
                     const float xi = fmaf(alpha, d.p[i], d.x[i]);
-                    const float ri = fmaf(-alpha, d.q[i], d.r[i]);
+                    const float ri = (d.mm != nullptr && d.mm[i] != 0)
+                                         ? 0.0f
+                                         : fmaf(-alpha, d.q[i], d.r[i]);
                     d.x[i] = xi;
                     d.r[i] = ri;
                     s0 += (double)ri * ri;

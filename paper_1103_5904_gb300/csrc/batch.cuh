@@ -54,6 +54,7 @@ struct VecDesc {
     float *x, *r, *p, *q, *b;
     const float *y;
     const uint8_t *mask;
+    const uint8_t *mm;  // map mask (nullable): restricts b, r, p, x0
     double *S;       // the problem's FP64 slots (S_*)
     double *report;  // (n_iter + 1) x 2: J, r.r
     int64_t n, m;    // voxels, pixels

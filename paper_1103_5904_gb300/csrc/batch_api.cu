@@ -44,6 +44,7 @@ struct BatchPlan {
     DevBuf rtpre_dev, rsched_dev;
     int64_t rn_chunks = 0;
     DevBuf flay;  // layout copies of the forward's source cubes (2 x voxels)
+    DevBuf mcube;  // map-masked cubes / transpose scratch (1 x voxels)
     int64_t pn_chunks = 0;
     bool lay_dirty = false;
     cudaEvent_t ready = nullptr;
@@ -71,7 +72,7 @@ void free_plan(tomo_ctx *ctx)
                        &p->call_counter, &p->call_jobs, &p->call_fjobs,
                        &p->vec, &p->timg, &p->S, &p->partials, &p->counters,
                        &p->walk_desc, &p->vec_desc, &p->prefixes,
-                       &p->solve_jobs, &p->solve_fjobs };
+                       &p->solve_jobs, &p->solve_fjobs, &p->mcube };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (p->exec) cudaGraphExecDestroy(p->exec);
@@ -388,27 +389,20 @@ int walk_grid(const tomo_ctx *ctx)
     return (ctx->num_sms > 0 ? ctx->num_sms : 152) * walk_batched_blocks_per_sm();
 }
 
-tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
-                         bool adjoint, uint32_t flags, cudaStream_t s)
+// The walks of one batched projection or transpose; cubes[i] is the cube
+// that problem i's walk reads (forward) or accumulates into (transpose).
+tomo_status batched_walk_core(tomo_ctx *ctx, int32_t n,
+                              const tomo_problem *probs, bool adjoint,
+                              float *const *cubes, cudaStream_t s)
 {
     tomo_status st;
-    for (int32_t i = 0; i < n; ++i)
-        if ((st = check_problem(ctx, &probs[i], i, true, true))) return st;
-    if ((st = prepare_batch(ctx, n, probs, s))) return st;
     BatchPlan *P = ctx->plan;
     std::vector<WalkDesc> d(n);
     for (int32_t i = 0; i < n; ++i)
         d[i] = adjoint ? walk_desc(P, probs[i], i, probs[i].images_dev,
-                                   probs[i].cube_dev, nullptr, false)
-                       : walk_desc(P, probs[i], i, probs[i].cube_dev,
+                                   cubes[i], nullptr, false)
+                       : walk_desc(P, probs[i], i, cubes[i],
                                    probs[i].images_dev, nullptr, true);
-    if (adjoint && !(flags & TOMO_ACCUMULATE))
-        for (int32_t i = 0; i < n; ++i)
-            CUDA_TRY(ctx, cudaMemsetAsync(probs[i].cube_dev, 0,
-                                          sizeof(float) * probs[i].cube.nx *
-                                              probs[i].cube.ny * probs[i].cube.nz,
-                                          s));
-    if (P->tile_prefix[n] == 0) return TOMO_OK;
     // two queue counters: the plane-tile walk and the per-ray walk of the
     // problems too dense for it
     if ((st = upload(ctx, P->call_desc, d.data(), sizeof(WalkDesc) * n, s)) ||
@@ -421,9 +415,7 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         if (P->lay_dirty)
             CUDA_TRY(ctx, cudaMemsetAsync(P->lay.p, 0,
                                           sizeof(float) * 2 * P->vox_off[n], s));
-        std::vector<float *> cubes(n);
-        for (int32_t i = 0; i < n; ++i) cubes[i] = probs[i].cube_dev;
-        const std::vector<LayoutJob> jobs = layout_jobs(P, n, probs, cubes.data(), nullptr);
+        const std::vector<LayoutJob> jobs = layout_jobs(P, n, probs, cubes, nullptr);
         if ((st = upload(ctx, P->call_jobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
             return st;
         P->lay_dirty = true;
@@ -448,10 +440,8 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         return TOMO_OK;
     }
     if (!adjoint && batch_plane_forward(ctx, n, probs)) {
-        std::vector<float *> cubes(n);
-        for (int32_t i = 0; i < n; ++i) cubes[i] = probs[i].cube_dev;
         const std::vector<LayoutJob> jobs =
-            layout_jobs(P, n, probs, cubes.data(), nullptr, true);
+            layout_jobs(P, n, probs, cubes, nullptr, true);
         if ((st = upload(ctx, P->call_fjobs, jobs.data(), sizeof(LayoutJob) * jobs.size(), s)))
             return st;
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
@@ -479,6 +469,61 @@ tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                                (const int2 *)P->sched_dev.p, P->n_chunks,
                                (unsigned long long *)P->call_counter.p,
                                walk_grid(ctx), s));
+    return TOMO_OK;
+}
+
+// Map masks (tomo_problem.map_mask_dev): the forward walks a copy of K x
+// (scratch), the transpose is followed by x = K x, or with ACCUMULATE runs
+// into zeroed scratch whose kept voxels are then added.
+tomo_status batched_walk(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
+                         bool adjoint, uint32_t flags, cudaStream_t s)
+{
+    tomo_status st;
+    for (int32_t i = 0; i < n; ++i)
+        if ((st = check_problem(ctx, &probs[i], i, true, true))) return st;
+    if ((st = prepare_batch(ctx, n, probs, s))) return st;
+    BatchPlan *P = ctx->plan;
+    const bool accumulate = (flags & TOMO_ACCUMULATE) != 0;
+    bool scratch = false;
+    for (int32_t i = 0; i < n; ++i)
+        scratch |= probs[i].map_mask_dev != nullptr && (!adjoint || accumulate);
+    if (scratch &&
+        (st = ensure(ctx, P->mcube, sizeof(float) * (P->vox_off[n] > 0 ? P->vox_off[n] : 1))))
+        return st;
+    std::vector<float *> cubes(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t nvox = P->vox_off[i + 1] - P->vox_off[i];
+        const uint8_t *mm = probs[i].map_mask_dev;
+        float *tmp = (float *)P->mcube.p + P->vox_off[i];
+        cubes[i] = probs[i].cube_dev;
+        if (!adjoint && mm) {
+            LAUNCH(ctx, TOMO_K_VECTOR, s,
+                   launch_map_keep_copy(probs[i].cube_dev, tmp, false, mm,
+                                        nvox, 1, s));
+            cubes[i] = tmp;
+        } else if (adjoint && mm && accumulate) {
+            CUDA_TRY(ctx, cudaMemsetAsync(tmp, 0, sizeof(float) * nvox, s));
+            cubes[i] = tmp;
+        } else if (adjoint && !accumulate) {
+            CUDA_TRY(ctx, cudaMemsetAsync(cubes[i], 0, sizeof(float) * nvox, s));
+        }
+    }
+    if (P->tile_prefix[n] == 0) return TOMO_OK;
+    if ((st = batched_walk_core(ctx, n, probs, adjoint, cubes.data(), s)))
+        return st;
+    if (adjoint)
+        for (int32_t i = 0; i < n; ++i) {
+            const uint8_t *mm = probs[i].map_mask_dev;
+            if (!mm) continue;
+            const int64_t nvox = P->vox_off[i + 1] - P->vox_off[i];
+            if (accumulate)
+                LAUNCH(ctx, TOMO_K_VECTOR, s,
+                       launch_map_keep_add(probs[i].cube_dev, cubes[i], mm,
+                                           nvox, 1, s));
+            else
+                LAUNCH(ctx, TOMO_K_VECTOR, s,
+                       launch_map_zero(probs[i].cube_dev, mm, nvox, 1, s));
+        }
     return TOMO_OK;
 }
 
@@ -655,8 +700,8 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
     // graph key: geometry plan + caller buffers + lambdas + run shape
     uint64_t h = P->geom_key;
     for (int32_t i = 0; i < n; ++i) {
-        const void *ptrs[3] = { probs[i].images_dev, probs[i].cube_dev,
-                                probs[i].mask_dev };
+        const void *ptrs[4] = { probs[i].images_dev, probs[i].cube_dev,
+                                probs[i].mask_dev, probs[i].map_mask_dev };
         h = fnv1a(h, ptrs, sizeof(ptrs));
         h = fnv1a(h, &probs[i].lambda, sizeof(double));
     }
@@ -723,6 +768,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             v.b = bi;
             v.y = p.images_dev;
             v.mask = p.mask_dev;
+            v.mm = p.map_mask_dev;
             v.S = Si;
             v.report = rep + (size_t)i * stride;
             v.n = voff[i + 1] - voff[i];

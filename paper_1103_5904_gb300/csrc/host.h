@@ -60,6 +60,8 @@ struct tomo_ctx {
     tomo::host::DevBuf lay1, lay2;
     // solver workspace
     tomo::host::DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
+    // map-masked cube copy (forward) / transpose scratch (accumulate)
+    tomo::host::DevBuf mcube;
     // tuned tile shapes per problem size, and the cached batch plan
     std::vector<tomo::host::Tuned> tuned;
     tomo::host::BatchPlan *plan = nullptr;

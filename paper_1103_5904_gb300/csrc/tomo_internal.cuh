@@ -202,25 +202,41 @@ cudaError_t launch_masked_sumsq(const float *y, const uint8_t *mask,
                                 unsigned int *counter, double *S,
                                 int grid, cudaStream_t s);
 // r = b - q (or r = b if q == NULL); p = r (+ bf16 copy); S[RR], S[RR0],
-// report row 0 from r.r and x.(r + b)
-cudaError_t launch_cg_init(const float *b, const float *q, const float *x,
-                           float *r, float *p, uint16_t *p16, int64_t n,
-                           double tol2, double *partials,
-                           unsigned int *counter, double *S, double *report,
-                           int grid, cudaStream_t s);
+// report row 0 from r.r and x.(r + b).  map_mask (nullable): b, r, p set
+// to 0 on the excluded voxels.
+cudaError_t launch_cg_init(float *b, const float *q, const float *x,
+                           float *r, float *p, uint16_t *p16,
+                           const uint8_t *map_mask, int64_t n, double tol2,
+                           double *partials, unsigned int *counter, double *S,
+                           double *report, int grid, cudaStream_t s);
 // S[S_PQ] = p.q, S[S_ALPHA] = rr / pq
 cudaError_t launch_cg_pq(const float *p, const float *q, int64_t n,
                          double *partials, unsigned int *counter, double *S,
                          int grid, cudaStream_t s);
-// x += alpha p; r -= alpha q; S[RR] <- r.r, beta, report row
+// x += alpha p; r -= alpha q (r = 0 on voxels excluded by map_mask);
+// S[RR] <- r.r, beta, report row
 cudaError_t launch_cg_update(float *x, float *r, const float *p,
-                             const float *q, const float *b, int64_t n,
+                             const float *q, const float *b,
+                             const uint8_t *map_mask, int64_t n,
                              double *partials, unsigned int *counter,
                              double *S, double *report, int grid,
                              cudaStream_t s);
 // p = r + beta p (+ bf16 copy)
 cudaError_t launch_cg_direction(const float *r, float *p, uint16_t *p16,
                                 int64_t n, const double *S, int grid,
+                                cudaStream_t s);
+
+// ---- mapmask.cu (map mask K = diag(1 - mask), same mask for every frame)
+// dst = K src over `frames` frames of n voxels (float32 or bf16 bits)
+cudaError_t launch_map_keep_copy(const void *src, void *dst, bool bf16,
+                                 const uint8_t *mm, int64_t n, int32_t frames,
+                                 cudaStream_t s);
+// x = K x
+cudaError_t launch_map_zero(float *x, const uint8_t *mm, int64_t n,
+                            int32_t frames, cudaStream_t s);
+// dst += K src
+cudaError_t launch_map_keep_add(float *dst, const float *src,
+                                const uint8_t *mm, int64_t n, int32_t frames,
                                 cudaStream_t s);
 
 }  // namespace tomo

@@ -62,7 +62,7 @@ class Problem(C.Structure):
     _fields_ = [("cube", CubeGeom), ("img", ImageGeom), ("reserved", C.c_int32),
                 ("pointing_host", C.POINTER(Pointing)), ("mask_dev", C.c_void_p),
                 ("images_dev", C.c_void_p), ("cube_dev", C.c_void_p),
-                ("lam", C.c_double)]
+                ("lam", C.c_double), ("map_mask_dev", C.c_void_p)]
 
 
 class TilingResult(C.Structure):
@@ -72,7 +72,7 @@ class TilingResult(C.Structure):
 
 
 assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
-assert C.sizeof(Problem) == 128
+assert C.sizeof(Problem) == 136
 
 
 class TomoError(RuntimeError):
@@ -97,12 +97,13 @@ _SIGNATURES = {
     "tomo_profile_read": (C.c_int, [_VP, C.POINTER(Profile), C.c_int32]),
     "tomo_project": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32, _VP,
                                C.c_int, C.POINTER(ImageGeom),
-                               C.POINTER(Pointing), _VP, _VP, _VP]),
+                               C.POINTER(Pointing), _VP, _VP, _VP, _VP]),
     "tomo_backproject": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32,
                                    C.POINTER(ImageGeom), C.POINTER(Pointing),
-                                   _VP, _VP, _VP, C.c_uint32, _VP]),
+                                   _VP, _VP, _VP, _VP, C.c_uint32, _VP]),
     "tomo_solve": (C.c_int, [_VP, C.POINTER(CubeGeom), C.POINTER(ImageGeom),
-                             C.POINTER(Pointing), _VP, _VP, _VP, C.c_double,
+                             C.POINTER(Pointing), _VP, _VP, _VP, _VP,
+                             C.c_double,
                              C.c_int32, C.c_double, C.c_uint32,
                              C.POINTER(C.c_double), C.POINTER(C.c_int32),
                              _VP]),
@@ -257,6 +258,16 @@ def _check_mask(mask, n_img, nu, nv):
                          % (n_img * nu * nv, mask.numel()))
 
 
+def _check_map_mask(map_mask, geom):
+    """Map mask: uint8 ``[nz][ny][nx]`` on the device, nonzero = voxel
+    excluded from the map (one mask for every frame)."""
+    _dev(map_mask, torch.uint8, "map_mask")
+    nvox = int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"])
+    if map_mask is not None and map_mask.numel() != nvox:
+        raise ValueError("map_mask must have nx * ny * nz = %d elements (got %d)"
+                         % (nvox, map_mask.numel()))
+
+
 def _stream_ptr(stream, device):
     s = stream if stream is not None else torch.cuda.current_stream(device)
     return _VP(s.cuda_stream)
@@ -273,9 +284,10 @@ def _ctx(ctx):
 # ------------------------------------------------------------- entry points
 
 def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
-                 out=None, ctx=None, stream=None):
+                 out=None, ctx=None, stream=None, map_mask=None):
     """``y = P x``: images ``[n_img][nv][nu]`` float32 from a float32 or
-    bfloat16 cube ``[T][nz][ny][nx]``."""
+    bfloat16 cube ``[T][nz][ny][nx]``; with ``map_mask`` the excluded voxels
+    are read as 0."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
     n_img = ptg.shape[0]
@@ -297,18 +309,19 @@ def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
     if out.numel() != n_img * nu * nv:
         raise ValueError("out must have n_img * nv * nu elements")
     _check_mask(mask, n_img, nu, nv)
+    _check_map_mask(map_mask, geom)
     cg, ig = cube_geom_struct(geom), ImageGeom(n_img, int(nu), int(nv))
     ctx.check(load_library().tomo_project(
         ctx.handle, C.byref(cg), int(n_frames), _ptr(cube), dtype,
-        C.byref(ig), _ptg_ptr(ptg), _ptr(mask), _ptr(out),
+        C.byref(ig), _ptg_ptr(ptg), _ptr(mask), _ptr(map_mask), _ptr(out),
         _stream_ptr(stream, cube.device)))
     return out
 
 
 def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
-                     accumulate=False, ctx=None, stream=None):
+                     accumulate=False, ctx=None, stream=None, map_mask=None):
     """``x = P^T y``: float32 cube ``[T][nz][ny][nx]`` from float32 images
-    ``[n_img][nv][nu]``."""
+    ``[n_img][nv][nu]``; with ``map_mask`` the excluded voxels receive 0."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
     _dev(images, torch.float32, "images")
@@ -325,10 +338,11 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
     if out.numel() != int(np.prod(shape)):
         raise ValueError("out has the wrong size")
     _check_mask(mask, n_img, nu, nv)
+    _check_map_mask(map_mask, geom)
     cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
     ctx.check(load_library().tomo_backproject(
         ctx.handle, C.byref(cg), int(n_frames), C.byref(ig), _ptg_ptr(ptg),
-        _ptr(mask), _ptr(images), _ptr(out),
+        _ptr(mask), _ptr(map_mask), _ptr(images), _ptr(out),
         TOMO_ACCUMULATE if accumulate else 0,
         _stream_ptr(stream, images.device)))
     return out
@@ -336,9 +350,10 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
 
 def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
                x0=None, bf16=False, out=None, report=True, ctx=None,
-               stream=None):
-    """CG on ``(P^T M P + lam D^T D) x = P^T M y``.  Returns ``(x, info)``
-    with ``info = {"J": ..., "rr": ..., "iters": ...}`` when ``report``."""
+               stream=None, map_mask=None):
+    """CG on ``(P^T M P + lam D^T D) x = P^T M y`` (restricted to the voxels
+    that ``map_mask`` keeps).  Returns ``(x, info)`` with
+    ``info = {"J": ..., "rr": ..., "iters": ...}`` when ``report``."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
     _dev(y, torch.float32, "y")
@@ -358,12 +373,13 @@ def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
     if bf16:
         flags |= TOMO_SOLVE_BF16
     _check_mask(mask, n_img, nu, nv)
+    _check_map_mask(map_mask, geom)
     cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
     rep = np.full(2 * (int(max_iter) + 1), np.nan) if report else None
     iters = C.c_int32(0)
     ctx.check(load_library().tomo_solve(
         ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
-        _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
+        _ptr(map_mask), _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
         rep.ctypes.data_as(C.POINTER(C.c_double)) if report else None,
         C.byref(iters) if report else None, _stream_ptr(stream, y.device)))
     info = None
@@ -412,7 +428,7 @@ def tomo_count_segments(geom, pointing, nu, nv, mask=None, ctx=None,
 
 def _problems(problems, need_cube=True, need_images=True):
     """ctypes array of tomo_problem from dicts with keys geom, pointing, nu,
-    nv, cube, images, mask (optional), lam (optional).  Returns the array and
+    nv, cube, images, mask (optional), map_mask (optional), lam (optional).  Returns the array and
     the pointing arrays it points into (keep them alive)."""
     arr = (Problem * len(problems))()
     keep = []
@@ -425,6 +441,8 @@ def _problems(problems, need_cube=True, need_images=True):
         _dev(cube, torch.float32, "cube")
         _dev(images, torch.float32, "images")
         _check_mask(mask, n_img, nu, nv)
+        map_mask = p.get("map_mask")
+        _check_map_mask(map_mask, p["geom"])
         nvox = int(p["geom"]["nx"]) * int(p["geom"]["ny"]) * int(p["geom"]["nz"])
         if need_cube and (cube is None or cube.numel() != nvox):
             raise ValueError("problem %d: cube must have nx*ny*nz elements" % i)
@@ -439,6 +457,7 @@ def _problems(problems, need_cube=True, need_images=True):
         arr[i].images_dev = None if images is None else images.data_ptr()
         arr[i].cube_dev = None if cube is None else cube.data_ptr()
         arr[i].lam = float(p.get("lam", 0.0))
+        arr[i].map_mask_dev = None if map_mask is None else map_mask.data_ptr()
     return arr, keep
 
 

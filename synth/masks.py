@@ -1,4 +1,4 @@
-"""Pixel masks of a coronagraph-like instrument.
+"""Pixel masks of a coronagraph-like instrument, and map masks.
 
 A coronagraph hides the solar disk behind an occulter and sees out to a field
 edge; both are disks in the image plane, centred on the direction of Sun
@@ -14,6 +14,8 @@ with ``theta_u = (i_u - crpix_u) cdelt_u + crval_u``.  Masks are uint8
 """
 
 import numpy as np
+
+from .geometry import voxel_centres
 
 
 def occulter_mask(pointing, nu, nv, r_occ=None, r_edge=None):
@@ -37,3 +39,20 @@ def occulter_mask(pointing, nu, nv, r_occ=None, r_edge=None):
             m |= rho > r_edge
         mask[k] = m
     return mask
+
+
+def shell_map_mask(geom, r_in=None, r_out=None):
+    """Map mask of a spherical shell: voxels whose centre lies below ``r_in``
+    (inside the photosphere) or above ``r_out`` (beyond the field of view)
+    are excluded.  uint8 ``[nz][ny][nx]``; nonzero means excluded."""
+    x = voxel_centres(geom, "x")
+    y = voxel_centres(geom, "y")
+    z = voxel_centres(geom, "z")
+    r = np.sqrt(z[:, None, None] ** 2 + y[None, :, None] ** 2 +
+                x[None, None, :] ** 2)
+    m = np.zeros(r.shape, dtype=bool)
+    if r_in is not None:
+        m |= r < r_in
+    if r_out is not None:
+        m |= r > r_out
+    return m.astype(np.uint8)

@@ -42,8 +42,10 @@ def test_status_strings_and_null_context(lib):
     assert lib.tomo_status_string(-6) == b"numerical breakdown"
     # NULL context: argument error before any CUDA call
     assert lib.tomo_project(None, None, 1, None, 0, None, None, None, None,
-                            None) == -1
-    assert lib.tomo_solve(None, None, None, None, None, None, None,
+                            None, None) == -1
+    assert lib.tomo_backproject(None, None, 1, None, None, None, None, None,
+                                None, 0, None) == -1
+    assert lib.tomo_solve(None, None, None, None, None, None, None, None,
                           C.c_double(0), 0, C.c_double(0), 0, None, None,
                           None) == -1
     h = C.c_void_p()
@@ -58,10 +60,12 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "tomo.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(tomo_cube_geom),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tomo_cube_geom),
          offsetof(tomo_cube_geom, x0), offsetof(tomo_cube_geom, dz),
          offsetof(tomo_cube_geom, r_obs),
-         sizeof(tomo_image_geom), sizeof(tomo_pointing), sizeof(tomo_profile));
+         sizeof(tomo_image_geom), sizeof(tomo_pointing), sizeof(tomo_profile),
+         sizeof(tomo_problem), offsetof(tomo_problem, lambda),
+         offsetof(tomo_problem, map_mask_dev));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -71,7 +75,9 @@ int main(void) {
     want = [C.sizeof(tomo.CubeGeom), tomo.CubeGeom.x0.offset,
             tomo.CubeGeom.dz.offset, tomo.CubeGeom.r_obs.offset,
             C.sizeof(tomo.ImageGeom),
-            C.sizeof(tomo.Pointing), C.sizeof(tomo.Profile)]
+            C.sizeof(tomo.Pointing), C.sizeof(tomo.Profile),
+            C.sizeof(tomo.Problem), tomo.Problem.lam.offset,
+            tomo.Problem.map_mask_dev.offset]
     assert got == want
 
 
