@@ -53,7 +53,7 @@ def test_bad_geometry_and_pointing(T):
     assert lib.tomo_project(ctx.handle, C.byref(cg), 1,
                             C.c_void_p(cube.data_ptr()), 0, C.byref(ig),
                             T.tomo._ptg_ptr(np.ascontiguousarray(ptg)), None,
-                            C.c_void_p(out.data_ptr()), None) == ARG
+                            None, C.c_void_p(out.data_ptr()), None) == ARG
     bad = dict(g, dy=-0.1)
     assert _status(T, T.tomo_project, cube, bad, ptg, 16, 16) == ARG
     p = ptg.copy()
@@ -85,13 +85,13 @@ def test_bad_pointers_flags_and_options(T):
     pp = T.tomo._ptg_ptr(np.ascontiguousarray(ptg))
     st = lib.tomo_project(ctx.handle, C.byref(cg), 1,
                           C.c_void_p(cube.data_ptr() + 1), 0, C.byref(ig), pp,
-                          None, C.c_void_p(out.data_ptr()), None)
+                          None, None, C.c_void_p(out.data_ptr()), None)
     assert st == ARG and b"misaligned" in lib.tomo_last_error(ctx.handle)
     st = lib.tomo_project(ctx.handle, C.byref(cg), 1, None, 0, C.byref(ig),
-                          pp, None, C.c_void_p(out.data_ptr()), None)
+                          pp, None, None, C.c_void_p(out.data_ptr()), None)
     assert st == ARG
     st = lib.tomo_backproject(ctx.handle, C.byref(cg), 1, C.byref(ig), pp,
-                              None, C.c_void_p(out.data_ptr()),
+                              None, None, C.c_void_p(out.data_ptr()),
                               C.c_void_p(cube.data_ptr()), 0x80, None)
     assert st == ARG
     assert lib.tomo_set_option(ctx.handle, 99, 1) == ARG
@@ -119,3 +119,20 @@ def test_invalid_device(T):
     lib = T.load_library()
     h = C.c_void_p()
     assert lib.tomo_create(C.byref(h), 1 << 20) == ARG
+
+
+def test_map_mask_arguments(T):
+    """A map mask must be a uint8 CUDA tensor of nx * ny * nz elements."""
+    g, ptg = _scene()
+    cube = torch.ones((16, 16, 16), device="cuda")
+    y = torch.ones((2, 16, 16), device="cuda")
+    with pytest.raises(ValueError):
+        T.tomo_project(cube, g, ptg, 16, 16,
+                       map_mask=torch.zeros(100, dtype=torch.uint8,
+                                            device="cuda"))
+    with pytest.raises(TypeError):
+        T.tomo_backproject(y, g, ptg, map_mask=torch.zeros(
+            (16, 16, 16), dtype=torch.float32, device="cuda"))
+    with pytest.raises(TypeError):
+        T.tomo_solve(y, g, ptg, map_mask=torch.zeros((16, 16, 16),
+                                                     dtype=torch.uint8))
