@@ -571,6 +571,8 @@ SWEEP = [
     ("paper256", 0, False),
     ("cg256", 20, True),
 ]
+# configs also measured with the photosphere and a map mask inside it
+SOLAR_SETTING = ("paper128", "cg256")
 
 
 def run_sweep(args, local_rank):
@@ -678,6 +680,28 @@ def run_sweep(args, local_rank):
                     line["cg_bf16_s_to_f32_criterion"] = b_ms / 1e3
                     line["cg_f32_s"] = cg_ms / 1e3
             del x
+        if name in SOLAR_SETTING:
+            # the solar-tomography setting: opaque photosphere (lines of
+            # sight end at r = 1) and a map mask that excludes the voxels
+            # inside it; segments, P and P^T times, CG seconds per iteration
+            go = dict(g, r_obs=1.0)
+            mm = torch.from_numpy(synth.shell_map_mask(go, 1.0)).to(dev)
+            segs_o = T.tomo_count_segments(go, ptg, nu, nv, mask=mask, ctx=ctx)
+            yo = T.tomo_project(X, go, ptg, nu, nv, mask=mask, ctx=ctx)
+            line["solar_segments"] = int(segs_o)
+            line["solar_P_ms"] = med_ms(lambda: T.tomo_project(
+                X, go, ptg, nu, nv, mask=mask, map_mask=mm, out=yo, ctx=ctx),
+                reps)
+            line["solar_PT_ms"] = med_ms(lambda: T.tomo_backproject(
+                yo, go, ptg, mask=mask, map_mask=mm, out=out, ctx=ctx), reps)
+            if cg_iters:
+                x = torch.empty_like(X)
+                cg_o = med_ms(lambda: T.tomo_solve(
+                    yo, go, ptg, mask=mask, lam=c["lam"], max_iter=cg_iters,
+                    out=x, report=False, map_mask=mm, ctx=ctx), 3)
+                line["solar_cg_s_per_iter"] = cg_o / 1e3 / cg_iters
+                del x
+            del yo, mm
         # the oracle on one core and on all host cores (seeded ray sample)
         c_host = dict(c)
         nthreads = siddon.get_threads()
