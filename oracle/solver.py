@@ -13,6 +13,13 @@ with A = M P (the masked projector: masked pixels are not projected, Section
 differences ``x[i+1] - x[i]`` along x, y and z, without wrap-around (N - 1
 differences per line), the same lambda on every axis (as in Table hypers).
 
+Height-weighted prior (Eq. srt_inversion, Section 3.3.1): B = D R with R a
+diagonal operator, "the height of the voxels" on its diagonal, so that the
+smoothing grows with altitude.  The oracle takes the diagonal as given
+(``prior_weight``, one value per voxel; which height, e.g. the radius or
+the altitude above the photosphere, is the caller's choice); the normal
+operator's prior term is lambda R D^T D R.
+
 A map mask (nonzero = voxel excluded from the map) restricts the unknowns
 to the other voxels; reading: the excluded voxels are zero in the map that P
 and D see, so with K = diag(1 - mask) the criterion is
@@ -69,7 +76,7 @@ class Problem:
     """One static reconstruction: cube geometry, pointing, mask, data, lambda."""
 
     def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0,
-                 map_mask=None):
+                 map_mask=None, prior_weight=None):
         self.geom, self.pointing = geom, np.asarray(pointing, np.float64)
         self.nu, self.nv = int(nu), int(nv)
         self.mask = mask
@@ -78,10 +85,16 @@ class Problem:
         self.shape = (geom["nz"], geom["ny"], geom["nx"])
         self.keep = (None if map_mask is None else
                      (np.asarray(map_mask) == 0).astype(np.float64))
+        self.w = (None if prior_weight is None else
+                  np.asarray(prior_weight, dtype=np.float64).reshape(self.shape))
 
     def K(self, x):
         """The map mask: excluded voxels set to 0."""
         return x if self.keep is None else x * self.keep
+
+    def R(self, x):
+        """The prior's diagonal weight (identity without one)."""
+        return x if self.w is None else x * self.w
 
     def P(self, x):
         return siddon.project(self.geom, self.K(x), self.pointing, self.nu,
@@ -101,13 +114,16 @@ class Problem:
         return self.Pt(self.masked(self.y))
 
     def normal(self, v):
-        """K (P^T M P + lambda D^T D) K v (K = identity without map mask)."""
-        return self.Pt(self.P(v)) + self.lam * self.K(DtD(self.K(v)))
+        """K (P^T M P + lambda R D^T D R) K v (K, R = identity without map
+        mask or prior weight)."""
+        return self.Pt(self.P(v)) + self.lam * self.K(
+            self.R(DtD(self.R(self.K(v)))))
 
     def J(self, x):
-        """Eq. criterion: ||M (y - P K x)||^2 + lambda ||D K x||^2."""
+        """Eq. criterion: ||M (y - P K x)||^2 + lambda ||D R K x||^2."""
         r = self.masked(self.y - self.P(x))
-        return float(np.sum(r * r)) + self.lam * prior_energy(self.K(x))
+        return float(np.sum(r * r)) + self.lam * prior_energy(
+            self.R(self.K(x)))
 
 
 def cg(problem, n_iter, x0=None, track_J=True):

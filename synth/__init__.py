@@ -16,14 +16,14 @@ from .geometry import (POINTING_COLUMNS, cube_geom, pointing_table,
                        cdelt_for_fov, voxel_centres)
 from .corona import (radial_exp, radial_power, add_structures, random_axes,
                      uniform_noise, corona_cube, corona_frames)
-from .masks import occulter_mask, shell_map_mask
+from .masks import occulter_mask, shell_map_mask, height_weights
 from .configs import (CONFIGS, make_config, noise_draw, add_noise,
                       problem_seeds_batched)
 
 __all__ = [
     "POINTING_COLUMNS", "cube_geom", "pointing_table", "cdelt_for_fov",
     "voxel_centres", "radial_exp", "radial_power", "add_structures",
-    "random_axes", "uniform_noise", "corona_cube", "corona_frames", "occulter_mask", "shell_map_mask",
+    "random_axes", "uniform_noise", "corona_cube", "corona_frames", "occulter_mask", "shell_map_mask", "height_weights",
     "CONFIGS", "make_config", "noise_draw", "add_noise",
     "problem_seeds_batched",
 ]

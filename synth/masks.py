@@ -1,4 +1,5 @@
-"""Pixel masks of a coronagraph-like instrument, and map masks.
+"""Pixel masks of a coronagraph-like instrument, map masks and the radial
+weights of a height-weighted prior.
 
 A coronagraph hides the solar disk behind an occulter and sees out to a field
 edge; both are disks in the image plane, centred on the direction of Sun
@@ -56,3 +57,15 @@ def shell_map_mask(geom, r_in=None, r_out=None):
     if r_out is not None:
         m |= r > r_out
     return m.astype(np.uint8)
+
+
+def height_weights(geom, r_ref=0.0, floor=0.0):
+    """Diagonal of a height-weighted prior: the distance of each voxel centre
+    from Sun centre minus ``r_ref`` (``r_ref = 1``: altitude above the
+    photosphere), not below ``floor``.  float64 ``[nz][ny][nx]``."""
+    x = voxel_centres(geom, "x")
+    y = voxel_centres(geom, "y")
+    z = voxel_centres(geom, "z")
+    r = np.sqrt(z[:, None, None] ** 2 + y[None, :, None] ** 2 +
+                x[None, None, :] ** 2)
+    return np.maximum(r - r_ref, floor)

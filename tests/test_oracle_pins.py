@@ -546,6 +546,48 @@ def test_map_mask_projection_special_cases():
     assert not np.any(x_all)
 
 
+def test_height_weighted_prior_solves_the_dense_system():
+    """Eq. srt_inversion: with B = D R (R diagonal) CG reaches the direct
+    solve built from the dense difference matrix times diag(R); with a map
+    mask too, the excluded columns are deleted from A and from D R; a
+    constant weight c equals the unweighted prior with lambda c^2."""
+    pb0 = _dense_problem()
+    A, B = _dense_AB(pb0)
+    rng = np.random.default_rng(12)
+    w = rng.uniform(0.5, 3.0, 80)
+    ym = np.where(pb0.mask == 0, pb0.y, 0.0).reshape(-1)
+    pb = solver.Problem(pb0.geom, pb0.pointing, 8, 8, pb0.y, pb0.mask,
+                        pb0.lam, prior_weight=w.reshape(4, 4, 5))
+    BR = B * w[None, :]
+    x_direct = np.linalg.solve(A.T @ A + pb.lam * BR.T @ BR, A.T @ ym)
+    x_cg, rep = solver.cg(pb, 400)
+    np.testing.assert_allclose(x_cg.reshape(-1), x_direct, rtol=0,
+                               atol=1e-9 * np.abs(x_direct).max())
+    Jmin = float(np.sum((ym - A @ x_direct) ** 2) +
+                 pb.lam * np.sum((BR @ x_direct) ** 2))
+    assert rep["J"][-1] == pytest.approx(Jmin, rel=1e-10)
+    # with a map mask
+    _, mm = _map_mask_problem(17)
+    keep = mm.reshape(-1) == 0
+    pbm = solver.Problem(pb0.geom, pb0.pointing, 8, 8, pb0.y, pb0.mask,
+                         pb0.lam, map_mask=mm, prior_weight=w)
+    Ak, Bk = A[:, keep], BR[:, keep]
+    xk = np.linalg.solve(Ak.T @ Ak + pb.lam * Bk.T @ Bk, Ak.T @ ym)
+    x_m, _ = solver.cg(pbm, 400)
+    x_m = x_m.reshape(-1)
+    assert np.all(x_m[~keep] == 0.0)
+    np.testing.assert_allclose(x_m[keep], xk, rtol=0,
+                               atol=1e-9 * np.abs(xk).max())
+    # constant weight
+    pc = solver.Problem(pb0.geom, pb0.pointing, 8, 8, pb0.y, pb0.mask,
+                        pb0.lam, prior_weight=np.full(80, 1.7))
+    pl = solver.Problem(pb0.geom, pb0.pointing, 8, 8, pb0.y, pb0.mask,
+                        pb0.lam * 1.7 ** 2)
+    v = rng.random((4, 4, 5))
+    np.testing.assert_allclose(pc.normal(v), pl.normal(v), rtol=1e-13)
+    assert pc.J(v) == pytest.approx(pl.J(v), rel=1e-13)
+
+
 def test_crossing_weights():
     """C_j with unit images counts the rays crossing each voxel: it matches
     the brute-force clip (positive lengths), and its total is the number of
