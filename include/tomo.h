@@ -231,18 +231,23 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
                              const float *images_dev, float *cube_dev,
                              uint32_t flags, void *stream);
 
-/* Regularised least squares (Eq. criterion with A = M P, B = D):
- *     x = argmin ||M (y - P x)||^2 + lambda ||D x||^2 ,
+/* Regularised least squares (Eq. criterion with A = M P, B = D, or
+ * B = D R for the height-weighted prior of Eq. srt_inversion):
+ *     x = argmin ||M (y - P x)||^2 + lambda ||D R x||^2 ,
  * D = forward differences along x, y, z without wrap (Section 3.3.1, "a
- * finite-difference operator along each axis"), by conjugate gradients on
- * (P^T M P + lambda D^T D) x = P^T M y, one static frame, FP32 vectors and
- * FP64 scalars (alpha, beta, residual norms, J).
+ * finite-difference operator along each axis"), R = diag(prior weight) or
+ * the identity, by conjugate gradients on
+ * (P^T M P + lambda R D^T D R) x = P^T M y, one static frame, FP32 vectors
+ * and FP64 scalars (alpha, beta, residual norms, J).
  *   y_dev:       [n_img][nv][nu] float32 data
  *   map_mask_dev: nullable; restricts the unknowns to the other voxels:
  *                the criterion becomes ||M (y - P K x)||^2 +
  *                lambda ||D K x||^2 and CG runs on K (P^T M P +
  *                lambda D^T D) K x = K P^T M y; the excluded voxels of the
  *                result (and of the initial guess, in place) are 0
+ *   prior_weight_dev: nullable; [nz][ny][nx] float32, the diagonal of R
+ *                (Eq. srt_inversion puts the voxels' height there; the
+ *                caller chooses which height), 4-byte aligned
  *   x_dev:       [nz][ny][nx] float32; initial guess if flags has
  *                TOMO_SOLVE_X0 (else start from 0); receives the result
  *   lambda:      >= 0
@@ -259,16 +264,20 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                        const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
                        const uint8_t *mask_dev, const uint8_t *map_mask_dev,
-                       const float *y_dev, float *x_dev, double lambda,
-                       int32_t max_iter, double tol, uint32_t flags,
-                       double *report_host, int32_t *iters_host,
-                       void *stream);
+                       const float *prior_weight_dev, const float *y_dev,
+                       float *x_dev, double lambda, int32_t max_iter,
+                       double tol, uint32_t flags, double *report_host,
+                       int32_t *iters_host, void *stream);
 
 /* q = lambda D^T D x (+ q if flags has TOMO_ACCUMULATE), the gradient of the
- * prior term lambda ||D x||^2 / 2 (Section 3.3.1); x, q: [nz][ny][nx] f32. */
+ * prior term lambda ||D x||^2 / 2 (Section 3.3.1); with prior_weight_dev
+ * (nullable, the diagonal of R) q = lambda R D^T D R x, the gradient of
+ * lambda ||D R x||^2 / 2 (Eq. srt_inversion).  x, q, weight: [nz][ny][nx]
+ * f32. */
 tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
-                             const float *x_dev, float *q_dev, double lambda,
-                             uint32_t flags, void *stream);
+                             const float *x_dev,
+                             const float *prior_weight_dev, float *q_dev,
+                             double lambda, uint32_t flags, void *stream);
 
 /* Number of positive-length voxel intersections (Siddon segments) of the
  * unmasked rays, counted on the device with the projector's own walk. */
@@ -304,6 +313,8 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
  *                             calls (project: excluded voxels read as 0;
  *                             backproject: they receive 0; solve: the
  *                             restricted system)
+ *   prior_weight_dev          nullable; solve: the diagonal of R of the
+ *                             height-weighted prior, as for tomo_solve
  */
 typedef struct {
     tomo_cube_geom cube;
@@ -315,6 +326,7 @@ typedef struct {
     float *cube_dev;
     double lambda;
     const uint8_t *map_mask_dev;
+    const float *prior_weight_dev;
 } tomo_problem;
 
 /* A tile shape and its measured times (tomo_autotune). */

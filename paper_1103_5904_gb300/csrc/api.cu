@@ -645,8 +645,9 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
 }
 
 tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
-                             const float *x_dev, float *q_dev, double lambda,
-                             uint32_t flags, void *stream)
+                             const float *x_dev,
+                             const float *prior_weight_dev, float *q_dev,
+                             double lambda, uint32_t flags, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
@@ -656,13 +657,16 @@ tomo_status tomo_prior_apply(tomo_ctx *ctx, const tomo_cube_geom *cube,
         return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
     if (!x_dev || !q_dev || !aligned(x_dev, 4) || !aligned(q_dev, 4))
         return fail(ctx, TOMO_ERR_ARG, "x_dev / q_dev NULL or misaligned");
+    if (!aligned(prior_weight_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "misaligned prior_weight_dev");
     if (!isfinite(lambda) || lambda < 0)
         return fail(ctx, TOMO_ERR_ARG, "lambda must be finite and >= 0");
     DeviceGuard guard(ctx->device);
     if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
     cudaStream_t s = (cudaStream_t)stream;
     LAUNCH(ctx, TOMO_K_PRIOR, s,
-           launch_prior(cube_dev(cube), x_dev, q_dev, (float)lambda,
+           launch_prior(cube_dev(cube), x_dev, prior_weight_dev, q_dev,
+                        (float)lambda,
                         (flags & TOMO_ACCUMULATE) != 0, nullptr, s));
     return TOMO_OK;
 }
@@ -701,9 +705,10 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                        const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
                        const uint8_t *mask_dev, const uint8_t *map_mask_dev,
-                       const float *y_dev, float *x_dev, double lambda,
-                       int32_t max_iter, double tol, uint32_t flags,
-                       double *report_host, int32_t *iters_host, void *stream)
+                       const float *prior_weight_dev, const float *y_dev,
+                       float *x_dev, double lambda, int32_t max_iter,
+                       double tol, uint32_t flags, double *report_host,
+                       int32_t *iters_host, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
@@ -719,6 +724,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         return fail(ctx, TOMO_ERR_ARG, "tol must be finite and >= 0");
     if (!x_dev || !aligned(x_dev, 4))
         return fail(ctx, TOMO_ERR_ARG, "x_dev NULL or misaligned");
+    if (!aligned(prior_weight_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "misaligned prior_weight_dev");
     if (img->n_img > 0 && (!y_dev || !aligned(y_dev, 4)))
         return fail(ctx, TOMO_ERR_ARG, "y_dev NULL or misaligned");
     DeviceGuard guard(ctx->device);
@@ -783,7 +790,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         // r0 = b - (P^T M P + lambda D^T D) x0
         if (mm)
             LAUNCH(ctx, TOMO_K_VECTOR, s, launch_map_zero(x_dev, mm, n, 1, s));
-        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, q, lam, false, nullptr, s));
+        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, prior_weight_dev, q, lam, false,
+                                                  nullptr, s));
         if (m > 0 &&
             ((st = forward_one(ctx, x_dev, TOMO_F32, 1, mask_dev, t, cube, img,
                                tl, nullptr, s)) ||
@@ -805,7 +813,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
             (st = forward_one(ctx, p_gather, p_dtype, 1, mask_dev, t, cube, img,
                               tl, done, s)))
             return st;
-        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, q, lam, false, done, s));
+        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, prior_weight_dev, q, lam, false,
+                                                  done, s));
         if (m > 0 &&
             (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, done, s)))
             return st;

@@ -404,7 +404,7 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
                     const int i = (int)(v % nx);
                     const int64_t r = v / nx;
                     const int j = (int)(r % ny), k = (int)(r / ny);
-                    d.q[v] = prior_at(src, v, i, j, k, nx, ny, nz, d.lam);
+                    d.q[v] = prior_at(src, d.w, v, i, j, k, nx, ny, nz, d.lam);
                 }
             }
         } else if (op == V_PQ) {

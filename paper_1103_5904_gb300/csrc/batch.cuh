@@ -55,6 +55,7 @@ struct VecDesc {
     const float *y;
     const uint8_t *mask;
     const uint8_t *mm;  // map mask (nullable): restricts b, r, p, x0
+    const float *w;     // prior weight R (nullable): lambda R D^T D R
     double *S;       // the problem's FP64 slots (S_*)
     double *report;  // (n_iter + 1) x 2: J, r.r
     int64_t n, m;    // voxels, pixels

@@ -120,6 +120,8 @@ tomo_status check_problem(tomo_ctx *ctx, const tomo_problem *p, int32_t i,
                     "problem %d: images_dev NULL or misaligned", i);
     if (!isfinite(p->lambda) || p->lambda < 0)
         return fail(ctx, TOMO_ERR_ARG, "problem %d: lambda must be >= 0", i);
+    if (!aligned(p->prior_weight_dev, 4))
+        return fail(ctx, TOMO_ERR_ARG, "problem %d: misaligned prior_weight_dev", i);
     return TOMO_OK;
 }
 
@@ -700,8 +702,9 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
     // graph key: geometry plan + caller buffers + lambdas + run shape
     uint64_t h = P->geom_key;
     for (int32_t i = 0; i < n; ++i) {
-        const void *ptrs[4] = { probs[i].images_dev, probs[i].cube_dev,
-                                probs[i].mask_dev, probs[i].map_mask_dev };
+        const void *ptrs[5] = { probs[i].images_dev, probs[i].cube_dev,
+                                probs[i].mask_dev, probs[i].map_mask_dev,
+                                probs[i].prior_weight_dev };
         h = fnv1a(h, ptrs, sizeof(ptrs));
         h = fnv1a(h, &probs[i].lambda, sizeof(double));
     }
@@ -769,6 +772,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             v.y = p.images_dev;
             v.mask = p.mask_dev;
             v.mm = p.map_mask_dev;
+            v.w = p.prior_weight_dev;
             v.S = Si;
             v.report = rep + (size_t)i * stride;
             v.n = voff[i + 1] - voff[i];

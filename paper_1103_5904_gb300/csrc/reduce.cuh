@@ -84,21 +84,37 @@ __device__ __forceinline__ void cg_finalize_update(double *S, double *report,
     }
 }
 
-// The 7-point stencil of lambda D^T D at voxel (i, j, k) of x.
+// The 7-point stencil of lambda D^T D at voxel (i, j, k) of x, or with a
+// diagonal weight w (nullable) the stencil of lambda R D^T D R, R = diag(w)
+// (the height-weighted prior ||D R x||^2 of Eq. srt_inversion): the
+// differences are taken of w x and the result is scaled by w at (i, j, k).
 __device__ __forceinline__ float prior_at(const float *__restrict__ x,
+                                          const float *__restrict__ w,
                                           int64_t v, int i, int j, int k,
                                           int nx, int ny, int nz, float lam)
 {
     const int64_t sy = nx, sz = (int64_t)nx * ny;
-    const float xc = x[v];
+    if (w == nullptr) {
+        const float xc = x[v];
+        float s = 0.0f;
+        if (i > 0) s += xc - x[v - 1];
+        if (i < nx - 1) s += xc - x[v + 1];
+        if (j > 0) s += xc - x[v - sy];
+        if (j < ny - 1) s += xc - x[v + sy];
+        if (k > 0) s += xc - x[v - sz];
+        if (k < nz - 1) s += xc - x[v + sz];
+        return lam * s;
+    }
+    const float wc = w[v];
+    const float xc = wc * x[v];
     float s = 0.0f;
-    if (i > 0) s += xc - x[v - 1];
-    if (i < nx - 1) s += xc - x[v + 1];
-    if (j > 0) s += xc - x[v - sy];
-    if (j < ny - 1) s += xc - x[v + sy];
-    if (k > 0) s += xc - x[v - sz];
-    if (k < nz - 1) s += xc - x[v + sz];
-    return lam * s;
+    if (i > 0) s += xc - w[v - 1] * x[v - 1];
+    if (i < nx - 1) s += xc - w[v + 1] * x[v + 1];
+    if (j > 0) s += xc - w[v - sy] * x[v - sy];
+    if (j < ny - 1) s += xc - w[v + sy] * x[v + sy];
+    if (k > 0) s += xc - w[v - sz] * x[v - sz];
+    if (k < nz - 1) s += xc - w[v + sz] * x[v + sz];
+    return lam * wc * s;
 }
 
 }  // namespace tomo

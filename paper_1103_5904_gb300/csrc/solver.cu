@@ -70,7 +70,8 @@ __device__ __forceinline__ float direction_store(float v, uint16_t *p16,
 }
 
 __global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
-                        float *__restrict__ q, float lam, bool accumulate,
+                        const float *__restrict__ w, float *__restrict__ q,
+                        float lam, bool accumulate,
                         const double *__restrict__ done)
 {
     if (done != nullptr && *done != 0.0) return;
@@ -79,7 +80,7 @@ __global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
     const int k = blockIdx.z;
     if (i >= nx || j >= ny) return;
     const int64_t v = ((int64_t)k * ny + j) * nx + i;
-    const float val = prior_at(x, v, i, j, k, nx, ny, nz, lam);
+    const float val = prior_at(x, w, v, i, j, k, nx, ny, nz, lam);
     q[v] = accumulate ? q[v] + val : val;
 }
 
@@ -204,13 +205,14 @@ unsigned int fill_grid(int64_t n)
 
 }  // namespace
 
-cudaError_t launch_prior(CubeDev c, const float *x, float *q, float lam,
-                         bool accumulate, const double *done, cudaStream_t s)
+cudaError_t launch_prior(CubeDev c, const float *x, const float *w, float *q,
+                         float lam, bool accumulate, const double *done,
+                         cudaStream_t s)
 {
     const dim3 block(32, 8);
     const dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
                     (unsigned)c.nz);
-    k_prior<<<grid, block, 0, s>>>(c.nx, c.ny, c.nz, x, q, lam, accumulate,
+    k_prior<<<grid, block, 0, s>>>(c.nx, c.ny, c.nz, x, w, q, lam, accumulate,
                                    done);
     return cudaGetLastError();
 }

@@ -192,8 +192,10 @@ cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
                          unsigned long long *count, cudaStream_t s);
 
 // ---- solver.cu
-cudaError_t launch_prior(CubeDev cube, const float *x, float *q, float lam,
-                         bool accumulate, const double *done, cudaStream_t s);
+// q = lambda D^T D x, or lambda R D^T D R x with R = diag(w) (w nullable)
+cudaError_t launch_prior(CubeDev cube, const float *x, const float *w,
+                         float *q, float lam, bool accumulate,
+                         const double *done, cudaStream_t s);
 cudaError_t launch_fill_f32(float *p, float v, int64_t n, cudaStream_t s);
 cudaError_t launch_fill_f64(double *p, double v, int64_t n, cudaStream_t s);
 // S[S_YMY] = sum over unmasked pixels of y^2

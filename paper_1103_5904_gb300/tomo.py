@@ -62,7 +62,8 @@ class Problem(C.Structure):
     _fields_ = [("cube", CubeGeom), ("img", ImageGeom), ("reserved", C.c_int32),
                 ("pointing_host", C.POINTER(Pointing)), ("mask_dev", C.c_void_p),
                 ("images_dev", C.c_void_p), ("cube_dev", C.c_void_p),
-                ("lam", C.c_double), ("map_mask_dev", C.c_void_p)]
+                ("lam", C.c_double), ("map_mask_dev", C.c_void_p),
+                ("prior_weight_dev", C.c_void_p)]
 
 
 class TilingResult(C.Structure):
@@ -72,7 +73,7 @@ class TilingResult(C.Structure):
 
 
 assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
-assert C.sizeof(Problem) == 136
+assert C.sizeof(Problem) == 144
 
 
 class TomoError(RuntimeError):
@@ -102,12 +103,12 @@ _SIGNATURES = {
                                    C.POINTER(ImageGeom), C.POINTER(Pointing),
                                    _VP, _VP, _VP, _VP, C.c_uint32, _VP]),
     "tomo_solve": (C.c_int, [_VP, C.POINTER(CubeGeom), C.POINTER(ImageGeom),
-                             C.POINTER(Pointing), _VP, _VP, _VP, _VP,
+                             C.POINTER(Pointing), _VP, _VP, _VP, _VP, _VP,
                              C.c_double,
                              C.c_int32, C.c_double, C.c_uint32,
                              C.POINTER(C.c_double), C.POINTER(C.c_int32),
                              _VP]),
-    "tomo_prior_apply": (C.c_int, [_VP, C.POINTER(CubeGeom), _VP, _VP,
+    "tomo_prior_apply": (C.c_int, [_VP, C.POINTER(CubeGeom), _VP, _VP, _VP,
                                    C.c_double, C.c_uint32, _VP]),
     "tomo_count_segments": (C.c_int, [_VP, C.POINTER(CubeGeom),
                                       C.POINTER(ImageGeom),
@@ -268,6 +269,16 @@ def _check_map_mask(map_mask, geom):
                          % (nvox, map_mask.numel()))
 
 
+def _check_weight(w, geom):
+    """Prior weight: float32 ``[nz][ny][nx]`` on the device, the diagonal of
+    R in the height-weighted prior ``lam ||D R x||^2``."""
+    _dev(w, torch.float32, "prior_weight")
+    nvox = int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"])
+    if w is not None and w.numel() != nvox:
+        raise ValueError("prior_weight must have nx * ny * nz = %d elements "
+                         "(got %d)" % (nvox, w.numel()))
+
+
 def _stream_ptr(stream, device):
     s = stream if stream is not None else torch.cuda.current_stream(device)
     return _VP(s.cuda_stream)
@@ -350,9 +361,10 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
 
 def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
                x0=None, bf16=False, out=None, report=True, ctx=None,
-               stream=None, map_mask=None):
-    """CG on ``(P^T M P + lam D^T D) x = P^T M y`` (restricted to the voxels
-    that ``map_mask`` keeps).  Returns ``(x, info)`` with
+               stream=None, map_mask=None, prior_weight=None):
+    """CG on ``(P^T M P + lam R D^T D R) x = P^T M y`` (R = diag of
+    ``prior_weight``, else the identity; restricted to the voxels that
+    ``map_mask`` keeps).  Returns ``(x, info)`` with
     ``info = {"J": ..., "rr": ..., "iters": ...}`` when ``report``."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
@@ -374,12 +386,13 @@ def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
         flags |= TOMO_SOLVE_BF16
     _check_mask(mask, n_img, nu, nv)
     _check_map_mask(map_mask, geom)
+    _check_weight(prior_weight, geom)
     cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
     rep = np.full(2 * (int(max_iter) + 1), np.nan) if report else None
     iters = C.c_int32(0)
     ctx.check(load_library().tomo_solve(
         ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
-        _ptr(map_mask), _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
+        _ptr(map_mask), _ptr(prior_weight), _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
         rep.ctypes.data_as(C.POINTER(C.c_double)) if report else None,
         C.byref(iters) if report else None, _stream_ptr(stream, y.device)))
     info = None
@@ -391,8 +404,9 @@ def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
 
 
 def tomo_prior_apply(x, geom, lam, out=None, accumulate=False, ctx=None,
-                     stream=None):
-    """``q = lam D^T D x`` (+ q with ``accumulate``)."""
+                     stream=None, prior_weight=None):
+    """``q = lam D^T D x``, or ``lam R D^T D R x`` with ``prior_weight``
+    (the diagonal of R), + q with ``accumulate``."""
     ctx = _ctx(ctx)
     _dev(x, torch.float32, "x")
     if out is None:
@@ -402,9 +416,11 @@ def tomo_prior_apply(x, geom, lam, out=None, accumulate=False, ctx=None,
     nvox = int(geom["nx"]) * int(geom["ny"]) * int(geom["nz"])
     if x.numel() != nvox or out.numel() != nvox:
         raise ValueError("x and out must have nx * ny * nz elements")
+    _check_weight(prior_weight, geom)
     cg = cube_geom_struct(geom)
     ctx.check(load_library().tomo_prior_apply(
-        ctx.handle, C.byref(cg), _ptr(x), _ptr(out), float(lam),
+        ctx.handle, C.byref(cg), _ptr(x), _ptr(prior_weight), _ptr(out),
+        float(lam),
         TOMO_ACCUMULATE if accumulate else 0, _stream_ptr(stream, x.device)))
     return out
 
@@ -428,7 +444,8 @@ def tomo_count_segments(geom, pointing, nu, nv, mask=None, ctx=None,
 
 def _problems(problems, need_cube=True, need_images=True):
     """ctypes array of tomo_problem from dicts with keys geom, pointing, nu,
-    nv, cube, images, mask (optional), map_mask (optional), lam (optional).  Returns the array and
+    nv, cube, images, mask, map_mask, prior_weight, lam (the last four
+    optional).  Returns the array and
     the pointing arrays it points into (keep them alive)."""
     arr = (Problem * len(problems))()
     keep = []
@@ -443,6 +460,8 @@ def _problems(problems, need_cube=True, need_images=True):
         _check_mask(mask, n_img, nu, nv)
         map_mask = p.get("map_mask")
         _check_map_mask(map_mask, p["geom"])
+        weight = p.get("prior_weight")
+        _check_weight(weight, p["geom"])
         nvox = int(p["geom"]["nx"]) * int(p["geom"]["ny"]) * int(p["geom"]["nz"])
         if need_cube and (cube is None or cube.numel() != nvox):
             raise ValueError("problem %d: cube must have nx*ny*nz elements" % i)
@@ -458,6 +477,7 @@ def _problems(problems, need_cube=True, need_images=True):
         arr[i].cube_dev = None if cube is None else cube.data_ptr()
         arr[i].lam = float(p.get("lam", 0.0))
         arr[i].map_mask_dev = None if map_mask is None else map_mask.data_ptr()
+        arr[i].prior_weight_dev = None if weight is None else weight.data_ptr()
     return arr, keep
 
 

@@ -46,7 +46,7 @@ def test_status_strings_and_null_context(lib):
     assert lib.tomo_backproject(None, None, 1, None, None, None, None, None,
                                 None, 0, None) == -1
     assert lib.tomo_solve(None, None, None, None, None, None, None, None,
-                          C.c_double(0), 0, C.c_double(0), 0, None, None,
+                          None, C.c_double(0), 0, C.c_double(0), 0, None, None,
                           None) == -1
     h = C.c_void_p()
     assert lib.tomo_create(C.byref(h), -1) == -1  # invalid device
@@ -65,7 +65,7 @@ int main(void) {
          offsetof(tomo_cube_geom, r_obs),
          sizeof(tomo_image_geom), sizeof(tomo_pointing), sizeof(tomo_profile),
          sizeof(tomo_problem), offsetof(tomo_problem, lambda),
-         offsetof(tomo_problem, map_mask_dev));
+         offsetof(tomo_problem, prior_weight_dev));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -77,7 +77,7 @@ int main(void) {
             C.sizeof(tomo.ImageGeom),
             C.sizeof(tomo.Pointing), C.sizeof(tomo.Profile),
             C.sizeof(tomo.Problem), tomo.Problem.lam.offset,
-            tomo.Problem.map_mask_dev.offset]
+            tomo.Problem.prior_weight_dev.offset]
     assert got == want
 
 
