@@ -13,10 +13,11 @@ Modules:
   siddon.py        ctypes bindings of the C oracle
   checks.py        brute-force voxel clipping and fine sampling (pins)
   solver.py        finite-difference prior D, criterion J, textbook CG
+  thomson.py       Thomson-scattering coefficients and the pB / B operators
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 against geometry, closed forms and brute force.  Agreement with the paper's
 own software is unpinned: the paper prints no projector outputs.
 """
 
-from . import siddon, checks, solver  # noqa: F401
+from . import siddon, checks, solver, thomson  # noqa: F401

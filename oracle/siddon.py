@@ -61,6 +61,8 @@ def lib():
         L.orc_count_segments.argtypes = [cp, C.c_int32, C.c_int32, C.c_int32,
                                          dp, up, C.c_int64, lp]
         L.orc_count_segments.restype = C.c_int64
+        L.orc_impact2.argtypes = [C.c_int32, C.c_int32, C.c_int32, dp, dp]
+        L.orc_impact2.restype = C.c_int
         L.orc_get_threads.restype = C.c_int
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -214,3 +216,14 @@ def count_segments(geom, pointing, nu, nv, mask=None, ray_ids=None):
     r, nr, rp = _rays(ray_ids)
     return int(lib().orc_count_segments(C.byref(c), ptg.shape[0], int(nu),
                                         int(nv), _dp(ptg), mp, nr, rp))
+
+
+def impact2(pointing, nu, nv):
+    """rho^2 = |o x u|^2 of every pixel's line of sight, ``[n_img][nv][nu]``
+    (the squared distance of Sun centre from the line)."""
+    ptg = _f64(pointing)
+    out = np.zeros((ptg.shape[0], int(nv), int(nu)))
+    if lib().orc_impact2(ptg.shape[0], int(nu), int(nv), _dp(ptg),
+                         _dp(out)) != 0:
+        raise ValueError("pointing frame undefined")
+    return out

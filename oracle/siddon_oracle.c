@@ -466,3 +466,25 @@ int64_t orc_count_segments(const orc_cube *c, int32_t n_img, int32_t nu,
     }
     return sum;
 }
+
+/* ------------------------------------------------- impact parameter */
+
+/* Squared impact parameter of every pixel's line of sight: rho^2 = |o x u|^2,
+ * the squared distance from Sun centre to the line (Section 3.5: the pB
+ * operator's per-pixel diagonal o_k = rho_k^2, Eq. thomson_lo).  out is
+ * [n_img][nv][nu].  Returns 0, or -1 on an undefined pointing frame. */
+int orc_impact2(int32_t n_img, int32_t nu, int32_t nv, const double *pointing,
+                double *out)
+{
+    for (int32_t n = 0; n < n_img; ++n)
+        for (int32_t iv = 0; iv < nv; ++iv)
+            for (int32_t iu = 0; iu < nu; ++iu) {
+                double o[3], u[3], c[3];
+                if (orc_ray(pointing + (size_t)n * C_NCOL, iu, iv, o, u) != 0)
+                    return -1;
+                cross3(o, u, c);
+                out[((size_t)n * nv + iv) * nu + iu] =
+                    c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+            }
+    return 0;
+}

@@ -20,6 +20,10 @@ smoothing grows with altitude.  The oracle takes the diagonal as given
 the altitude above the photosphere, is the caller's choice); the normal
 operator's prior term is lambda R D^T D R.
 
+White-light data (Section 3.5): with ``kind`` PB or B the projector P is
+replaced by the Thomson operator T_pB or T_B of ``thomson.py`` (limb
+darkening ``limb_u``) in every formula here.
+
 A map mask (nonzero = voxel excluded from the map) restricts the unknowns
 to the other voxels; reading: the excluded voxels are zero in the map that P
 and D see, so with K = diag(1 - mask) the criterion is
@@ -34,7 +38,7 @@ tried no preconditioner, Section 5.2).
 
 import numpy as np
 
-from . import siddon
+from . import siddon, thomson
 
 
 def D(x):
@@ -76,7 +80,7 @@ class Problem:
     """One static reconstruction: cube geometry, pointing, mask, data, lambda."""
 
     def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0,
-                 map_mask=None, prior_weight=None):
+                 map_mask=None, prior_weight=None, kind=0, limb_u=0.0):
         self.geom, self.pointing = geom, np.asarray(pointing, np.float64)
         self.nu, self.nv = int(nu), int(nv)
         self.mask = mask
@@ -85,6 +89,7 @@ class Problem:
         self.shape = (geom["nz"], geom["ny"], geom["nx"])
         self.keep = (None if map_mask is None else
                      (np.asarray(map_mask) == 0).astype(np.float64))
+        self.kind, self.limb_u = int(kind), float(limb_u)
         self.w = (None if prior_weight is None else
                   np.asarray(prior_weight, dtype=np.float64).reshape(self.shape))
 
@@ -97,10 +102,18 @@ class Problem:
         return x if self.w is None else x * self.w
 
     def P(self, x):
+        if self.kind:
+            return thomson.project(self.kind, self.geom, self.K(x),
+                                   self.pointing, self.nu, self.nv,
+                                   self.limb_u, self.mask)
         return siddon.project(self.geom, self.K(x), self.pointing, self.nu,
                               self.nv, self.mask)
 
     def Pt(self, y):
+        if self.kind:
+            return self.K(thomson.backproject(self.kind, self.geom, y,
+                                              self.pointing, self.nu, self.nv,
+                                              self.limb_u, self.mask))
         return self.K(siddon.backproject(self.geom, y, self.pointing, self.nu,
                                          self.nv, self.mask))
 

@@ -701,3 +701,106 @@ def test_obstacle_adjoint_identity_and_blocking_fp64():
     assert np.all(Pty[far < 1.0] == 0.0)
     g0 = dict(g, r_obs=0.0)
     assert np.all(Px <= siddon.project(g0, x, ptg, 17, 13) + 1e-12)
+
+
+# ------------------------------------------------------ Thomson scattering
+
+def _disk_integrals(r, u):
+    """Direct quadrature over the limb-darkened solar disk seen from distance
+    r (radius 1): an unpolarised ray from direction n, at angle t from the
+    direction of Sun centre, scattered at 90 degrees, gives intensity
+    1 - (e.n)^2 along each polarisation e; averaged over the azimuth this is
+    1 - sin^2(t)/2 for the tangential one and the tangential minus radial
+    difference is cos^2(t) - sin^2(t)/2.  The disk's brightness is
+    1 - u + u mu with mu the cosine of the emission angle at the surface."""
+    from scipy.integrate import quad
+    om = math.asin(1.0 / r)
+
+    def bright(t):
+        return 1.0 - u + u * math.sqrt(max(1.0 - (r * math.sin(t)) ** 2, 0.0))
+    kw = dict(limit=400, epsabs=1e-14, epsrel=1e-12)
+    qt = 2 * math.pi * quad(lambda t: bright(t) * (1 - 0.5 * math.sin(t) ** 2)
+                            * math.sin(t), 0.0, om, **kw)[0]
+    qp = 2 * math.pi * quad(lambda t: bright(t) * (math.cos(t) ** 2 - 0.5 *
+                                                   math.sin(t) ** 2)
+                            * math.sin(t), 0.0, om, **kw)[0]
+    return qt, qp
+
+
+@pytest.mark.parametrize("r", [1.02, 1.3, 2.0, 5.0])
+def test_thomson_coefficients_against_disk_quadrature(r):
+    """pi ((1-u) C1 + u C2) and pi ((1-u) C3 + u C4) (Eq. 4C with sin Omega =
+    1/r and +1/8 on C4) equal the disk integrals that define them; the
+    printed -1/8 on C4 fails them.  Also the surface values and the
+    point-source limit (C2/C1 and C4/C3 -> 2/3, the flux ratio of a fully
+    limb-darkened disk)."""
+    from oracle import thomson
+    C1, C2, C3, C4 = [float(v) for v in thomson.coefficients(r)]
+    for u in (0.0, 0.4, 1.0):
+        qt, qp = _disk_integrals(r, u)
+        assert math.pi * ((1 - u) * C1 + u * C2) == pytest.approx(qp, rel=1e-9)
+        assert math.pi * ((1 - u) * C3 + u * C4) == pytest.approx(qt, rel=1e-9)
+    qt, _ = _disk_integrals(r, 1.0)
+    assert math.pi * -C4 != pytest.approx(qt, rel=1e-3)
+    c0 = [float(v) for v in thomson.coefficients(1.0)]
+    assert c0 == pytest.approx([0.0, 0.25, 4.0 / 3.0, 0.75], abs=1e-15)
+    far = [float(v) for v in thomson.coefficients(300.0)]
+    assert far[1] / far[0] == pytest.approx(2.0 / 3.0, rel=1e-4)
+    assert far[3] / far[2] == pytest.approx(2.0 / 3.0, rel=1e-4)
+
+
+def test_impact2_matches_pixel_angles():
+    """rho^2 of a pixel's ray equals (d sin theta)^2 with theta the angle of
+    the pixel from the boresight (boresight on Sun centre, crval 0), for
+    rolled views too."""
+    ptg = synth.pointing_table([10.0, 200.0], [4.0, -6.0], 215.0, 16, 12, 4.0,
+                               roll_deg=17.0)
+    r2 = siddon.impact2(ptg, 16, 12)
+    for n in range(2):
+        d, cu, cv, pu, pv = ptg[n, 0], ptg[n, 4], ptg[n, 5], ptg[n, 6], ptg[n, 7]
+        tu = np.tan((np.arange(16) - pu) * cu)
+        tv = np.tan((np.arange(12) - pv) * cv)
+        t2 = tv[:, None] ** 2 + tu[None, :] ** 2
+        np.testing.assert_allclose(r2[n], d * d * t2 / (1 + t2), rtol=1e-10)
+
+
+@pytest.mark.parametrize("T", [1, 3])
+def test_thomson_operators_adjoint_and_rows(T):
+    """T_pB and T_B against brute-force rows (exact voxel lengths times the
+    voxel-centre factors, rho^2 from the pixel angles), their FP64 adjoint
+    identities (pixel mask, map mask, frames), and m = m' = 0 inside the
+    photosphere."""
+    from oracle import thomson
+    g, ptg, mask, rng = _small_scene(T)
+    shape = ((T,) if T > 1 else ()) + (g["nz"], g["ny"], g["nx"])
+    x = rng.random(shape)
+    y = rng.random((5, 6, 10))
+    mm = (rng.random((g["nz"], g["ny"], g["nx"])) < 0.2).astype(np.uint8)
+    u = 0.6
+    m, mp = thomson.voxel_factors(g, u)
+    ax = [synth.voxel_centres(g, a) for a in "xyz"]
+    rad = np.sqrt(ax[2][:, None, None] ** 2 + ax[1][None, :, None] ** 2 +
+                  ax[0][None, None, :] ** 2)
+    assert np.all(m[rad <= 1] == 0) and np.all(mp[rad <= 1] == 0)
+    assert np.all(m[rad > 1] > 0) and np.all(mp[rad > 1] > 0)
+    for kind in (thomson.PB, thomson.B):
+        Tx = thomson.project(kind, g, x, ptg, 10, 6, u, mask, T, map_mask=mm)
+        Tty = thomson.backproject(kind, g, y, ptg, 10, 6, u, mask, T,
+                                  map_mask=mm)
+        lhs = float(np.sum(Tx * np.where(mask == 0, y, 0)))
+        assert lhs == pytest.approx(float(np.sum(x * Tty)), rel=1e-12)
+        if T > 1:
+            continue
+        keep = (mm == 0).reshape(-1)
+        for r in rng.choice(5 * 60, 30, replace=False):
+            n, iv, iu = r // 60, (r // 10) % 6, r % 10
+            o, dirn = siddon.ray(ptg[n], iu, iv)
+            row = checks.brute_force_ray(g, o, dirn) * keep * ptg[n, 10]
+            tu = math.tan((iu - ptg[n, 6]) * ptg[n, 4])
+            tv = math.tan((iv - ptg[n, 7]) * ptg[n, 5])
+            rho2 = ptg[n, 0] ** 2 * (tu * tu + tv * tv) / (1 + tu * tu + tv * tv)
+            pm = float(np.sum(row * (m * x).reshape(-1)))
+            want = rho2 * pm if kind == thomson.PB else \
+                float(np.sum(row * (mp * x).reshape(-1))) - rho2 * pm
+            want = 0.0 if mask[n, iv, iu] else want
+            assert Tx[n, iv, iu] == pytest.approx(want, rel=1e-10, abs=1e-16)
