@@ -23,8 +23,8 @@
  *    not these formulas; this is the library's reading.
  *  - Voxels are half-open, [x0 + i dx, x0 + (i+1) dx): a ray lying exactly on
  *    a face is charged to the voxel above it.
- *  - Masks: uint8 [n_img][nv][nu], nonzero = excluded (Section 4: masked
- *    pixels are not projected).  P writes 0 there, P^T ignores them.
+ *  - Masks: uint8 [n_img][nv][nu], nonzero = excluded (Section 4: the
+ *    projector skips masked pixels).  P writes 0 there, P^T ignores them.
  *  - Map masks: uint8 [nz][ny][nx], nonzero = voxel excluded from the map
  *    (Section 4 names masks of the data and of the map; the paper gives no
  *    formula).  Reading: an excluded voxel is not an unknown.  P reads it as
@@ -79,8 +79,8 @@ typedef struct {
     double dx, dy, dz;
     /* Radius of an opaque sphere centred at the frame origin (the
      * photosphere, in the cube's units), or 0 for none.  Lines of sight end
-     * where they first reach it (the paper stops the integration "when the
-     * ray reaches the photosphere", Section 4); a line of sight from an
+     * where they first reach it (the paper ends the line-of-sight
+     * integration at the photosphere, Section 4); a line of sight from an
      * observer inside the sphere integrates nothing.  Must be finite and
      * >= 0. */
     double r_obs;
@@ -234,8 +234,8 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
 /* Regularised least squares (Eq. criterion with A = M P, B = D, or
  * B = D R for the height-weighted prior of Eq. srt_inversion):
  *     x = argmin ||M (y - P x)||^2 + lambda ||D R x||^2 ,
- * D = forward differences along x, y, z without wrap (Section 3.3.1, "a
- * finite-difference operator along each axis"), R = diag(prior weight) or
+ * D = forward differences along x, y, z without wrap (Section 3.3.1: finite
+ * differences along each axis of the map), R = diag(prior weight) or
  * the identity, by conjugate gradients on
  * (P^T M P + lambda R D^T D R) x = P^T M y, one static frame, FP32 vectors
  * and FP64 scalars (alpha, beta, residual norms, J).

@@ -13,9 +13,10 @@
  *
  * where P_{k,j} is the length of the line of sight of pixel k inside voxel j
  * and g_n the gain of the image n holding pixel k (Eq. two_spacecraft).  The
- * paper's index letters are garbled (it writes "e_i ... voxel j"); this file
+ * paper's index letters are garbled (the voxel index of Eq. lo is written
+ * with two different letters); this file
  * reads k as the pixel and j as the voxel.  Masked pixels project to 0 and are
- * ignored by the transpose (Section 4: "masked pixels are not projected").
+ * ignored by the transpose (Section 4: the projector skips masked pixels).
  * The transpose is the exact matrix transpose of the same P.
  *
  * Siddon's algorithm is cited by the paper (Section 3.1) but not restated.
@@ -138,9 +139,8 @@ int orc_ray(const double *p, int32_t iu, int32_t iv, double o[3], double u[3])
  * in [lo_a, lo_a + n_a d_a).  Returns 1 on a hit of positive length. */
 /* The part of the half-line o + a u (a >= 0, u a unit vector) that the line
  * of sight integrates: the slab clip against the cube, ended where the ray
- * first meets the opaque sphere if there is one.  The paper stops the
- * integration "when the ray reaches the photosphere" (Section 4) and gives
- * no formula; reading: the first root a of |o + a u| = r_obs ends the
+ * first meets the opaque sphere if there is one.  The paper ends the
+ * integration at the photosphere (Section 4) and gives no formula; reading: the first root a of |o + a u| = r_obs ends the
  * interval, a ray from an observer inside (or on) the sphere integrates
  * nothing, and a ray that misses or only grazes the sphere is unchanged. */
 int orc_clip(const orc_cube *c, const double o[3], const double u[3],

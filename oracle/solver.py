@@ -7,14 +7,14 @@ The criterion is Eq. criterion of the paper (Section 2.2),
     J(x) = ||y - A x||^2 + lambda ||B x||^2 ,
     x_hat = (A^T A + lambda B^T B)^{-1} A^T y ,
 
-with A = M P (the masked projector: masked pixels are not projected, Section
-4) and B = D, "a finite-difference operator along each axis of the maps"
-(Section 3.3.1).  Reading of D where the paper is silent: forward
+with A = M P (the masked projector: the projector skips masked pixels,
+Section 4) and B = D, finite differences along each axis of the map (Section
+3.3.1).  Reading of D where the paper is silent: forward
 differences ``x[i+1] - x[i]`` along x, y and z, without wrap-around (N - 1
 differences per line), the same lambda on every axis (as in Table hypers).
 
 Height-weighted prior (Eq. srt_inversion, Section 3.3.1): B = D R with R a
-diagonal operator, "the height of the voxels" on its diagonal, so that the
+diagonal operator holding the voxels' heights, so that the
 smoothing grows with altitude.  The oracle takes the diagonal as given
 (``prior_weight``, one value per voxel; which height, e.g. the radius or
 the altitude above the photosphere, is the caller's choice); the normal

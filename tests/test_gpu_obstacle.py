@@ -1,6 +1,6 @@
 """Opaque photosphere (cube geometry r_obs > 0): lines of sight end where
-they first reach the sphere of that radius at the origin (Section 4 stops
-the integration "when the ray reaches the photosphere").
+they first reach the sphere of that radius at the origin (Section 4 ends
+the line-of-sight integration at the photosphere).
 
 The GPU path applies it in the FP64 ray setup, so every walk inherits it
 through the chord; these cases compare P, P^T and CG with the FP64 oracle
