@@ -86,9 +86,30 @@ typedef struct {
     double r_obs;
 } tomo_cube_geom;
 
-/* Image stack geometry: n_img images of nv rows by nu columns. */
+/* What the images measure (Section 3.5; tomo_image_geom.kind). */
+#define TOMO_KIND_EMISSION 0 /* line-of-sight integral y = P x (EUV, Eq. srt) */
+#define TOMO_KIND_PB 1       /* polarised brightness, y = O P M x */
+#define TOMO_KIND_B 2        /* total brightness, y = P M' x - O P M x */
+
+/* Image stack geometry: n_img images of nv rows by nu columns, and what
+ * they measure.  With kind PB or B the single-problem entry points apply
+ * the Thomson operator instead of P (its transpose instead of P^T, in the
+ * solver too): O = diag(rho_k^2), rho = impact parameter of the pixel's line
+ * of sight; M = diag(m_j), M' = diag(m'_j) at the voxel centre's distance r
+ * from Sun centre, with sin(Omega) = 1/r and the coefficients C1..C4 of
+ * Eq. 4C:
+ *     m_j  = ((1 - u) C1 + u C2) / r^4 ,
+ *     m'_j = 2 ((1 - u) C3 + u C4) / r^2      (Eq. brightness),
+ * 0 for r <= 1 (inside the photosphere).  Readings: C4 takes +1/8 (the
+ * printed -1/8 makes the scattered intensity of a limb-darkened Sun
+ * negative), m_j keeps the u on C2 and m'_j the factor 2 of Eq. brightness,
+ * and the constant pi sigma I0 / 2 is left to the per-image gains.
+ * limb_u: limb-darkening coefficient u in [0, 1] (ignored for EMISSION).
+ * The batched and allocation-free entry points accept EMISSION only. */
 typedef struct {
     int32_t n_img, nu, nv;
+    int32_t kind;
+    double limb_u;
 } tomo_image_geom;
 
 /* One pointing record (96 bytes; the 12 doubles of one row of a float64

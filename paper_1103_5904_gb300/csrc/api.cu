@@ -94,6 +94,11 @@ tomo_status check_img(tomo_ctx *ctx, const tomo_image_geom *g)
                          g->nv > 1 << 19))
         return fail(ctx, TOMO_ERR_ARG, "image size out of range (%d x %d)",
                     g->nu, g->nv);
+    if (g->kind < TOMO_KIND_EMISSION || g->kind > TOMO_KIND_B)
+        return fail(ctx, TOMO_ERR_ARG, "unknown image kind %d", g->kind);
+    if (g->kind != TOMO_KIND_EMISSION &&
+        !(isfinite(g->limb_u) && g->limb_u >= 0.0 && g->limb_u <= 1.0))
+        return fail(ctx, TOMO_ERR_ARG, "limb_u must be in [0, 1]");
     return TOMO_OK;
 }
 
@@ -224,6 +229,15 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                             (const double *)ctx->tan_u.p,
                             (const double *)ctx->tan_v.p, cube_dev(c),
                             g->n_img, g->nu, g->nv, (RayRec *)ctx->rays.p, s));
+    if (g->kind != TOMO_KIND_EMISSION) {
+        if ((st = ensure(ctx, ctx->rho2, sizeof(float) * (npix > 0 ? npix : 1))))
+            return st;
+        LAUNCH(ctx, TOMO_K_SETUP, s,
+               launch_impact2((const Frame *)ctx->frames.p,
+                              (const double *)ctx->tan_u.p,
+                              (const double *)ctx->tan_v.p, g->n_img, g->nu,
+                              g->nv, (float *)ctx->rho2.p, s));
+    }
     CUDA_TRY(ctx, cudaEventRecord(ctx->setup_done, s));
     ctx->key = h;
     ctx->key_valid = true;
@@ -391,6 +405,113 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
     return TOMO_OK;
 }
 
+// (m, m') per voxel for the cube geometry and limb darkening, cached.
+tomo_status ensure_thomson(tomo_ctx *ctx, const tomo_cube_geom *c, double u,
+                           cudaStream_t s)
+{
+    uint64_t h = 1469598103934665603ull;
+    const int32_t cn[3] = { c->nx, c->ny, c->nz };
+    const double cv[7] = { c->x0, c->y0, c->z0, c->dx, c->dy, c->dz, u };
+    h = fnv1a(h, cn, sizeof(cn));
+    h = fnv1a(h, cv, sizeof(cv));
+    if (ctx->thf_valid && ctx->thf_key == h) return TOMO_OK;
+    ctx->thf_valid = false;
+    const int64_t n = (int64_t)c->nx * c->ny * c->nz;
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->thf, sizeof(float2) * n))) return st;
+    LAUNCH(ctx, TOMO_K_SETUP, s,
+           launch_thomson_factors(cube_dev(c), u, (float2 *)ctx->thf.p, s));
+    ctx->thf_key = h;
+    ctx->thf_valid = true;
+    return TOMO_OK;
+}
+
+// y = T x for the image kind: P (emission), O P M x (pB) or
+// P M' x - O P M x (B).  mm (map mask) is applied by the Thomson prologue
+// only; the emission path leaves it to the caller.
+tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
+                       int32_t n_frames, const uint8_t *mask,
+                       const uint8_t *mm, float *out, const tomo_cube_geom *c,
+                       const tomo_image_geom *g, Tiling t, const double *done,
+                       cudaStream_t s)
+{
+    if (g->kind == TOMO_KIND_EMISSION)
+        return forward_one(ctx, src, dtype, n_frames, mask, out, c, g, t,
+                           done, s);
+    const int64_t n = (int64_t)c->nx * c->ny * c->nz;
+    const int64_t npix = (int64_t)g->n_img * g->nu * g->nv;
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
+        (g->kind == TOMO_KIND_B &&
+         (st = ensure(ctx, ctx->thimg, sizeof(float) * (npix > 0 ? npix : 1)))))
+        return st;
+    const float2 *mf = (const float2 *)ctx->thf.p;
+    const float *rho2 = (const float *)ctx->rho2.p;
+    float *c1 = (float *)ctx->th1.p;
+    const bool bf16 = dtype == TOMO_BF16;
+    // pB: M x; B: first M' x, then M x (the scratch is reused in order)
+    LAUNCH(ctx, TOMO_K_VECTOR, s,
+           launch_thomson_weight(src, bf16, mf, g->kind == TOMO_KIND_B ? 1 : 0,
+                                 mm, n, n_frames, c1, done, s));
+    if ((st = forward_one(ctx, c1, TOMO_F32, n_frames, mask, out, c, g, t,
+                          done, s)))
+        return st;
+    if (g->kind == TOMO_KIND_PB) {
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_rho2_apply(rho2, out, nullptr, out, npix, done, s));
+        return TOMO_OK;
+    }
+    float *ti = (float *)ctx->thimg.p;
+    LAUNCH(ctx, TOMO_K_VECTOR, s,
+           launch_thomson_weight(src, bf16, mf, 0, mm, n, n_frames, c1, done, s));
+    if ((st = forward_one(ctx, c1, TOMO_F32, n_frames, mask, ti, c, g, t,
+                          done, s)))
+        return st;
+    LAUNCH(ctx, TOMO_K_VECTOR, s,
+           launch_rho2_apply(rho2, out, ti, out, npix, done, s));
+    return TOMO_OK;
+}
+
+// dst += T^T y: P^T y (emission), M P^T O y (pB) or M' P^T y - M P^T O y
+// (B); the Thomson epilogue applies the map mask mm.
+tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
+                       const uint8_t *mm, float *dst, const tomo_cube_geom *c,
+                       int32_t n_frames, const tomo_image_geom *g, Tiling t,
+                       const double *done, cudaStream_t s)
+{
+    if (g->kind == TOMO_KIND_EMISSION)
+        return adjoint_one(ctx, images, mask, dst, c, n_frames, g, t, done, s);
+    const int64_t n = (int64_t)c->nx * c->ny * c->nz;
+    const int64_t npix = (int64_t)g->n_img * g->nu * g->nv;
+    const bool b = g->kind == TOMO_KIND_B;
+    tomo_status st;
+    if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
+        (b && (st = ensure(ctx, ctx->th2, sizeof(float) * n * n_frames))) ||
+        (st = ensure(ctx, ctx->thimg, sizeof(float) * (npix > 0 ? npix : 1))))
+        return st;
+    const float2 *mf = (const float2 *)ctx->thf.p;
+    const float *rho2 = (const float *)ctx->rho2.p;
+    float *c1 = (float *)ctx->th1.p, *c2 = (float *)ctx->th2.p;
+    float *ti = (float *)ctx->thimg.p;
+    LAUNCH(ctx, TOMO_K_VECTOR, s,
+           launch_rho2_apply(rho2, images, nullptr, ti, npix, done, s));
+    CUDA_TRY(ctx, cudaMemsetAsync(c1, 0, sizeof(float) * n * n_frames, s));
+    if (!b) {
+        if ((st = adjoint_one(ctx, ti, mask, c1, c, n_frames, g, t, done, s)))
+            return st;
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_thomson_add(dst, c1, nullptr, mf, mm, n, n_frames, done, s));
+        return TOMO_OK;
+    }
+    CUDA_TRY(ctx, cudaMemsetAsync(c2, 0, sizeof(float) * n * n_frames, s));
+    if ((st = adjoint_one(ctx, images, mask, c1, c, n_frames, g, t, done, s)) ||
+        (st = adjoint_one(ctx, ti, mask, c2, c, n_frames, g, t, done, s)))
+        return st;
+    LAUNCH(ctx, TOMO_K_VECTOR, s,
+           launch_thomson_add(dst, c1, c2, mf, mm, n, n_frames, done, s));
+    return TOMO_OK;
+}
+
 int reduce_grid(const tomo_ctx *ctx, int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -461,7 +582,8 @@ void tomo_destroy(tomo_ctx *ctx)
                        &ctx->params, &ctx->rays, &ctx->b, &ctx->r, &ctx->p,
                        &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
                        &ctx->counter, &ctx->count64, &ctx->layout_used,
-                       &ctx->lay1, &ctx->lay2, &ctx->mcube };
+                       &ctx->lay1, &ctx->lay2, &ctx->mcube, &ctx->rho2,
+                       &ctx->thf, &ctx->th1, &ctx->th2, &ctx->thimg };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     free_plan(ctx);
@@ -576,6 +698,12 @@ tomo_status tomo_project(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
         (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
         return st;
+    if (img->kind != TOMO_KIND_EMISSION) {
+        // the Thomson prologue applies the map mask with M or M'
+        if ((st = ensure_thomson(ctx, cube, img->limb_u, s))) return st;
+        return op_forward(ctx, cube_dev, dtype, n_frames, mask_dev,
+                          map_mask_dev, images_dev, cube, img, tl, nullptr, s);
+    }
     if (map_mask_dev) {
         // P K x: the walks read a copy with the excluded voxels at 0
         const int64_t nvox = (int64_t)cube->nx * cube->ny * cube->nz;
@@ -621,6 +749,12 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
         (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)))
         return st;
+    if (img->kind != TOMO_KIND_EMISSION) {
+        // dst += K T^T y: the Thomson epilogue skips the excluded voxels
+        if ((st = ensure_thomson(ctx, cube, img->limb_u, s))) return st;
+        return op_adjoint(ctx, images_dev, mask_dev, map_mask_dev, cube_dev,
+                          cube, n_frames, img, tl, nullptr, s);
+    }
     if (map_mask_dev && (flags & TOMO_ACCUMULATE)) {
         // cube += K P^T y: transpose into scratch, add the kept voxels
         const size_t bytes = sizeof(float) * fstride * n_frames;
@@ -749,7 +883,9 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const Tiling tl = tiling_for(ctx, cube, img);
     if (img->n_img > 0 &&
         ((st = ensure_plane(ctx, cube, 1, tl)) ||
-         (st = prepare_rays(ctx, cube, 1, img, pointing_host, s))))
+         (st = prepare_rays(ctx, cube, 1, img, pointing_host, s)) ||
+         (img->kind != TOMO_KIND_EMISSION &&
+          (st = ensure_thomson(ctx, cube, img->limb_u, s)))))
         return st;
 
     float *b = (float *)ctx->b.p, *r = (float *)ctx->r.p;
@@ -780,7 +916,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     }
     CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
     if (m > 0 &&
-        (st = adjoint_one(ctx, y_dev, mask_dev, b, cube, 1, img, tl, nullptr, s)))
+        (st = op_adjoint(ctx, y_dev, mask_dev, nullptr, b, cube, 1, img, tl,
+                         nullptr, s)))
         return st;
     // with a map mask, b, r and p are restricted by the init and update
     // kernels, and x0 here, so every iterate has 0 on the excluded voxels
@@ -793,9 +930,10 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, prior_weight_dev, q, lam, false,
                                                   nullptr, s));
         if (m > 0 &&
-            ((st = forward_one(ctx, x_dev, TOMO_F32, 1, mask_dev, t, cube, img,
-                               tl, nullptr, s)) ||
-             (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, nullptr, s))))
+            ((st = op_forward(ctx, x_dev, TOMO_F32, 1, mask_dev, nullptr, t,
+                              cube, img, tl, nullptr, s)) ||
+             (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, 1, img, tl,
+                              nullptr, s))))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, mm, n, tol * tol,
                                      partials, counter, S, report, grid, s));
@@ -810,13 +948,14 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     for (int32_t k = 0; k < max_iter; ++k) {
         // q = (P^T M P + lambda D^T D) p
         if (m > 0 &&
-            (st = forward_one(ctx, p_gather, p_dtype, 1, mask_dev, t, cube, img,
-                              tl, done, s)))
+            (st = op_forward(ctx, p_gather, p_dtype, 1, mask_dev, nullptr, t,
+                             cube, img, tl, done, s)))
             return st;
         LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, prior_weight_dev, q, lam, false,
                                                   done, s));
         if (m > 0 &&
-            (st = adjoint_one(ctx, t, mask_dev, q, cube, 1, img, tl, done, s)))
+            (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, 1, img, tl,
+                             done, s)))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, mm, n, partials, counter,

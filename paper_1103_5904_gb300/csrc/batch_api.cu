@@ -112,6 +112,10 @@ tomo_status check_problem(tomo_ctx *ctx, const tomo_problem *p, int32_t i,
         return fail(ctx, st, "problem %d: %s", i, ctx->err);
     if (p->reserved != 0)
         return fail(ctx, TOMO_ERR_ARG, "problem %d: reserved must be 0", i);
+    if (p->img.kind != TOMO_KIND_EMISSION)
+        return fail(ctx, TOMO_ERR_UNSUPPORTED,
+                    "problem %d: the batched entry points take emission "
+                    "images only", i);
     if (need_cube && (!p->cube_dev || !aligned(p->cube_dev, 4)))
         return fail(ctx, TOMO_ERR_ARG, "problem %d: cube_dev NULL or misaligned", i);
     if (need_images && p->img.n_img > 0 &&

@@ -62,6 +62,12 @@ struct tomo_ctx {
     tomo::host::DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
     // map-masked cube copy (forward) / transpose scratch (accumulate)
     tomo::host::DevBuf mcube;
+    // Thomson operators: rho^2 per pixel (computed with the ray records),
+    // (m, m') per voxel (keyed by cube geometry and u), two cube and one
+    // image scratch buffers
+    tomo::host::DevBuf rho2, thf, th1, th2, thimg;
+    uint64_t thf_key = 0;
+    bool thf_valid = false;
     // tuned tile shapes per problem size, and the cached batch plan
     std::vector<tomo::host::Tuned> tuned;
     tomo::host::BatchPlan *plan = nullptr;
@@ -114,6 +120,17 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                         int32_t n_frames, const uint8_t *mask, float *out,
                         const tomo_cube_geom *c, const tomo_image_geom *g,
                         Tiling t, const double *done, cudaStream_t s);
+tomo_status ensure_thomson(tomo_ctx *ctx, const tomo_cube_geom *c, double u,
+                           cudaStream_t s);
+tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
+                       int32_t n_frames, const uint8_t *mask,
+                       const uint8_t *mm, float *out, const tomo_cube_geom *c,
+                       const tomo_image_geom *g, Tiling t, const double *done,
+                       cudaStream_t s);
+tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
+                       const uint8_t *mm, float *dst, const tomo_cube_geom *c,
+                       int32_t n_frames, const tomo_image_geom *g, Tiling t,
+                       const double *done, cudaStream_t s);
 tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                         const uint8_t *mask, float *cube,
                         const tomo_cube_geom *c, int32_t n_frames,

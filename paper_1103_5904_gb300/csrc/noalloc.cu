@@ -65,6 +65,7 @@ tomo_project_noalloc(const tomo_cube_geom *cube, int32_t n_frames,
         (st = check_pointing(nullptr, pointing_host, img, n_frames)))
         return st;
     if (dtype != TOMO_F32 && dtype != TOMO_BF16) return TOMO_ERR_ARG;
+    if (img->kind != TOMO_KIND_EMISSION) return TOMO_ERR_UNSUPPORTED;
     if (img->n_img == 0) return TOMO_OK;
     if (!cube_dev || !images_dev) return TOMO_ERR_ARG;
     if (!aligned(cube_dev, dtype == TOMO_F32 ? 4 : 2) || !aligned(images_dev, 4))

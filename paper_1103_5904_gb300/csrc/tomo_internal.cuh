@@ -228,6 +228,29 @@ cudaError_t launch_cg_direction(const float *r, float *p, uint16_t *p16,
                                 int64_t n, const double *S, int grid,
                                 cudaStream_t s);
 
+// ---- thomson.cu (T_pB = O P M, T_B = P M' - O P M; Section 3.5)
+// per-voxel (m, m') in FP64, stored as float2 [nz][ny][nx]
+cudaError_t launch_thomson_factors(CubeDev c, double limb_u, float2 *mf,
+                                   cudaStream_t s);
+// rho^2 = |o x u|^2 per pixel, [n_img][nv][nu]
+cudaError_t launch_impact2(const Frame *frames, const double *tan_u,
+                           const double *tan_v, int32_t n_img, int32_t nu,
+                           int32_t nv, float *rho2, cudaStream_t s);
+// dst = (which ? m' : m) K src over frames (src float32 or bf16 bits)
+cudaError_t launch_thomson_weight(const void *src, bool bf16, const float2 *mf,
+                                  int which, const uint8_t *mm, int64_t n,
+                                  int32_t frames, float *dst,
+                                  const double *done, cudaStream_t s);
+// dst += K (m a) (b == NULL) or K (m' a - m b)
+cudaError_t launch_thomson_add(float *dst, const float *a, const float *b,
+                               const float2 *mf, const uint8_t *mm, int64_t n,
+                               int32_t frames, const double *done,
+                               cudaStream_t s);
+// out = rho^2 y (t == NULL), or out = y - rho^2 t
+cudaError_t launch_rho2_apply(const float *rho2, const float *y, const float *t,
+                              float *out, int64_t n, const double *done,
+                              cudaStream_t s);
+
 // ---- mapmask.cu (map mask K = diag(1 - mask), same mask for every frame)
 // dst = K src over `frames` frames of n voxels (float32 or bf16 bits)
 cudaError_t launch_map_keep_copy(const void *src, void *dst, bool bf16,

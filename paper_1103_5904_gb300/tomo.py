@@ -44,7 +44,19 @@ class CubeGeom(C.Structure):
 
 
 class ImageGeom(C.Structure):
-    _fields_ = [("n_img", C.c_int32), ("nu", C.c_int32), ("nv", C.c_int32)]
+    _fields_ = [("n_img", C.c_int32), ("nu", C.c_int32), ("nv", C.c_int32),
+                ("kind", C.c_int32), ("limb_u", C.c_double)]
+
+
+# what the images measure (tomo_image_geom.kind): line-of-sight emission,
+# polarised brightness pB or total brightness B (Thomson scattering)
+KINDS = {"emission": 0, "pB": 1, "B": 2}
+
+
+def _kind(kind):
+    if kind not in KINDS:
+        raise ValueError("kind must be one of %s" % sorted(KINDS))
+    return KINDS[kind]
 
 
 class Pointing(C.Structure):
@@ -73,7 +85,8 @@ class TilingResult(C.Structure):
 
 
 assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
-assert C.sizeof(Problem) == 144
+assert C.sizeof(ImageGeom) == 24
+assert C.sizeof(Problem) == 160
 
 
 class TomoError(RuntimeError):
@@ -295,7 +308,8 @@ def _ctx(ctx):
 # ------------------------------------------------------------- entry points
 
 def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
-                 out=None, ctx=None, stream=None, map_mask=None):
+                 out=None, ctx=None, stream=None, map_mask=None,
+                 kind="emission", limb_u=0.0):
     """``y = P x``: images ``[n_img][nv][nu]`` float32 from a float32 or
     bfloat16 cube ``[T][nz][ny][nx]``; with ``map_mask`` the excluded voxels
     are read as 0."""
@@ -321,7 +335,8 @@ def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
         raise ValueError("out must have n_img * nv * nu elements")
     _check_mask(mask, n_img, nu, nv)
     _check_map_mask(map_mask, geom)
-    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, int(nu), int(nv))
+    cg = cube_geom_struct(geom)
+    ig = ImageGeom(n_img, int(nu), int(nv), _kind(kind), float(limb_u))
     ctx.check(load_library().tomo_project(
         ctx.handle, C.byref(cg), int(n_frames), _ptr(cube), dtype,
         C.byref(ig), _ptg_ptr(ptg), _ptr(mask), _ptr(map_mask), _ptr(out),
@@ -330,7 +345,8 @@ def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
 
 
 def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
-                     accumulate=False, ctx=None, stream=None, map_mask=None):
+                     accumulate=False, ctx=None, stream=None, map_mask=None,
+                     kind="emission", limb_u=0.0):
     """``x = P^T y``: float32 cube ``[T][nz][ny][nx]`` from float32 images
     ``[n_img][nv][nu]``; with ``map_mask`` the excluded voxels receive 0."""
     ctx = _ctx(ctx)
@@ -350,7 +366,8 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
         raise ValueError("out has the wrong size")
     _check_mask(mask, n_img, nu, nv)
     _check_map_mask(map_mask, geom)
-    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
+    cg = cube_geom_struct(geom)
+    ig = ImageGeom(n_img, nu, nv, _kind(kind), float(limb_u))
     ctx.check(load_library().tomo_backproject(
         ctx.handle, C.byref(cg), int(n_frames), C.byref(ig), _ptg_ptr(ptg),
         _ptr(mask), _ptr(map_mask), _ptr(images), _ptr(out),
@@ -361,7 +378,8 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
 
 def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
                x0=None, bf16=False, out=None, report=True, ctx=None,
-               stream=None, map_mask=None, prior_weight=None):
+               stream=None, map_mask=None, prior_weight=None,
+               kind="emission", limb_u=0.0):
     """CG on ``(P^T M P + lam R D^T D R) x = P^T M y`` (R = diag of
     ``prior_weight``, else the identity; restricted to the voxels that
     ``map_mask`` keeps).  Returns ``(x, info)`` with
@@ -387,7 +405,8 @@ def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
     _check_mask(mask, n_img, nu, nv)
     _check_map_mask(map_mask, geom)
     _check_weight(prior_weight, geom)
-    cg, ig = cube_geom_struct(geom), ImageGeom(n_img, nu, nv)
+    cg = cube_geom_struct(geom)
+    ig = ImageGeom(n_img, nu, nv, _kind(kind), float(limb_u))
     rep = np.full(2 * (int(max_iter) + 1), np.nan) if report else None
     iters = C.c_int32(0)
     ctx.check(load_library().tomo_solve(
@@ -469,7 +488,8 @@ def _problems(problems, need_cube=True, need_images=True):
             raise ValueError("problem %d: images must have n_img*nv*nu elements"
                              % i)
         arr[i].cube = cube_geom_struct(p["geom"])
-        arr[i].img = ImageGeom(n_img, nu, nv)
+        arr[i].img = ImageGeom(n_img, nu, nv, _kind(p.get("kind", "emission")),
+                               float(p.get("limb_u", 0.0)))
         arr[i].reserved = 0
         arr[i].pointing_host = _ptg_ptr(ptg)
         arr[i].mask_dev = None if mask is None else mask.data_ptr()
