@@ -47,11 +47,17 @@ def _scene(seed=0, n_frames=1):
     return g, ptg, mask, rng
 
 
-def _transpose_bound(got, want, absw):
-    """Float32 bound for a sum of products: 1e-5 relative plus 64 ulp of the
-    sum of absolute terms (``absw``, the oracle's T^T of |y| with |factors|)."""
+def _transpose_bound(got, want, absw, cw, geom):
+    """Float32 bound of the transpose: 1e-5 relative, 64 ulp of the sum of
+    absolute terms (``absw``), and, as for the plain transpose, 8 ulp of the
+    longest chord per crossing ray (``cw``: the crossing weights of the
+    weighted images times the voxel factor), since a segment's length is a
+    difference of float crossing parameters and carries an absolute error."""
+    t_max = float(np.sqrt(sum((geom["n" + a] * geom["d" + a]) ** 2
+                              for a in "xyz")))
     err = np.abs(np.asarray(got, np.float64) - want)
-    bound = 1e-5 * np.abs(want) + 64 * 2.0 ** -24 * absw + 1e-30
+    bound = (1e-5 * np.abs(want) + 64 * 2.0 ** -24 * absw +
+             8 * 2.0 ** -24 * t_max * cw + 1e-30)
     assert np.all(err <= bound), float((err / bound).max())
 
 
@@ -87,10 +93,14 @@ def test_operators_against_oracle(T, kind, n_frames):
             m, mp = thomson.voxel_factors(g, u)
             o = siddon.impact2(ptg, 37, 41)
             absw = m * siddon.backproject(g, o * y, ptg, 37, 41, mask, n_frames)
+            cw = m * siddon.crossing_weights(g, o * y, ptg, 37, 41, mask,
+                                             n_frames)
             if k == thomson.B:
                 absw = absw + mp * siddon.backproject(g, y, ptg, 37, 41, mask,
                                                       n_frames)
-            _transpose_bound(got_t.cpu().numpy(), want_t, absw)
+                cw = cw + mp * siddon.crossing_weights(g, y, ptg, 37, 41, mask,
+                                                       n_frames)
+            _transpose_bound(got_t.cpu().numpy(), want_t, absw, cw, g)
             ctx.close()
 
 
