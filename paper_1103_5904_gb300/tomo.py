@@ -312,7 +312,10 @@ def tomo_project(cube, geom, pointing, nu, nv, mask=None, n_frames=1,
                  kind="emission", limb_u=0.0):
     """``y = P x``: images ``[n_img][nv][nu]`` float32 from a float32 or
     bfloat16 cube ``[T][nz][ny][nx]``; with ``map_mask`` the excluded voxels
-    are read as 0."""
+    are read as 0.  ``kind`` "pB" or "B" (white-light images, limb
+    darkening ``limb_u``) applies the Thomson operator O P M or
+    P M' - O P M instead of P; the transpose and the solver take the same
+    keywords."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
     n_img = ptg.shape[0]
