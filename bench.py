@@ -701,6 +701,18 @@ def run_sweep(args, local_rank):
                     out=x, report=False, map_mask=mm, ctx=ctx), 3)
                 line["solar_cg_s_per_iter"] = cg_o / 1e3 / cg_iters
                 del x
+            # white-light images (Thomson pB and B operators, limb
+            # darkening 0.6) on the same geometry
+            for kind in ("pB", "B"):
+                yk = T.tomo_project(X, go, ptg, nu, nv, mask=mask, kind=kind,
+                                    limb_u=0.6, ctx=ctx)
+                line[kind + "_P_ms"] = med_ms(lambda: T.tomo_project(
+                    X, go, ptg, nu, nv, mask=mask, kind=kind, limb_u=0.6,
+                    out=yk, ctx=ctx), reps)
+                line[kind + "_PT_ms"] = med_ms(lambda: T.tomo_backproject(
+                    yk, go, ptg, mask=mask, kind=kind, limb_u=0.6, out=out,
+                    ctx=ctx), reps)
+                del yk
             del yo, mm
         # the oracle on one core and on all host cores (seeded ray sample)
         c_host = dict(c)
