@@ -18,8 +18,9 @@ from . import tomo
 class TomoProject(torch.autograd.Function):
     @staticmethod
     def forward(fctx, cube, geom, pointing, nu, nv, mask=None, n_frames=1,
-                ctx=None, map_mask=None):
+                ctx=None, map_mask=None, kind="emission", limb_u=0.0):
         fctx.geom, fctx.pointing = geom, pointing
+        fctx.kind, fctx.limb_u = kind, limb_u
         fctx.n_frames, fctx.tctx = n_frames, ctx
         fctx.cube_shape, fctx.cube_dtype = cube.shape, cube.dtype
         empty = cube.new_empty(0)
@@ -29,7 +30,7 @@ class TomoProject(torch.autograd.Function):
         fctx.has_map_mask = map_mask is not None
         return tomo.tomo_project(cube.contiguous(), geom, pointing, nu, nv,
                                  mask=mask, n_frames=n_frames, ctx=ctx,
-                                 map_mask=map_mask)
+                                 map_mask=map_mask, kind=kind, limb_u=limb_u)
 
     @staticmethod
     def backward(fctx, grad_y):
@@ -40,13 +41,16 @@ class TomoProject(torch.autograd.Function):
                 grad_y.contiguous().float(), fctx.geom, fctx.pointing,
                 mask=mask if fctx.has_mask else None,
                 n_frames=fctx.n_frames, ctx=fctx.tctx,
-                map_mask=map_mask if fctx.has_map_mask else None)
+                map_mask=map_mask if fctx.has_map_mask else None,
+                kind=fctx.kind, limb_u=fctx.limb_u)
             grad = g.reshape(fctx.cube_shape).to(fctx.cube_dtype)
-        return grad, None, None, None, None, None, None, None, None
+        return (grad, None, None, None, None, None, None, None, None, None,
+                None)
 
 
 def project(cube, geom, pointing, nu, nv, mask=None, n_frames=1, ctx=None,
-            map_mask=None):
-    """Differentiable ``P x`` (``P K x`` with a map mask)."""
+            map_mask=None, kind="emission", limb_u=0.0):
+    """Differentiable ``P x`` (``P K x`` with a map mask; the Thomson
+    operator of white-light images with ``kind`` "pB" or "B")."""
     return TomoProject.apply(cube, geom, pointing, nu, nv, mask, n_frames, ctx,
-                             map_mask)
+                             map_mask, kind, limb_u)

@@ -138,3 +138,25 @@ def test_rejected_kinds(T):
                                  "nv": 41, "cube": X, "kind": "pB",
                                  "images": torch.zeros((5, 41, 37),
                                                        device="cuda")}])
+
+
+def test_autograd_pb(T):
+    """The gradient of <w, T_pB x> through the autograd Function is
+    T_pB^T w."""
+    from paper_1103_5904_gb300 import autograd
+    g, ptg, mask, rng = _scene(4)
+    u = 0.5
+    X = to_dev(rng.random((27, 31, 29)).astype(np.float32)).requires_grad_(True)
+    w = rng.random((5, 41, 37)).astype(np.float32)
+    y = autograd.project(X, g, ptg, 37, 41, mask=mask_dev(mask), kind="pB",
+                         limb_u=u)
+    assert torch.equal(y.detach(), T.tomo_project(X.detach(), g, ptg, 37, 41,
+                                                  mask=mask_dev(mask),
+                                                  kind="pB", limb_u=u))
+    (y * to_dev(w)).sum().backward()
+    want = thomson.backproject(thomson.PB, g, w, ptg, 37, 41, u, mask)
+    m, _ = thomson.voxel_factors(g, u)
+    o = siddon.impact2(ptg, 37, 41)
+    _transpose_bound(X.grad.cpu().numpy(), want,
+                     m * siddon.backproject(g, o * w, ptg, 37, 41, mask),
+                     m * siddon.crossing_weights(g, o * w, ptg, 37, 41, mask), g)
