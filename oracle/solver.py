@@ -20,6 +20,14 @@ smoothing grows with altitude.  The oracle takes the diagonal as given
 the altitude above the photosphere, is the caller's choice); the normal
 operator's prior term is lambda R D^T D R.
 
+Several frames (Section 3.3.3 and the block-diagonal smooth temporal model
+of Eq. srt_t / stsrt): with ``n_frames`` T > 1 the map is [T][nz][ny][nx],
+each image sees its frames through its time stamp (the projector's time
+weights; integer stamps make P block-diagonal, one frame per image group),
+the spatial prior applies to every frame and a temporal prior
+lambda_t ||D_t x||^2, D_t the forward difference x[t+1] - x[t] between
+consecutive frames (no wrap), is added.
+
 White-light data (Section 3.5): with ``kind`` PB or B the projector P is
 replaced by the Thomson operator T_pB or T_B of ``thomson.py`` (limb
 darkening ``limb_u``) in every formula here.
@@ -71,6 +79,27 @@ def DtD(x):
     return Dt(*D(x))
 
 
+def DtD_frames(x):
+    """D^T D applied to every frame of a map (3-D: the map itself)."""
+    x = np.asarray(x, dtype=np.float64)
+    return DtD(x) if x.ndim == 3 else np.stack([DtD(f) for f in x])
+
+
+def Dt_time(x):
+    """Temporal forward differences x[t+1] - x[t] of a [T][nz][ny][nx] map."""
+    return np.diff(np.asarray(x, dtype=np.float64), axis=0)
+
+
+def DtD_time(x):
+    """D_t^T D_t x: the adjoint of one forward difference along t applied to
+    D_t x (-g[t] + g[t-1], zero-padded at the ends)."""
+    g = Dt_time(x)
+    out = np.zeros(np.shape(x))
+    out[:-1] -= g
+    out[1:] += g
+    return out
+
+
 def prior_energy(x):
     """||D x||^2."""
     return float(sum(np.sum(g * g) for g in D(x)))
@@ -80,18 +109,21 @@ class Problem:
     """One static reconstruction: cube geometry, pointing, mask, data, lambda."""
 
     def __init__(self, geom, pointing, nu, nv, y, mask=None, lam=0.0,
-                 map_mask=None, prior_weight=None, kind=0, limb_u=0.0):
+                 map_mask=None, prior_weight=None, kind=0, limb_u=0.0,
+                 n_frames=1, lam_t=0.0):
         self.geom, self.pointing = geom, np.asarray(pointing, np.float64)
         self.nu, self.nv = int(nu), int(nv)
         self.mask = mask
         self.y = np.asarray(y, dtype=np.float64)
         self.lam = float(lam)
-        self.shape = (geom["nz"], geom["ny"], geom["nx"])
+        self.T, self.lam_t = int(n_frames), float(lam_t)
+        space = (geom["nz"], geom["ny"], geom["nx"])
+        self.shape = ((self.T,) if self.T > 1 else ()) + space
         self.keep = (None if map_mask is None else
                      (np.asarray(map_mask) == 0).astype(np.float64))
         self.kind, self.limb_u = int(kind), float(limb_u)
         self.w = (None if prior_weight is None else
-                  np.asarray(prior_weight, dtype=np.float64).reshape(self.shape))
+                  np.asarray(prior_weight, dtype=np.float64).reshape(space))
 
     def K(self, x):
         """The map mask: excluded voxels set to 0."""
@@ -105,17 +137,17 @@ class Problem:
         if self.kind:
             return thomson.project(self.kind, self.geom, self.K(x),
                                    self.pointing, self.nu, self.nv,
-                                   self.limb_u, self.mask)
+                                   self.limb_u, self.mask, self.T)
         return siddon.project(self.geom, self.K(x), self.pointing, self.nu,
-                              self.nv, self.mask)
+                              self.nv, self.mask, self.T)
 
     def Pt(self, y):
         if self.kind:
             return self.K(thomson.backproject(self.kind, self.geom, y,
                                               self.pointing, self.nu, self.nv,
-                                              self.limb_u, self.mask))
+                                              self.limb_u, self.mask, self.T))
         return self.K(siddon.backproject(self.geom, y, self.pointing, self.nu,
-                                         self.nv, self.mask))
+                                         self.nv, self.mask, self.T))
 
     def masked(self, y):
         if self.mask is None:
@@ -127,16 +159,25 @@ class Problem:
         return self.Pt(self.masked(self.y))
 
     def normal(self, v):
-        """K (P^T M P + lambda R D^T D R) K v (K, R = identity without map
-        mask or prior weight)."""
-        return self.Pt(self.P(v)) + self.lam * self.K(
-            self.R(DtD(self.R(self.K(v)))))
+        """K (P^T M P + lambda R D^T D R + lambda_t D_t^T D_t) K v (K, R =
+        identity without map mask or prior weight; D^T D per frame)."""
+        out = self.Pt(self.P(v)) + self.lam * self.K(
+            self.R(DtD_frames(self.R(self.K(v)))))
+        if self.T > 1 and self.lam_t != 0.0:
+            out = out + self.lam_t * self.K(DtD_time(self.K(v)))
+        return out
 
     def J(self, x):
-        """Eq. criterion: ||M (y - P K x)||^2 + lambda ||D R K x||^2."""
+        """Eq. criterion: ||M (y - P K x)||^2 + lambda ||D R K x||^2
+        (+ lambda_t ||D_t K x||^2 with frames)."""
         r = self.masked(self.y - self.P(x))
-        return float(np.sum(r * r)) + self.lam * prior_energy(
-            self.R(self.K(x)))
+        kx = self.K(x)
+        spatial = (prior_energy(self.R(kx)) if self.T == 1 else
+                   sum(prior_energy(self.R(f)) for f in kx))
+        j = float(np.sum(r * r)) + self.lam * spatial
+        if self.T > 1:
+            j += self.lam_t * float(np.sum(Dt_time(kx) ** 2))
+        return j
 
 
 def cg(problem, n_iter, x0=None, track_J=True):

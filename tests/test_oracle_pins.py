@@ -804,3 +804,65 @@ def test_thomson_operators_adjoint_and_rows(T):
                 float(np.sum(row * (mp * x).reshape(-1))) - rho2 * pm
             want = 0.0 if mask[n, iv, iu] else want
             assert Tx[n, iv, iu] == pytest.approx(want, rel=1e-10, abs=1e-16)
+
+
+# ----------------------------------------------- frames and temporal prior
+
+def _temporal_problem(times, lam_t, seed=21):
+    g = synth.cube_geom(5, 1.5, ny=4, nz=4)
+    rng = np.random.default_rng(seed)
+    n = len(times)
+    ptg = synth.pointing_table(rng.uniform(0, 360, n), rng.uniform(-30, 30, n),
+                               215.0, 8, 8, 3.4, time=np.asarray(times))
+    mask = (rng.random((n, 8, 8)) < 0.15).astype(np.uint8)
+    y = rng.random((n, 8, 8))
+    return g, ptg, mask, y, solver.Problem(g, ptg, 8, 8, y, mask, lam=0.3,
+                                           n_frames=2, lam_t=lam_t)
+
+
+def test_temporal_prior_solves_the_dense_system():
+    """Two frames, fractional time stamps, spatial and temporal priors: CG
+    reaches the direct solve built from dense rows ((1 - w) and w times the
+    brute-force row in the two frames' blocks), block-diagonal spatial
+    differences and frame-to-frame differences from index arithmetic."""
+    rng = np.random.default_rng(5)
+    times = rng.uniform(0, 1, 6)
+    g, ptg, mask, y, pb = _temporal_problem(times, lam_t=0.7)
+    nv_ = 80
+    A = np.zeros((6 * 64, 2 * nv_))
+    for r in range(6 * 64):
+        n, iv, iu = r // 64, (r // 8) % 8, r % 8
+        if mask.reshape(-1)[r]:
+            continue
+        o, u = siddon.ray(ptg[n], iu, iv)
+        row = checks.brute_force_ray(g, o, u) * ptg[n, 10]
+        w = times[n]
+        A[r, :nv_] = (1 - w) * row
+        A[r, nv_:] = w * row
+    _, B1 = _dense_AB(_dense_problem())
+    B = np.block([[B1, np.zeros_like(B1)], [np.zeros_like(B1), B1]])
+    Dt = np.hstack([-np.eye(nv_), np.eye(nv_)])
+    ym = np.where(mask == 0, y, 0.0).reshape(-1)
+    H = A.T @ A + 0.3 * B.T @ B + 0.7 * Dt.T @ Dt
+    x_direct = np.linalg.solve(H, A.T @ ym)
+    x_cg, rep = solver.cg(pb, 600)
+    np.testing.assert_allclose(x_cg.reshape(-1), x_direct, rtol=0,
+                               atol=1e-8 * np.abs(x_direct).max())
+    Jmin = float(np.sum((ym - A @ x_direct) ** 2) + 0.3 * np.sum(
+        (B @ x_direct) ** 2) + 0.7 * np.sum((Dt @ x_direct) ** 2))
+    assert rep["J"][-1] == pytest.approx(Jmin, rel=1e-9)
+
+
+def test_integer_stamps_without_temporal_prior_decouple():
+    """Integer time stamps and lambda_t = 0: the model is block-diagonal, and
+    each frame's solution is the static solution of the images taken at its
+    time."""
+    times = np.array([0, 1, 0, 1, 1, 0], dtype=np.float64)
+    g, ptg, mask, y, pb = _temporal_problem(times, lam_t=0.0)
+    x, _ = solver.cg(pb, 400)
+    for t in (0, 1):
+        sel = times == t
+        ps = solver.Problem(g, ptg[sel], 8, 8, y[sel], mask[sel], lam=0.3)
+        xs, _ = solver.cg(ps, 400)
+        np.testing.assert_allclose(x[t], xs, rtol=0,
+                                   atol=1e-8 * np.abs(xs).max())
