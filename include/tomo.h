@@ -281,14 +281,21 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
  *   iters_host:  nullable; receives the number of iterations done
  * No host synchronisation happens inside the loop.  If report_host or
  * iters_host is given, the call synchronises `stream` before returning. */
+/* Several frames (n_frames = T > 1; the smooth temporal model of Section
+ * 3.3.3, block-diagonal for integer time stamps as in Eq. srt_t / stsrt):
+ * x_dev is [T][nz][ny][nx], each image sees its frames through its time
+ * stamp, the spatial prior applies to every frame, and lambda_t >= 0 adds
+ * lambda_t ||D_t x||^2 with D_t the difference x[t+1] - x[t] of consecutive
+ * frames (normal operator + lambda_t D_t^T D_t).  A map mask with T > 1
+ * returns TOMO_ERR_UNSUPPORTED. */
 tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
-                       const tomo_image_geom *img,
+                       int32_t n_frames, const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
                        const uint8_t *mask_dev, const uint8_t *map_mask_dev,
                        const float *prior_weight_dev, const float *y_dev,
-                       float *x_dev, double lambda, int32_t max_iter,
-                       double tol, uint32_t flags, double *report_host,
-                       int32_t *iters_host, void *stream);
+                       float *x_dev, double lambda, double lambda_t,
+                       int32_t max_iter, double tol, uint32_t flags,
+                       double *report_host, int32_t *iters_host, void *stream);
 
 /* q = lambda D^T D x (+ q if flags has TOMO_ACCUMULATE), the gradient of the
  * prior term lambda ||D x||^2 / 2 (Section 3.3.1); with prior_weight_dev

@@ -512,6 +512,23 @@ tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
     return TOMO_OK;
 }
 
+// q = lambda R D^T D R x per frame (+ lambda_t D_t^T D_t x over frames).
+tomo_status apply_prior(tomo_ctx *ctx, const tomo_cube_geom *c, const float *x,
+                        const float *w, float *q, float lam, float lam_t,
+                        int32_t n_frames, const double *done, cudaStream_t s)
+{
+    const int64_t nvox = (int64_t)c->nx * c->ny * c->nz;
+    const CubeDev cd = cube_dev(c);
+    for (int32_t f = 0; f < n_frames; ++f)
+        LAUNCH(ctx, TOMO_K_PRIOR, s,
+               launch_prior(cd, x + f * nvox, w, q + f * nvox, lam, false,
+                            done, s));
+    if (n_frames > 1 && lam_t != 0.0f)
+        LAUNCH(ctx, TOMO_K_PRIOR, s,
+               launch_prior_time(x, q, lam_t, nvox, n_frames, done, s));
+    return TOMO_OK;
+}
+
 int reduce_grid(const tomo_ctx *ctx, int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -836,18 +853,23 @@ tomo_status tomo_count_segments(tomo_ctx *ctx, const tomo_cube_geom *cube,
 }
 
 tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
-                       const tomo_image_geom *img,
+                       int32_t n_frames, const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,
                        const uint8_t *mask_dev, const uint8_t *map_mask_dev,
                        const float *prior_weight_dev, const float *y_dev,
-                       float *x_dev, double lambda, int32_t max_iter,
-                       double tol, uint32_t flags, double *report_host,
-                       int32_t *iters_host, void *stream)
+                       float *x_dev, double lambda, double lambda_t,
+                       int32_t max_iter, double tol, uint32_t flags,
+                       double *report_host, int32_t *iters_host, void *stream)
 {
     if (!ctx) return TOMO_ERR_ARG;
     ctx->err[0] = 0;
-    tomo_status st = common_checks(ctx, cube, 1, img, pointing_host);
+    tomo_status st = common_checks(ctx, cube, n_frames, img, pointing_host);
     if (st) return st;
+    if (!isfinite(lambda_t) || lambda_t < 0)
+        return fail(ctx, TOMO_ERR_ARG, "lambda_t must be finite and >= 0");
+    if (n_frames > 1 && map_mask_dev)
+        return fail(ctx, TOMO_ERR_UNSUPPORTED,
+                    "a map mask with several frames is not supported");
     if (flags & ~(TOMO_SOLVE_X0 | TOMO_SOLVE_BF16))
         return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
     if (!isfinite(lambda) || lambda < 0)
@@ -866,7 +888,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
     cudaStream_t s = (cudaStream_t)stream;
 
-    const int64_t n = (int64_t)cube->nx * cube->ny * cube->nz;
+    // all frames' voxels are one CG vector
+    const int64_t n = (int64_t)cube->nx * cube->ny * cube->nz * n_frames;
     const int64_t m = (int64_t)img->n_img * img->nu * img->nv;
     const bool bf16 = (flags & TOMO_SOLVE_BF16) != 0;
     const size_t n_report = 2 * ((size_t)max_iter + 1);
@@ -882,8 +905,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         return st;
     const Tiling tl = tiling_for(ctx, cube, img);
     if (img->n_img > 0 &&
-        ((st = ensure_plane(ctx, cube, 1, tl)) ||
-         (st = prepare_rays(ctx, cube, 1, img, pointing_host, s)) ||
+        ((st = ensure_plane(ctx, cube, n_frames, tl)) ||
+         (st = prepare_rays(ctx, cube, n_frames, img, pointing_host, s)) ||
          (img->kind != TOMO_KIND_EMISSION &&
           (st = ensure_thomson(ctx, cube, img->limb_u, s)))))
         return st;
@@ -903,7 +926,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     const tomo_pointing *ptgd = (const tomo_pointing *)ctx->ptg.p;
     const CubeDev cd = cube_dev(cube);
     const int nxny = cube->nx * cube->ny;
-    const float lam = (float)lambda;
+    const float lam = (float)lambda, lam_t = (float)lambda_t;
     const int grid = reduce_grid(ctx, n > m ? n : m);
 
     CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
@@ -916,8 +939,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     }
     CUDA_TRY(ctx, cudaMemsetAsync(b, 0, sizeof(float) * n, s));
     if (m > 0 &&
-        (st = op_adjoint(ctx, y_dev, mask_dev, nullptr, b, cube, 1, img, tl,
-                         nullptr, s)))
+        (st = op_adjoint(ctx, y_dev, mask_dev, nullptr, b, cube, n_frames, img,
+                         tl, nullptr, s)))
         return st;
     // with a map mask, b, r and p are restricted by the init and update
     // kernels, and x0 here, so every iterate has 0 on the excluded voxels
@@ -927,13 +950,14 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
         // r0 = b - (P^T M P + lambda D^T D) x0
         if (mm)
             LAUNCH(ctx, TOMO_K_VECTOR, s, launch_map_zero(x_dev, mm, n, 1, s));
-        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, x_dev, prior_weight_dev, q, lam, false,
-                                                  nullptr, s));
+        if ((st = apply_prior(ctx, cube, x_dev, prior_weight_dev, q, lam, lam_t,
+                              n_frames, nullptr, s)))
+            return st;
         if (m > 0 &&
-            ((st = op_forward(ctx, x_dev, TOMO_F32, 1, mask_dev, nullptr, t,
-                              cube, img, tl, nullptr, s)) ||
-             (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, 1, img, tl,
-                              nullptr, s))))
+            ((st = op_forward(ctx, x_dev, TOMO_F32, n_frames, mask_dev, nullptr,
+                              t, cube, img, tl, nullptr, s)) ||
+             (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, n_frames, img,
+                              tl, nullptr, s))))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, mm, n, tol * tol,
                                      partials, counter, S, report, grid, s));
@@ -948,14 +972,15 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     for (int32_t k = 0; k < max_iter; ++k) {
         // q = (P^T M P + lambda D^T D) p
         if (m > 0 &&
-            (st = op_forward(ctx, p_gather, p_dtype, 1, mask_dev, nullptr, t,
-                             cube, img, tl, done, s)))
+            (st = op_forward(ctx, p_gather, p_dtype, n_frames, mask_dev, nullptr,
+                             t, cube, img, tl, done, s)))
             return st;
-        LAUNCH(ctx, TOMO_K_PRIOR, s, launch_prior(cd, p, prior_weight_dev, q, lam, false,
-                                                  done, s));
+        if ((st = apply_prior(ctx, cube, p, prior_weight_dev, q, lam, lam_t,
+                              n_frames, done, s)))
+            return st;
         if (m > 0 &&
-            (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, 1, img, tl,
-                             done, s)))
+            (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, n_frames, img,
+                             tl, done, s)))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, mm, n, partials, counter,

@@ -84,6 +84,27 @@ __global__ void k_prior(int nx, int ny, int nz, const float *__restrict__ x,
     q[v] = accumulate ? q[v] + val : val;
 }
 
+// q += lambda_t D_t^T D_t x over T frames of n voxels (temporal prior of the
+// block-diagonal smooth temporal model): frame t gets
+// (x[t] - x[t-1]) for t > 0 plus (x[t] - x[t+1]) for t < T - 1.
+__global__ void k_prior_time(const float *__restrict__ x, float *__restrict__ q,
+                             float lam_t, int64_t n, int32_t T,
+                             const double *__restrict__ done)
+{
+    if (done != nullptr && *done != 0.0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int32_t t = 0; t < T; ++t) {
+            const int64_t j = (int64_t)t * n + i;
+            const float xc = x[j];
+            float s = 0.0f;
+            if (t > 0) s += xc - x[j - n];
+            if (t < T - 1) s += xc - x[j + n];
+            q[j] += lam_t * s;
+        }
+    }
+}
+
 __global__ void k_fill_f32(float *p, float v, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -214,6 +235,15 @@ cudaError_t launch_prior(CubeDev c, const float *x, const float *w, float *q,
                     (unsigned)c.nz);
     k_prior<<<grid, block, 0, s>>>(c.nx, c.ny, c.nz, x, w, q, lam, accumulate,
                                    done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prior_time(const float *x, float *q, float lam_t,
+                              int64_t n, int32_t T, const double *done,
+                              cudaStream_t s)
+{
+    if (n <= 0 || T <= 1) return cudaSuccess;
+    k_prior_time<<<fill_grid(n), kThreads, 0, s>>>(x, q, lam_t, n, T, done);
     return cudaGetLastError();
 }
 

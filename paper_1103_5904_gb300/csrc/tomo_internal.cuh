@@ -196,6 +196,10 @@ cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
 cudaError_t launch_prior(CubeDev cube, const float *x, const float *w,
                          float *q, float lam, bool accumulate,
                          const double *done, cudaStream_t s);
+// q += lambda_t D_t^T D_t x over T frames of n voxels
+cudaError_t launch_prior_time(const float *x, float *q, float lam_t,
+                              int64_t n, int32_t T, const double *done,
+                              cudaStream_t s);
 cudaError_t launch_fill_f32(float *p, float v, int64_t n, cudaStream_t s);
 cudaError_t launch_fill_f64(double *p, double v, int64_t n, cudaStream_t s);
 // S[S_YMY] = sum over unmasked pixels of y^2

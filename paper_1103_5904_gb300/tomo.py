@@ -115,9 +115,10 @@ _SIGNATURES = {
     "tomo_backproject": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32,
                                    C.POINTER(ImageGeom), C.POINTER(Pointing),
                                    _VP, _VP, _VP, _VP, C.c_uint32, _VP]),
-    "tomo_solve": (C.c_int, [_VP, C.POINTER(CubeGeom), C.POINTER(ImageGeom),
+    "tomo_solve": (C.c_int, [_VP, C.POINTER(CubeGeom), C.c_int32,
+                             C.POINTER(ImageGeom),
                              C.POINTER(Pointing), _VP, _VP, _VP, _VP, _VP,
-                             C.c_double,
+                             C.c_double, C.c_double,
                              C.c_int32, C.c_double, C.c_uint32,
                              C.POINTER(C.c_double), C.POINTER(C.c_int32),
                              _VP]),
@@ -382,16 +383,21 @@ def tomo_backproject(images, geom, pointing, mask=None, n_frames=1, out=None,
 def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
                x0=None, bf16=False, out=None, report=True, ctx=None,
                stream=None, map_mask=None, prior_weight=None,
-               kind="emission", limb_u=0.0):
+               kind="emission", limb_u=0.0, n_frames=1, lam_t=0.0):
     """CG on ``(P^T M P + lam R D^T D R) x = P^T M y`` (R = diag of
     ``prior_weight``, else the identity; restricted to the voxels that
-    ``map_mask`` keeps).  Returns ``(x, info)`` with
-    ``info = {"J": ..., "rr": ..., "iters": ...}`` when ``report``."""
+    ``map_mask`` keeps).  With ``n_frames`` T > 1 the map is
+    ``[T][nz][ny][nx]`` (images reach frames through their time stamps) and
+    ``lam_t`` weighs the temporal prior ``||D_t x||^2``.  Returns
+    ``(x, info)`` with ``info = {"J": ..., "rr": ..., "iters": ...}`` when
+    ``report``."""
     ctx = _ctx(ctx)
     ptg = pointing_array(pointing)
     _dev(y, torch.float32, "y")
     n_img, nv, nu = y.shape
     shape = (int(geom["nz"]), int(geom["ny"]), int(geom["nx"]))
+    if int(n_frames) > 1:
+        shape = (int(n_frames),) + shape
     flags = 0
     if n_img != ptg.shape[0]:
         raise ValueError("one pointing record per image")
@@ -413,8 +419,9 @@ def tomo_solve(y, geom, pointing, mask=None, lam=0.0, max_iter=10, tol=0.0,
     rep = np.full(2 * (int(max_iter) + 1), np.nan) if report else None
     iters = C.c_int32(0)
     ctx.check(load_library().tomo_solve(
-        ctx.handle, C.byref(cg), C.byref(ig), _ptg_ptr(ptg), _ptr(mask),
-        _ptr(map_mask), _ptr(prior_weight), _ptr(y), _ptr(out), float(lam), int(max_iter), float(tol), flags,
+        ctx.handle, C.byref(cg), int(n_frames), C.byref(ig), _ptg_ptr(ptg),
+        _ptr(mask), _ptr(map_mask), _ptr(prior_weight), _ptr(y), _ptr(out),
+        float(lam), float(lam_t), int(max_iter), float(tol), flags,
         rep.ctypes.data_as(C.POINTER(C.c_double)) if report else None,
         C.byref(iters) if report else None, _stream_ptr(stream, y.device)))
     info = None

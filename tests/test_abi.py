@@ -45,9 +45,9 @@ def test_status_strings_and_null_context(lib):
                             None, None) == -1
     assert lib.tomo_backproject(None, None, 1, None, None, None, None, None,
                                 None, 0, None) == -1
-    assert lib.tomo_solve(None, None, None, None, None, None, None, None,
-                          None, C.c_double(0), 0, C.c_double(0), 0, None, None,
-                          None) == -1
+    assert lib.tomo_solve(None, None, 1, None, None, None, None, None, None,
+                          None, C.c_double(0), C.c_double(0), 0, C.c_double(0),
+                          0, None, None, None) == -1
     h = C.c_void_p()
     assert lib.tomo_create(C.byref(h), -1) == -1  # invalid device
 
