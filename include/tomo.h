@@ -286,8 +286,8 @@ tomo_status tomo_backproject(tomo_ctx *ctx, const tomo_cube_geom *cube,
  * x_dev is [T][nz][ny][nx], each image sees its frames through its time
  * stamp, the spatial prior applies to every frame, and lambda_t >= 0 adds
  * lambda_t ||D_t x||^2 with D_t the difference x[t+1] - x[t] of consecutive
- * frames (normal operator + lambda_t D_t^T D_t).  A map mask with T > 1
- * returns TOMO_ERR_UNSUPPORTED. */
+ * frames (normal operator + lambda_t D_t^T D_t).  A map mask applies to
+ * every frame. */
 tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                        int32_t n_frames, const tomo_image_geom *img,
                        const tomo_pointing *pointing_host,

@@ -867,9 +867,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if (st) return st;
     if (!isfinite(lambda_t) || lambda_t < 0)
         return fail(ctx, TOMO_ERR_ARG, "lambda_t must be finite and >= 0");
-    if (n_frames > 1 && map_mask_dev)
-        return fail(ctx, TOMO_ERR_UNSUPPORTED,
-                    "a map mask with several frames is not supported");
+
     if (flags & ~(TOMO_SOLVE_X0 | TOMO_SOLVE_BF16))
         return fail(ctx, TOMO_ERR_ARG, "unknown flags 0x%x", flags);
     if (!isfinite(lambda) || lambda < 0)
@@ -889,7 +887,8 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     cudaStream_t s = (cudaStream_t)stream;
 
     // all frames' voxels are one CG vector
-    const int64_t n = (int64_t)cube->nx * cube->ny * cube->nz * n_frames;
+    const int64_t nvox = (int64_t)cube->nx * cube->ny * cube->nz;
+    const int64_t n = nvox * n_frames;
     const int64_t m = (int64_t)img->n_img * img->nu * img->nv;
     const bool bf16 = (flags & TOMO_SOLVE_BF16) != 0;
     const size_t n_report = 2 * ((size_t)max_iter + 1);
@@ -949,7 +948,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
     if (flags & TOMO_SOLVE_X0) {
         // r0 = b - (P^T M P + lambda D^T D) x0
         if (mm)
-            LAUNCH(ctx, TOMO_K_VECTOR, s, launch_map_zero(x_dev, mm, n, 1, s));
+            LAUNCH(ctx, TOMO_K_VECTOR, s, launch_map_zero(x_dev, mm, nvox, n_frames, s));
         if ((st = apply_prior(ctx, cube, x_dev, prior_weight_dev, q, lam, lam_t,
                               n_frames, nullptr, s)))
             return st;
@@ -959,11 +958,11 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
              (st = op_adjoint(ctx, t, mask_dev, nullptr, q, cube, n_frames, img,
                               tl, nullptr, s))))
             return st;
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, mm, n, tol * tol,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, q, x_dev, r, p, p16, mm, nvox, n, tol * tol,
                                      partials, counter, S, report, grid, s));
     } else {
         CUDA_TRY(ctx, cudaMemsetAsync(x_dev, 0, sizeof(float) * n, s));
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, nullptr, nullptr, r, p, p16, mm, n,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_init(b, nullptr, nullptr, r, p, p16, mm, nvox, n,
                                      tol * tol, partials, counter, S, report,
                                      grid, s));
     }
@@ -983,7 +982,7 @@ tomo_status tomo_solve(tomo_ctx *ctx, const tomo_cube_geom *cube,
                              tl, done, s)))
             return st;
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_pq(p, q, n, partials, counter, S, grid, s));
-        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, mm, n, partials, counter,
+        LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_update(x_dev, r, p, q, b, mm, nvox, n, partials, counter,
                                        S, report, grid, s));
         LAUNCH(ctx, TOMO_K_VECTOR, s, launch_cg_direction(r, p, p16, n, S, grid, s));
     }

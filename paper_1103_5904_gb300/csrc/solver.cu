@@ -137,19 +137,20 @@ __global__ void k_masked_sumsq(const float *__restrict__ y,
         S[S_YMY] = tot[0];
 }
 
-// With a map mask (mm != NULL) b, r and p are set to 0 on the excluded
-// voxels, so every later iterate stays in the restricted space.
+// With a map mask (mm != NULL, mm_n voxels per frame, the same mask for
+// every frame) b, r and p are set to 0 on the excluded voxels, so every
+// later iterate stays in the restricted space.
 __global__ void k_cg_init(float *__restrict__ b, const float *__restrict__ q,
                           const float *__restrict__ x, float *__restrict__ r,
                           float *__restrict__ p, uint16_t *__restrict__ p16,
-                          const uint8_t *__restrict__ mm, int64_t n,
-                          double tol2, double *partials,
+                          const uint8_t *__restrict__ mm, int64_t mm_n,
+                          int64_t n, double tol2, double *partials,
                           unsigned int *counter, double *S, double *report)
 {
     double v[2] = { 0.0, 0.0 };
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const bool out = mm != nullptr && mm[i] != 0;
+        const bool out = mm != nullptr && mm[i % mm_n] != 0;
         if (out) b[i] = 0.0f;
         const float bi = out ? 0.0f : b[i];
         const float ri = out ? 0.0f : ((q != nullptr) ? bi - q[i] : bi);
@@ -183,9 +184,9 @@ __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
                             const float *__restrict__ p,
                             const float *__restrict__ q,
                             const float *__restrict__ b,
-                            const uint8_t *__restrict__ mm, int64_t n,
-                            double *partials, unsigned int *counter,
-                            double *S, double *report)
+                            const uint8_t *__restrict__ mm, int64_t mm_n,
+                            int64_t n, double *partials,
+                            unsigned int *counter, double *S, double *report)
 {
     if (S[S_DONE] != 0.0) return;
     const float alpha = (float)S[S_ALPHA];
@@ -193,7 +194,7 @@ __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float xi = fmaf(alpha, p[i], x[i]);
-        const float ri = (mm != nullptr && mm[i] != 0)
+        const float ri = (mm != nullptr && mm[i % mm_n] != 0)
                              ? 0.0f
                              : fmaf(-alpha, q[i], r[i]);
         x[i] = xi;
@@ -272,11 +273,13 @@ cudaError_t launch_masked_sumsq(const float *y, const uint8_t *mask,
 
 cudaError_t launch_cg_init(float *b, const float *q, const float *x,
                            float *r, float *p, uint16_t *p16,
-                           const uint8_t *map_mask, int64_t n, double tol2,
-                           double *partials, unsigned int *counter, double *S,
-                           double *report, int grid, cudaStream_t s)
+                           const uint8_t *map_mask, int64_t mm_n, int64_t n,
+                           double tol2, double *partials,
+                           unsigned int *counter, double *S, double *report,
+                           int grid, cudaStream_t s)
 {
-    k_cg_init<<<grid, kThreads, 0, s>>>(b, q, x, r, p, p16, map_mask, n, tol2,
+    k_cg_init<<<grid, kThreads, 0, s>>>(b, q, x, r, p, p16, map_mask,
+                                        mm_n > 0 ? mm_n : 1, n, tol2,
                                         partials, counter, S, report);
     return cudaGetLastError();
 }
@@ -291,12 +294,13 @@ cudaError_t launch_cg_pq(const float *p, const float *q, int64_t n,
 
 cudaError_t launch_cg_update(float *x, float *r, const float *p,
                              const float *q, const float *b,
-                             const uint8_t *map_mask, int64_t n,
+                             const uint8_t *map_mask, int64_t mm_n, int64_t n,
                              double *partials, unsigned int *counter,
                              double *S, double *report, int grid,
                              cudaStream_t s)
 {
-    k_cg_update<<<grid, kThreads, 0, s>>>(x, r, p, q, b, map_mask, n, partials,
+    k_cg_update<<<grid, kThreads, 0, s>>>(x, r, p, q, b, map_mask,
+                                          mm_n > 0 ? mm_n : 1, n, partials,
                                           counter, S, report);
     return cudaGetLastError();
 }

@@ -208,11 +208,12 @@ cudaError_t launch_masked_sumsq(const float *y, const uint8_t *mask,
                                 unsigned int *counter, double *S,
                                 int grid, cudaStream_t s);
 // r = b - q (or r = b if q == NULL); p = r (+ bf16 copy); S[RR], S[RR0],
-// report row 0 from r.r and x.(r + b).  map_mask (nullable): b, r, p set
-// to 0 on the excluded voxels.
+// report row 0 from r.r and x.(r + b).  map_mask (nullable, mm_n voxels
+// per frame): b, r, p set to 0 on the excluded voxels of every frame.
 cudaError_t launch_cg_init(float *b, const float *q, const float *x,
                            float *r, float *p, uint16_t *p16,
-                           const uint8_t *map_mask, int64_t n, double tol2,
+                           const uint8_t *map_mask, int64_t mm_n, int64_t n,
+                           double tol2,
                            double *partials, unsigned int *counter, double *S,
                            double *report, int grid, cudaStream_t s);
 // S[S_PQ] = p.q, S[S_ALPHA] = rr / pq
@@ -223,7 +224,7 @@ cudaError_t launch_cg_pq(const float *p, const float *q, int64_t n,
 // S[RR] <- r.r, beta, report row
 cudaError_t launch_cg_update(float *x, float *r, const float *p,
                              const float *q, const float *b,
-                             const uint8_t *map_mask, int64_t n,
+                             const uint8_t *map_mask, int64_t mm_n, int64_t n,
                              double *partials, unsigned int *counter,
                              double *S, double *report, int grid,
                              cudaStream_t s);
