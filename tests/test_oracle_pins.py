@@ -764,6 +764,80 @@ def test_impact2_matches_pixel_angles():
         np.testing.assert_allclose(r2[n], d * d * t2 / (1 + t2), rtol=1e-10)
 
 
+def _thomson_golden(golden_dir):
+    rows = [ln.split() for ln in open(os.path.join(golden_dir,
+                                                   "thomson_voxel_factors.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    return [tuple(map(float, r)) for r in rows]
+
+
+def _factors_match_golden(voxel_factors, rows):
+    """True when voxel_factors gives the hand-evaluated m and m' at every
+    golden voxel centre (one-voxel cubes centred there), and in the same
+    [nz][ny][nx] order on a cube whose centres run along each axis."""
+    for cx, cy, cz, u, m_want, mp_want in rows:
+        g = _geom((1, 1, 1), (cx - 0.05, cy - 0.05, cz - 0.05),
+                  (0.1, 0.1, 0.1))
+        m, mp = voxel_factors(g, u)
+        if not (m.shape == (1, 1, 1) and
+                math.isclose(float(m[0, 0, 0]), m_want, rel_tol=1e-13,
+                             abs_tol=0.0) and
+                math.isclose(float(mp[0, 0, 0]), mp_want, rel_tol=1e-13,
+                             abs_tol=0.0)):
+            return False
+    # centres 2, 3, 4 along one axis, the other two at 0 (u = 0 rows)
+    want = {r[0] ** 2 + r[1] ** 2 + r[2] ** 2: (r[4], r[5])
+            for r in rows if r[3] == 0.0}
+    for axis in range(3):
+        n = [1, 1, 1]
+        n[axis] = 3
+        lo = [-0.5, -0.5, -0.5]
+        lo[axis] = 1.5
+        m, mp = voxel_factors(_geom(n, lo, (1.0, 1.0, 1.0)), 0.0)
+        m, mp = m.reshape(-1), mp.reshape(-1)
+        for k, r in enumerate((2.0, 3.0, 4.0)):
+            wm, wmp = want[r * r]
+            if not (math.isclose(float(m[k]), wm, rel_tol=1e-13) and
+                    math.isclose(float(mp[k]), wmp, rel_tol=1e-13)):
+                return False
+    return True
+
+
+def test_thomson_voxel_factors_against_hand_values(golden_dir):
+    """m and m' (Eq. brightness with Eq. 4C, Section 3.5) equal the values
+    reduced by hand at r = sqrt2, 2, 3, 4 for u = 0, 1/2, 1, vanish on and
+    inside the photosphere, and come out in [nz][ny][nx] order."""
+    from oracle import thomson
+    rows = _thomson_golden(golden_dir)
+    assert len(rows) == 14
+    assert _factors_match_golden(thomson.voxel_factors, rows)
+
+
+@pytest.mark.parametrize("old,new", [
+    ("rr ** 4", "rr ** 2"),                      # r^-2 for r^-4 in m
+    ("rr ** 2, 0.0)", "rr ** 4, 0.0)"),          # r^-4 for r^-2 in m'
+    ("2.0 * ((1.0 - u) * C3", "((1.0 - u) * C3"),  # factor 2 on m' dropped
+    ("u * C2)", "C2)"),                          # Eq. thomson_lo's missing u
+    ("u * C4)", "C3)"),                          # C3 for C4
+    ("r > 1.0", "r >= 0.0"),                     # scattering inside the Sun
+])
+def test_thomson_voxel_factors_pin_catches_planted_mistakes(golden_dir, old,
+                                                             new):
+    """The hand-value pin fails when one of these plausible mistakes is
+    planted in a copy of the oracle's voxel_factors (the oracle itself is
+    not modified)."""
+    import inspect
+    import textwrap
+
+    from oracle import thomson
+    src = textwrap.dedent(inspect.getsource(thomson.voxel_factors))
+    assert src.count(old) == 1, old
+    ns = dict(vars(thomson))
+    exec(compile(src.replace(old, new), "<planted>", "exec"), ns)
+    rows = _thomson_golden(golden_dir)
+    assert not _factors_match_golden(ns["voxel_factors"], rows)
+
+
 @pytest.mark.parametrize("T", [1, 3])
 def test_thomson_operators_adjoint_and_rows(T):
     """T_pB and T_B against brute-force rows (exact voxel lengths times the
