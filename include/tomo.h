@@ -407,9 +407,12 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
  * of it themselves (a framework's caching allocator, a fixed memory budget
  * shared with other jobs), and latency-critical loops in which a cudaMalloc
  * or cudaFree, which can wait for work already queued on the device, would
- * stall other streams.  tomo_project_noalloc computes the same projection
- * (same kernels, same results) with its scratch in a fixed array that is
- * part of the library image.
+ * stall other streams.  tomo_project_noalloc computes the same images as
+ * tomo_project, bit for bit, with its scratch in a fixed array that is part
+ * of the library image.  It always runs the per-ray forward walk; the
+ * plane-synchronous walk that tomo_project picks for many images gives the
+ * same sums in the same order, but can be faster, so this call may take
+ * longer than tomo_project on the same input.
  *
  * Scratch: one array of TOMO_NOALLOC_SCRATCH_BYTES per device, compiled into
  * the library and therefore held by every device on which this entry point
@@ -428,15 +431,21 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
  * finish before the next starts.
  *
  * Set-up: the first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and remembers it; make
- * that first call before any stream capture.
+ * (cudaGetSymbolAddress, with that device current) and remembers it for the
+ * rest of the process; make that first call before any stream capture.  A
+ * cudaDeviceReset reloads the library's device code at another address, so
+ * this entry point must not be called on a device after that device has
+ * been reset in the same process.
  *
  * Arguments are those of tomo_project without the context and without the
  * map mask (a masked copy of the cube would need cube-sized scratch; apply
  * the mask to the cube before the call): the current device is used, the stream is a cudaStream_t passed as void* (NULL = the
  * legacy default stream), and the call is asynchronous on it.  The
- * pointing table is copied during the call.  No cudaMalloc, cudaFree or
- * other allocating routine is called. */
+ * pointing table is copied to the array by a cudaMemcpyAsync queued on the
+ * stream: a table in page-locked (pinned) host memory is read only when the
+ * stream reaches that copy and must stay unchanged until then; a table in
+ * pageable memory may be reused as soon as the call returns.  No
+ * cudaMalloc, cudaFree or other allocating routine is called. */
 #define TOMO_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 tomo_status tomo_project_noalloc(const tomo_cube_geom *cube, int32_t n_frames,

@@ -6,7 +6,8 @@
 // name as an address (on the host the name denotes a stand-in object, not
 // device memory), so the first call on each device looks the device address
 // up with cudaGetSymbolAddress while that device is current, and every call
-// passes that address to the same kernels tomo_project launches.
+// passes that address to the ray-setup kernels and the per-ray forward
+// kernel that tomo_project also launches.
 #include <mutex>
 
 #include "host.h"
@@ -32,7 +33,9 @@ size_t round256(size_t n)
     return (n + 255) & ~(size_t)255;
 }
 
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array on the current device, looked up once
+// per device and kept for the process (the header forbids calls after a
+// cudaDeviceReset, which would move the array).
 cudaError_t scratch_address(void **out)
 {
     int dev = 0;

@@ -139,18 +139,17 @@ __global__ void k_masked_sumsq(const float *__restrict__ y,
 
 // With a map mask (mm != NULL, mm_n voxels per frame, the same mask for
 // every frame) b, r and p are set to 0 on the excluded voxels, so every
-// later iterate stays in the restricted space.
-__global__ void k_cg_init(float *__restrict__ b, const float *__restrict__ q,
-                          const float *__restrict__ x, float *__restrict__ r,
-                          float *__restrict__ p, uint16_t *__restrict__ p16,
-                          const uint8_t *__restrict__ mm, int64_t mm_n,
-                          int64_t n, double tol2, double *partials,
-                          unsigned int *counter, double *S, double *report)
-{
-    double v[2] = { 0.0, 0.0 };
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const bool out = mm != nullptr && mm[i % mm_n] != 0;
+// later iterate stays in the restricted space.  Masked vectors are walked
+// voxel by voxel with the frames in an inner loop, so each mask byte is read
+// once and no index needs a division.
+struct CgInitElem {
+    float *b;
+    const float *q, *x;
+    float *r, *p;
+    uint16_t *p16;
+    __device__ __forceinline__ void operator()(int64_t i, bool out,
+                                               double v[2]) const
+    {
         if (out) b[i] = 0.0f;
         const float bi = out ? 0.0f : b[i];
         const float ri = out ? 0.0f : ((q != nullptr) ? bi - q[i] : bi);
@@ -159,6 +158,37 @@ __global__ void k_cg_init(float *__restrict__ b, const float *__restrict__ q,
         v[0] += (double)ri * ri;
         if (x != nullptr) v[1] += (double)x[i] * ((double)ri + bi);
     }
+};
+
+// Calls f(i, excluded, v) for every element of n = frames * mm_n (mm_n = n
+// without a mask) in a grid-stride order.
+template <class F>
+__device__ __forceinline__ void masked_elements(const uint8_t *__restrict__ mm,
+                                                int64_t mm_n, int64_t n,
+                                                const F &f, double v[2])
+{
+    const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (mm == nullptr) {
+        for (int64_t i = start; i < n; i += stride) f(i, false, v);
+        return;
+    }
+    for (int64_t i = start; i < mm_n; i += stride) {
+        const bool out = mm[i] != 0;
+        for (int64_t j = i; j < n; j += mm_n) f(j, out, v);
+    }
+}
+
+__global__ void k_cg_init(float *__restrict__ b, const float *__restrict__ q,
+                          const float *__restrict__ x, float *__restrict__ r,
+                          float *__restrict__ p, uint16_t *__restrict__ p16,
+                          const uint8_t *__restrict__ mm, int64_t mm_n,
+                          int64_t n, double tol2, double *partials,
+                          unsigned int *counter, double *S, double *report)
+{
+    double v[2] = { 0.0, 0.0 };
+    const CgInitElem f = { b, q, x, r, p, p16 };
+    masked_elements(mm, mm_n, n, f, v);
     double tot[2];
     if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
         cg_finalize_init(S, report, tot[0], tot[1], tol2);
@@ -180,6 +210,22 @@ __global__ void k_cg_pq(const float *__restrict__ p, const float *__restrict__ q
 
 // With a map mask the residual stays 0 on the excluded voxels (q there is
 // the unrestricted operator's value; p, x and b are already 0).
+struct CgUpdateElem {
+    float *x, *r;
+    const float *p, *q, *b;
+    float alpha;
+    __device__ __forceinline__ void operator()(int64_t i, bool out,
+                                               double v[2]) const
+    {
+        const float xi = fmaf(alpha, p[i], x[i]);
+        const float ri = out ? 0.0f : fmaf(-alpha, q[i], r[i]);
+        x[i] = xi;
+        r[i] = ri;
+        v[0] += (double)ri * ri;
+        v[1] += (double)xi * ((double)ri + b[i]);
+    }
+};
+
 __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
                             const float *__restrict__ p,
                             const float *__restrict__ q,
@@ -189,19 +235,9 @@ __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
                             unsigned int *counter, double *S, double *report)
 {
     if (S[S_DONE] != 0.0) return;
-    const float alpha = (float)S[S_ALPHA];
     double v[2] = { 0.0, 0.0 };
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float xi = fmaf(alpha, p[i], x[i]);
-        const float ri = (mm != nullptr && mm[i % mm_n] != 0)
-                             ? 0.0f
-                             : fmaf(-alpha, q[i], r[i]);
-        x[i] = xi;
-        r[i] = ri;
-        v[0] += (double)ri * ri;
-        v[1] += (double)xi * ((double)ri + b[i]);
-    }
+    const CgUpdateElem f = { x, r, p, q, b, (float)S[S_ALPHA] };
+    masked_elements(mm, mm_n, n, f, v);
     double tot[2];
     if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
         cg_finalize_update(S, report, tot[0], tot[1]);
