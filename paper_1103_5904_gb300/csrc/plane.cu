@@ -49,8 +49,21 @@ namespace tomo {
 
 namespace {
 
+// Slabs per iteration of the middle range (plane_walk) and resident CTAs per
+// SM the register allocation targets, measured on GB300 (256^3 cube, 240
+// views of 512^2): the static forward keeps the loads of four slabs in
+// flight (8.72 ms against 9.25 ms one slab at a time; two slabs at five
+// CTAs 10.7 ms, eight slabs at three CTAs 9.71 ms); the transpose, bound by
+// instruction issue and L2 reductions, walks one slab per iteration (9.75
+// ms against 10.0 ms with two slabs and 10.2 ms before the middle range).
+constexpr int kFwdUnroll = 4;
+constexpr int kFwdTimeUnroll = 1;
+constexpr int kFwdMinBlocks = 4;
+constexpr int kAdjUnroll = 1;
+constexpr int kAdjMinBlocks = 5;
+
 template <typename CubeT, bool kTime>
-__global__ void __launch_bounds__(256, 6)
+__global__ void __launch_bounds__(256, kFwdMinBlocks)
 k_forward_plane(const RayRec *__restrict__ rays,
                 const ImgParam *__restrict__ prm, PlaneCubes cubes,
                 int64_t frame_stride, const uint8_t *__restrict__ mask,
@@ -85,7 +98,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
         op.w0 = 1.0f - q.w;
         op.w1 = q.w;
         op.acc = 0.0f;
-        plane_walk_for(q.pad, p, regular, op);
+        plane_walk_for<kFwdTimeUnroll>(q.pad, p, regular, op);
         acc = op.acc;
         if (live && !regular) {
             GatherTimeOp<CubeT> op2;
@@ -101,7 +114,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
         PlaneGatherOp<CubeT> op;
         op.c = lay;
         op.acc = 0.0f;
-        plane_walk_for(q.pad, p, regular, op);
+        plane_walk_for<kFwdUnroll>(q.pad, p, regular, op);
         acc = op.acc;
         if (live && !regular) {
             GatherOp<CubeT> op2;
@@ -115,7 +128,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
 }
 
 template <bool kTime>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, kAdjMinBlocks)
 k_adjoint_plane(const RayRec *__restrict__ rays,
                 const ImgParam *__restrict__ prm,
                 const float *__restrict__ images,
@@ -148,7 +161,7 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
         op.c1 = op.c0 + frame_stride;
         op.y0 = yv * (1.0f - q.w);
         op.y1 = yv * q.w;
-        plane_walk_for(q.pad, p, regular, op);
+        plane_walk_for<kAdjUnroll>(q.pad, p, regular, op);
         if (live && !regular) {
             ScatterTimeOp op2;
             op2.c0 = acc.c[0] + f0;
@@ -161,7 +174,7 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
         PlaneScatterOp op;
         op.c = lay;
         op.y = yv;
-        plane_walk_for(q.pad, p, regular, op);
+        plane_walk_for<kAdjUnroll>(q.pad, p, regular, op);
         if (live && !regular) {
             ScatterOp op2;
             op2.c = acc.c[0];

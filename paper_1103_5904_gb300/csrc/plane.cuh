@@ -112,6 +112,60 @@ __device__ __forceinline__ int slab_past(float AM, float t0M, float x, bool reac
     return j;
 }
 
+// Per-lane state of the plane walk: distance travelled t, next crossings
+// t1, t2 of the two minor axes and their crossing counts, current voxel.
+struct PlaneState {
+    float t, t1, t2, k1, k2;
+    int idx;
+};
+
+// The fast slab body: at most one crossing, of a1, inside the slab that ends
+// at te.  Emits two segment slots; `go` says whether the lane walks this slab.
+__device__ __forceinline__ void slab_fast(const PlaneRay &p, int sM, PlaneState &s,
+                                          bool go, float te, bool *o, int *id,
+                                          float *ln)
+{
+    const bool c1 = go && s.t1 < te;
+    o[0] = go;
+    id[0] = s.idx;
+    ln[0] = fminf(s.t1, te) - s.t;
+    o[1] = c1;
+    id[1] = s.idx + p.s1;
+    ln[1] = te - s.t1;
+    s.k1 = c1 ? s.k1 + 1.0f : s.k1;
+    s.t1 = c1 ? fmaf(s.k1, p.A1, p.t01) : s.t1;
+    s.idx += (c1 ? p.s1 : 0) + (go ? sM : 0);
+    s.t = go ? te : s.t;
+}
+
+// The general slab body: up to one crossing of each minor axis, in either
+// order.  Emits three segment slots.
+__device__ __forceinline__ void slab_general(const PlaneRay &p, int sM,
+                                             PlaneState &s, bool go, float te,
+                                             bool *o, int *id, float *ln)
+{
+    const bool first1 = s.t1 <= s.t2;
+    const float ta = first1 ? s.t1 : s.t2;
+    const float tb = first1 ? s.t2 : s.t1;
+    const int sa = first1 ? p.s1 : p.s2;
+    o[0] = go;
+    id[0] = s.idx;
+    ln[0] = fminf(ta, te) - s.t;
+    o[1] = go && ta < te;
+    id[1] = s.idx + sa;
+    ln[1] = fminf(tb, te) - ta;
+    o[2] = go && tb < te;
+    id[2] = s.idx + p.s1 + p.s2;
+    ln[2] = te - tb;
+    const bool c1 = go && s.t1 < te, c2 = go && s.t2 < te;
+    s.k1 = c1 ? s.k1 + 1.0f : s.k1;
+    s.k2 = c2 ? s.k2 + 1.0f : s.k2;
+    s.t1 = c1 ? fmaf(s.k1, p.A1, p.t01) : s.t1;
+    s.t2 = c2 ? fmaf(s.k2, p.A2, p.t02) : s.t2;
+    s.idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? sM : 0);
+    s.t = go ? te : s.t;
+}
+
 // Walks the regular lanes of the warp plane by plane; op(on, idx, len) is
 // called for every segment with on == true (len may be 0 at ties, which adds
 // an exact zero) and, with on == false, for slots without a segment (idx
@@ -135,79 +189,126 @@ __device__ __forceinline__ int slab_past(float AM, float t0M, float x, bool reac
 // many slabs, since a row's rays differ slightly in slope and the observer
 // is ~200 cube widths away), the votes and bound updates would cost more
 // than they save.
-template <bool kEveryGeneral, class Op>
+//
+// Inside the slabs that every regular lane walks and that end before every
+// regular lane's last slab ([lo_all, hi_all)), no lane needs the "does it
+// walk this slab" test nor the cap of the slab's far plane at the chord
+// (that plane lies below the chord there, in the walk's own float values),
+// and the slab index is carried as an exact float counter.  That middle
+// range runs U slabs per iteration: the segment slots of U slabs are
+// computed first and op is called on them afterwards, in slab order, so a
+// gathering op can have all of its loads in flight at once while the sums
+// keep their order (and their bits).
+template <bool kEveryGeneral, int U, class Op>
 __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
                                            Op &op)
 {
+    constexpr int kSlots = kEveryGeneral ? 3 : 2;
     const unsigned full = 0xffffffffu;
     const int kmin = __reduce_min_sync(full, regular ? p.key : INT_MAX);
     const int j0 = regular ? p.key - kmin : 0;
     // the walk ends in the first slab whose far plane reaches the chord
     const int jend = regular ? 1 + slab_past(p.AM, p.t0M, p.chord, true) : 0;
     const int i_end = __reduce_max_sync(full, regular ? j0 + jend : 0);
-    float t = 0.0f, k1 = 0.0f, k2 = 0.0f;
-    float t1 = p.t01, t2 = p.t02;
-    int idx = p.idx;
-    if (kEveryGeneral) {
-        for (int i = 0; i < i_end; ++i) {
-            const int j = i - j0;
-            const bool go = (unsigned)j < (unsigned)jend;
-            const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
-            const bool first1 = t1 <= t2;
-            const float ta = first1 ? t1 : t2;
-            const float tb = first1 ? t2 : t1;
-            const int sa = first1 ? p.s1 : p.s2;
-            op(go, idx, fminf(ta, te) - t);
-            op(go && ta < te, idx + sa, fminf(tb, te) - ta);
-            op(go && tb < te, idx + p.s1 + p.s2, te - tb);
-            const bool c1 = go && t1 < te, c2 = go && t2 < te;
-            k1 = c1 ? k1 + 1.0f : k1;
-            k2 = c2 ? k2 + 1.0f : k2;
-            t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
-            t2 = c2 ? fmaf(k2, p.A2, p.t02) : t2;
-            idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? p.sM : 0);
-            t = go ? te : t;
+    const int lo_all = __reduce_max_sync(full, regular ? j0 : 0);
+    const int hi_all = __reduce_min_sync(full, regular ? j0 + jend - 1 : INT_MAX);
+    // non-regular lanes never advance (their slots are all off)
+    const int sM = regular ? p.sM : 0;
+    PlaneState s;
+    s.t = 0.0f;
+    s.k1 = 0.0f;
+    s.k2 = 0.0f;
+    s.t1 = p.t01;
+    s.t2 = p.t02;
+    s.idx = p.idx;
+
+    // one slab with the lane tests (outside the middle range)
+    auto edge = [&](int i, bool general) {
+        const int j = i - j0;
+        const bool go = (unsigned)j < (unsigned)jend;
+        const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
+        bool o[3];
+        int id[3];
+        float ln[3];
+        if (general) {
+            slab_general(p, sM, s, go, te, o, id, ln);
+            op(o[0], id[0], ln[0]);
+            op(o[1], id[1], ln[1]);
+            op(o[2], id[2], ln[2]);
+        } else {
+            slab_fast(p, sM, s, go, te, o, id, ln);
+            op(o[0], id[0], ln[0]);
+            op(o[1], id[1], ln[1]);
         }
+    };
+    // slabs [i, m_end) inside the middle range, kSlots-segment body
+    auto middle = [&](int &i, int m_end) {
+        float jf = (float)(i - j0);
+        for (; i + U <= m_end; i += U) {
+            bool o[U * kSlots];
+            int id[U * kSlots];
+            float ln[U * kSlots];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float te = fmaf(jf, p.AM, p.t0M);
+                jf += 1.0f;
+                if constexpr (kEveryGeneral)
+                    slab_general(p, sM, s, regular, te, o + u * kSlots,
+                                 id + u * kSlots, ln + u * kSlots);
+                else
+                    slab_fast(p, sM, s, regular, te, o + u * kSlots,
+                              id + u * kSlots, ln + u * kSlots);
+            }
+#pragma unroll
+            for (int k = 0; k < U * kSlots; ++k) op(o[k], id[k], ln[k]);
+        }
+        for (; i < m_end; ++i) {
+            bool o[kSlots];
+            int id[kSlots];
+            float ln[kSlots];
+            const float te = fmaf(jf, p.AM, p.t0M);
+            jf += 1.0f;
+            if constexpr (kEveryGeneral)
+                slab_general(p, sM, s, regular, te, o, id, ln);
+            else
+                slab_fast(p, sM, s, regular, te, o, id, ln);
+#pragma unroll
+            for (int k = 0; k < kSlots; ++k) op(o[k], id[k], ln[k]);
+        }
+    };
+    // slabs [i, stop) with the kSlots-segment body
+    auto run = [&](int &i, int stop) {
+        const int e1 = stop < lo_all ? stop : lo_all;
+        for (; i < e1; ++i) edge(i, kEveryGeneral);
+        const int m_end = stop < hi_all ? stop : hi_all;
+        if (i < m_end) middle(i, m_end);
+        for (; i < stop; ++i) edge(i, kEveryGeneral);
+    };
+
+    int i = 0;
+    if constexpr (kEveryGeneral) {
+        run(i, i_end);
         return;
     }
     // slab of the next a2 crossing (the first whose far plane lies beyond it)
-    int j2 = (regular && t2 < p.chord) ? slab_past(p.AM, p.t0M, t2, false) : INT_MAX;
+    int j2 = (regular && s.t2 < p.chord) ? slab_past(p.AM, p.t0M, s.t2, false) : INT_MAX;
     int next = __reduce_min_sync(full, j2 < jend ? j0 + j2 : INT_MAX);
-    int i = 0;
     while (i < i_end) {
-        const int stop = next < i_end ? next : i_end;
-        for (; i < stop; ++i) {
-            const int j = i - j0;
-            const bool go = (unsigned)j < (unsigned)jend;
-            const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
-            const bool c1 = go && t1 < te;
-            op(go, idx, fminf(t1, te) - t);
-            op(c1, idx + p.s1, te - t1);
-            k1 = c1 ? k1 + 1.0f : k1;
-            t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
-            idx += (c1 ? p.s1 : 0) + (go ? p.sM : 0);
-            t = go ? te : t;
-        }
+        run(i, next < i_end ? next : i_end);
         if (i >= i_end) break;
         // slab i holds a crossing of a2 for at least one lane
         const int j = i - j0;
         const bool go = (unsigned)j < (unsigned)jend;
         const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
-        const bool first1 = t1 <= t2;
-        const float ta = first1 ? t1 : t2;
-        const float tb = first1 ? t2 : t1;
-        const int sa = first1 ? p.s1 : p.s2;
-        op(go, idx, fminf(ta, te) - t);
-        op(go && ta < te, idx + sa, fminf(tb, te) - ta);
-        op(go && tb < te, idx + p.s1 + p.s2, te - tb);
-        const bool c1 = go && t1 < te, c2 = go && t2 < te;
-        k1 = c1 ? k1 + 1.0f : k1;
-        k2 = c2 ? k2 + 1.0f : k2;
-        t1 = c1 ? fmaf(k1, p.A1, p.t01) : t1;
-        t2 = c2 ? fmaf(k2, p.A2, p.t02) : t2;
-        idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? p.sM : 0);
-        t = go ? te : t;
-        if (c2) j2 = t2 < p.chord ? slab_past(p.AM, p.t0M, t2, false) : INT_MAX;
+        const bool c2 = go && s.t2 < te;
+        bool o[3];
+        int id[3];
+        float ln[3];
+        slab_general(p, sM, s, go, te, o, id, ln);
+        op(o[0], id[0], ln[0]);
+        op(o[1], id[1], ln[1]);
+        op(o[2], id[2], ln[2]);
+        if (c2) j2 = s.t2 < p.chord ? slab_past(p.AM, p.t0M, s.t2, false) : INT_MAX;
         ++i;
         next = __reduce_min_sync(full, j2 < jend ? j0 + j2 : INT_MAX);
     }
@@ -215,14 +316,14 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
 
 // The walk variant the image's hint selects (the hint is the same for the
 // whole CTA, so every lane of a warp takes the same branch).
-template <class Op>
+template <int U = 1, class Op>
 __device__ __forceinline__ void plane_walk_for(int hint, const PlaneRay &p,
                                                bool regular, Op &op)
 {
     if (hint & kPlaneGeneralBit)
-        plane_walk<true>(p, regular, op);
+        plane_walk<true, U>(p, regular, op);
     else
-        plane_walk<false>(p, regular, op);
+        plane_walk<false, U>(p, regular, op);
 }
 
 template <typename CubeT>

@@ -26,6 +26,12 @@ import torch
 RTOL_F32 = 1e-5
 ATOL_FRAC = 1e-7
 
+# (what, elements that meet the relative bound only with the absolute term,
+# elements compared): printed at the end of the session (tests/conftest.py),
+# so that a regression hiding under the absolute term shows as a growing
+# share
+FLOOR_SHARES = []
+
 
 def require_gpu():
     if not torch.cuda.is_available():
@@ -47,6 +53,8 @@ def close_report(got, want, rtol=RTOL_F32, atol_frac=ATOL_FRAC):
 
 def assert_close(got, want, what, rtol=RTOL_F32, atol_frac=ATOL_FRAC):
     bad, rel, scale = close_report(got, want, rtol, atol_frac)
+    floor = (rel > rtol) & ~bad
+    FLOOR_SHARES.append((what, int(floor.sum()), int(bad.size)))
     assert not bad.any(), (
         "%s: %d of %d values outside %.1e rel + %.1e x max (max %.3e); worst "
         "rel err %.3e" % (what, int(bad.sum()), bad.size, rtol, atol_frac,
@@ -63,6 +71,8 @@ def assert_transpose_close(got, want, cw, geom, what, rtol=RTOL_F32):
     bound = rtol * np.abs(want) + 8.0 * 2.0 ** -24 * t_max * np.asarray(cw)
     err = np.abs(got - want)
     bad = err > bound
+    floor = (err > rtol * np.abs(want)) & ~bad
+    FLOOR_SHARES.append((what, int(floor.sum()), int(bad.size)))
     assert not bad.any(), (
         "%s: %d of %d voxels outside the bound; worst err/bound %.3f"
         % (what, int(bad.sum()), bad.size, float((err / np.maximum(
