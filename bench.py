@@ -66,6 +66,9 @@ def parse_args(argv=None):
                     help="CG iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the comparisons timed after the headline "
+                         "(bf16, autograd, temporal, batched, Thomson)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--plane-sync", type=int, default=None,
@@ -432,6 +435,11 @@ def run_gpu(args, rank, local_rank, world):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": 1e3 * e_s / args.steps}
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and \
+            args.workload == "cg256" and not args.images:
+        extras = run_extras(ctx, dev, c, y, mask, args.iters, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, desc, _, _ = oracle_sample(c, args.cpu_seconds)
@@ -467,6 +475,8 @@ def run_gpu(args, rank, local_rank, world):
             "clocks": clk,
             "wall_s": t_wall,
         }
+        if extras is not None:
+            line.update(extras)
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -557,6 +567,204 @@ def run_batched(args, rank, local_rank, world):
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+# ------------------------------------------------ comparisons (extras)
+
+def _med_ms(fn, reps, flush):
+    """Median device time of fn() over reps calls (CUDA events on the
+    current stream), L2 flushed before each call outside the events."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def run_extras(ctx, dev, c, y, mask, iters, flush):
+    """The forms compared against the plain FP32 single-instance path on the
+    same GPU, timed after the headline (which they do not change):
+      bf16:     P with the cube stored in bf16, and CG with a bf16 copy of
+                the direction run to the FP32 criterion of `iters` iterations
+      temporal: P and P^T of the 8-frame time-interpolated workload (frame
+                pairs side by side), f32 and bf16 frames
+      autograd: forward + backward of 0.5 ||P X||^2 through the autograd
+                Function against the plain P and P^T calls (temporal)
+      thomson:  pB and B operators (one walk for B) against P, photosphere
+                geometry
+      batched:  the 32-problem workload: one graph replay of 10 CG
+                iterations and one batched P / P^T against the per-problem
+                calls."""
+    import torch
+    import synth
+    import paper_1103_5904_gb300 as T
+    out = {}
+    g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
+    X = torch.from_numpy(c["cube"]).to(dev)
+    segs = T.tomo_count_segments(g, ptg, nu, nv, mask=mask, ctx=ctx)
+    yy = torch.empty_like(y)
+    p32 = _med_ms(lambda: T.tomo_project(X, g, ptg, nu, nv, mask=mask,
+                                         out=yy, ctx=ctx), 5, flush)
+    Xb = X.to(torch.bfloat16)
+    p16 = _med_ms(lambda: T.tomo_project(Xb, g, ptg, nu, nv, mask=mask,
+                                         out=yy, ctx=ctx), 5, flush)
+    del Xb
+    x = torch.empty_like(X)
+    _, i32 = T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"], max_iter=iters,
+                          out=x, ctx=ctx)
+    _, i16 = T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"],
+                          max_iter=int(1.5 * iters), out=x, bf16=True, ctx=ctx)
+    target = i32["J"][iters] * (1 + 1e-4)
+    hit = np.flatnonzero(i16["J"] <= target)
+    k16 = int(hit[0]) if hit.size else -1
+    cg32 = _med_ms(lambda: T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"],
+                                        max_iter=iters, out=x, report=False,
+                                        ctx=ctx), 3, flush)
+    cg16 = (_med_ms(lambda: T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"],
+                                         max_iter=k16, out=x, bf16=True,
+                                         report=False, ctx=ctx), 3, flush)
+            if k16 > 0 else None)
+    out["bf16"] = {"P_f32_ms": p32, "P_bf16_ms": p16,
+                   "cg_f32_iters": iters, "cg_bf16_iters_to_f32_criterion": k16,
+                   "cg_f32_ms": cg32, "cg_bf16_ms_to_f32_criterion": cg16,
+                   "what": "%s: bf16-stored cube against float32 (P), and CG "
+                           "with a bf16 copy of the direction run until its "
+                           "criterion reaches the float32 criterion after %d "
+                           "iterations" % (c["name"], iters)}
+    # Thomson operators on the same geometry with the photosphere
+    go = dict(g, r_obs=1.0)
+    th = {}
+    for kind in ("emission", "pB", "B"):
+        kw = {} if kind == "emission" else {"kind": kind, "limb_u": 0.6}
+        yk = T.tomo_project(X, go, ptg, nu, nv, mask=mask, ctx=ctx, **kw)
+        th[kind + "_P_ms"] = _med_ms(lambda: T.tomo_project(
+            X, go, ptg, nu, nv, mask=mask, out=yk, ctx=ctx, **kw), 5, flush)
+        th[kind + "_PT_ms"] = _med_ms(lambda: T.tomo_backproject(
+            yk, go, ptg, mask=mask, out=x, ctx=ctx, **kw), 5, flush)
+        del yk
+    th["B_over_pB"] = {"P": th["B_P_ms"] / th["pB_P_ms"],
+                       "PT": th["B_PT_ms"] / th["pB_PT_ms"]}
+    th["what"] = ("%s with the opaque photosphere r_obs = 1, limb darkening "
+                  "0.6: emission P, T_pB = O P M and T_B = P M' - O P M (one "
+                  "walk on (m' x, m x) pairs)" % c["name"])
+    out["thomson"] = th
+    del X, x, yy
+    torch.cuda.empty_cache()
+    # time-interpolated workload and the autograd Function
+    ct = synth.make_config("temporal")
+    gt, pt, tf = ct["geom"], ct["pointing"], ct["n_frames"]
+    Xt = torch.from_numpy(ct["cube"]).to(dev)
+    st = T.tomo_count_segments(gt, pt, ct["nu"], ct["nv"], ctx=ctx)
+    yt = T.tomo_project(Xt, gt, pt, ct["nu"], ct["nv"], n_frames=tf, ctx=ctx)
+    xt = torch.empty_like(Xt)
+    tp = _med_ms(lambda: T.tomo_project(Xt, gt, pt, ct["nu"], ct["nv"],
+                                        n_frames=tf, out=yt, ctx=ctx), 5, flush)
+    ta = _med_ms(lambda: T.tomo_backproject(yt, gt, pt, n_frames=tf, out=xt,
+                                            ctx=ctx), 5, flush)
+    Xtb = Xt.to(torch.bfloat16)
+    tpb = _med_ms(lambda: T.tomo_project(Xtb, gt, pt, ct["nu"], ct["nv"],
+                                         n_frames=tf, out=yt, ctx=ctx), 5, flush)
+    del Xtb
+    out["temporal"] = {"segments": int(st), "P_ms": tp, "PT_ms": ta,
+                       "P_bf16_ms": tpb,
+                       "P_segments_per_s": st / (tp / 1e3),
+                       "PT_segments_per_s": st / (ta / 1e3),
+                       "what": WORKLOAD_TEXT_TEMPORAL}
+    Xg = Xt.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        Xg.grad = None
+        P = T.autograd.project(Xg, gt, pt, ct["nu"], ct["nv"], n_frames=tf,
+                               ctx=ctx)
+        P.backward(P.detach())
+    out["autograd"] = {"fwd_bwd_ms": _med_ms(fwd_bwd, 5, flush),
+                       "plain_P_plus_PT_ms": tp + ta,
+                       "what": "temporal: forward + backward of 0.5 ||P X||^2 "
+                               "through the autograd Function (backward = the "
+                               "transpose kernel) against the plain P and P^T "
+                               "calls"}
+    del Xt, xt, yt, Xg
+    torch.cuda.empty_cache()
+    out["batched"] = batched_compare(T, ctx, dev, flush, steps=3, warmup=1)
+    return out
+
+
+WORKLOAD_TEXT_TEMPORAL = (
+    "temporal: 8 frames of 256^3 f32 over [-1.5,1.5]^3 R_sun; 240 images "
+    "512x512, time stamps U[0,7]; two observer groups 40 deg apart")
+
+
+def batched_compare(T, ctx, dev, flush, steps, warmup, iters=10):
+    """The 32-problem workload: graph-replayed batched CG against the
+    per-problem loop, and one batched P and P^T over all problems against
+    the per-problem calls (ray records cached in both)."""
+    import torch
+    import synth
+    probs, segs = [], 0
+    for c in synth.configs.batched():
+        cube = torch.from_numpy(c["cube"]).to(dev)
+        y = T.tomo_project(cube, c["geom"], c["pointing"], c["nu"], c["nv"],
+                           ctx=ctx)
+        segs += T.tomo_count_segments(c["geom"], c["pointing"], c["nu"],
+                                      c["nv"], ctx=ctx)
+        probs.append({"geom": c["geom"], "pointing": c["pointing"],
+                      "nu": c["nu"], "nv": c["nv"], "images": y,
+                      "cube": torch.zeros_like(cube), "lam": c["lam"],
+                      "x_true": cube})
+    T.tomo_solve_batched(probs, iters, autotune=True, report=False, ctx=ctx)
+
+    def batched_cg():
+        T.tomo_solve_batched(probs, iters, report=False, ctx=ctx)
+
+    def sequential_cg():
+        for p in probs:
+            T.tomo_solve(p["images"], p["geom"], p["pointing"], lam=p["lam"],
+                         max_iter=iters, out=p["cube"], report=False, ctx=ctx)
+    fwd_b = [dict(p, cube=p["x_true"], images=torch.empty_like(p["images"]))
+             for p in probs]
+    adj_b = [dict(p, cube=torch.empty_like(p["x_true"])) for p in probs]
+
+    def batched_p():
+        T.tomo_project_batched(fwd_b, ctx=ctx)
+
+    def batched_pt():
+        T.tomo_backproject_batched(adj_b, ctx=ctx)
+
+    def seq_p():
+        for p, d in zip(probs, fwd_b):
+            T.tomo_project(p["x_true"], p["geom"], p["pointing"], p["nu"],
+                           p["nv"], out=d["images"], ctx=ctx)
+
+    def seq_pt():
+        for p, d in zip(probs, adj_b):
+            T.tomo_backproject(p["images"], p["geom"], p["pointing"],
+                               out=d["cube"], ctx=ctx)
+    res = {}
+    for name, fn in (("cg_graph_ms", batched_cg), ("cg_sequential_ms",
+                                                   sequential_cg),
+                     ("P_batched_ms", batched_p), ("P_sequential_ms", seq_p),
+                     ("PT_batched_ms", batched_pt),
+                     ("PT_sequential_ms", seq_pt)):
+        for _ in range(warmup):
+            fn()
+        res[name] = _med_ms(fn, steps, flush)
+    res["cg_speedup"] = res["cg_sequential_ms"] / res["cg_graph_ms"]
+    res["segments_per_projection_all_problems"] = int(segs)
+    res["cg_iters"] = iters
+    res["what"] = (WORKLOAD_TEXT["batched"] + "; batched = one graph replay "
+                   "(CG) or one persistent launch (P, P^T) over all problems, "
+                   "sequential = the single-problem calls one after another; "
+                   "ray records cached, L2 flushed before each timing")
+    return res
 
 
 # ------------------------------------------------------- measurement table

@@ -167,6 +167,17 @@ typedef struct tomo_ctx tomo_ctx;
                                   per side, else the per-ray walk is used.
                                   Costs two cube-sized float buffers (times
                                   the frames) of workspace. */
+#define TOMO_OPT_CHANNELS   8  /* bit mask (default 3) of the two-value
+                                  plane walks: bit 0, time-interpolated P
+                                  and P^T walk frame pairs (X[k], X[k+1])
+                                  stored side by side (one 8-byte load or
+                                  vector reduction per segment instead of
+                                  two 4-byte ones a cube apart; P stays
+                                  bit-identical); bit 1, the Thomson B
+                                  operator of a single frame runs one walk
+                                  on (m' x, m x) pairs instead of two walks.
+                                  Costs three buffers of 8 bytes per voxel
+                                  (times T - 1 frame pairs) of workspace. */
 
 /* Kernel classes of tomo_profile */
 enum {
@@ -357,22 +368,67 @@ typedef struct {
     const float *prior_weight_dev;
 } tomo_problem;
 
-/* A tile shape and its measured times (tomo_autotune). */
+/* Thresholds that choose, per image, which Siddon walk P and P^T run.
+ * "pitch": the image's pixel spacing at the distance of Sun centre, in
+ * voxels of the axis along which a row of pixels moves; "ratio": the less
+ * steep minor direction component of the image's central line of sight
+ * over its major component.  Only speed depends on them: every walk gives
+ * the same segments (P bit-identical, P^T up to the order of float
+ * additions).  Values >= 1e30 stand for "never". */
+typedef struct {
+    double min_pitch;      /* plane-synchronous walks when pitch >= this,
+                              per-ray walks below (default 0.16) */
+    double fwd_min_pitch;  /* P plane-synchronous when pitch >= this ... */
+    double fwd_max_ratio;  /* ... or ratio < this (defaults 0.75, 0.02; P
+                              per ray otherwise) */
+    double general_ratio;  /* plane walks cross every slab with the general
+                              three-segment body when ratio >= this, else
+                              they count the slabs to the next crossing of
+                              the rarer minor axis (default 0.035) */
+} tomo_plane_rules;
+
+/* A tile shape, walk rules and measured times (tomo_autotune): the
+ * per-ray tile and the rules the problem's size bucket uses, and the time
+ * of its P and P^T with them. */
 typedef struct {
     int32_t tile_u, tile_v, warp_u;
     float fwd_ms, adj_ms;
+    tomo_plane_rules rules;
 } tomo_tiling;
 
 #define TOMO_BATCH_AUTOTUNE 8u /* solve_batched: tune unseen problem sizes */
 
-/* Times the forward and transpose kernels of one problem (its cube_dev and
- * images_dev are read, not written) for a fixed list of 256-thread tile
- * shapes, keeps the fastest (forward + transpose time) for that problem size
- * in the context, and returns it in best_out (nullable).  Later single and
- * batched calls on problems of the same size use it.  Synchronises
+/* Tunes the schedule of one problem's size bucket (cube voxel counts and
+ * image size): times the per-ray forward and transpose kernels for a fixed
+ * list of 256-thread tile shapes and keeps the fastest; then, with that
+ * tile, times P and P^T as the single-problem calls run them under
+ * candidate walk rules (tomo_plane_rules: per-ray or plane-synchronous
+ * walks by pixel pitch, counted or every-slab plane walks by direction
+ * ratio, the plane forward by pitch and ratio), searching one threshold at
+ * a time and keeping the fastest P + P^T.  The problem's cube_dev and
+ * images_dev are read, not written.  The winners are kept in the context
+ * for the bucket and returned in best_out (nullable); later single and
+ * batched calls on problems of the same size use them.  Synchronises
  * `stream`. */
 tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
                           tomo_tiling *best_out, void *stream);
+
+/* Sets the walk rules of a size bucket (cube voxel counts and image size,
+ * both non-NULL), or the context's default for buckets without their own
+ * (cube and img NULL).  rules NULL: the built-in defaults.  Takes effect at
+ * the next call on a geometry of that bucket. */
+tomo_status tomo_set_plane_rules(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                                 const tomo_image_geom *img,
+                                 const tomo_plane_rules *rules);
+
+/* The walk chosen for each image of the most recent single-problem
+ * geometry (synchronises the legacy default stream):
+ *   bit 0: P^T (and P when bit 1) walk plane by plane (else per ray)
+ *   bit 1: P walks plane by plane
+ *   bit 2: the plane walks cross every slab with the general body
+ *   bits 3-4: the major axis (0 x, 1 y, 2 z); bits 5-6: the lateral axis
+ * codes_host: n_img entries; n_img must equal the geometry's image count. */
+tomo_status tomo_walk_plan(tomo_ctx *ctx, int32_t n_img, int32_t *codes_host);
 
 /* images = P cube for every problem, in one persistent launch (plus the FP64
  * ray setup of every problem when the set of geometries changes). */

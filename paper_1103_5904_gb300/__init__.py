@@ -12,6 +12,7 @@ from .tomo import (Context, TomoError, default_context, load_library,  # noqa
                    tomo_project, tomo_backproject, tomo_solve,
                    tomo_prior_apply, tomo_count_segments,
                    tomo_project_batched, tomo_backproject_batched,
-                   tomo_solve_batched, tomo_autotune, project,
+                   tomo_solve_batched, tomo_autotune,
+                   tomo_set_plane_rules, tomo_walk_plan, project,
                    backproject, solve, prior_apply, count_segments)
 from .autograd import TomoProject  # noqa: F401

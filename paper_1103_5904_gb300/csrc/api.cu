@@ -192,10 +192,33 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     h = fnv1a(h, cv, sizeof(cv));
     h = fnv1a(h, g, sizeof(*g));
     h = fnv1a(h, ptg, sizeof(tomo_pointing) * (size_t)g->n_img);
+    const tomo_plane_rules rules = rules_for(ctx, c, g);
+    const uint64_t hh = fnv1a(h, &rules, sizeof(rules));
     tomo_status st;
     if ((st = ensure(ctx, ctx->layout_used, sizeof(unsigned)))) return st;
     if (ctx->ray_cache && ctx->key_valid && ctx->key == h) {
+        if (ctx->hint_key == hh) {
+            CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
+            return TOMO_OK;
+        }
+        // same rays, other walk rules: only the per-image hints change
         CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
+        ctx->fwd_plane_possible = false;
+        ctx->plane_possible = false;
+        for (int32_t i = 0; i < g->n_img; ++i) {
+            ctx->plane_possible |= plane_estimate(ptg[i], c, rules);
+            ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c, rules);
+        }
+        LAUNCH(ctx, TOMO_K_SETUP, s,
+               launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
+                             g->nv, n_frames, (Frame *)ctx->frames.p,
+                             (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
+                             (ImgParam *)ctx->params.p,
+                             make_double3(c->dx, c->dy, c->dz),
+                             (unsigned *)ctx->layout_used.p, rules, s));
+        CUDA_TRY(ctx, cudaEventRecord(ctx->setup_done, s));
+        ctx->hint_key = hh;
         return TOMO_OK;
     }
     ctx->key_valid = false;
@@ -214,8 +237,8 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     ctx->fwd_plane_possible = false;
     ctx->plane_possible = false;
     for (size_t i = 0; i < n_img; ++i) {
-        ctx->plane_possible |= plane_estimate(ptg[i], c);
-        ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c);
+        ctx->plane_possible |= plane_estimate(ptg[i], c, rules);
+        ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c, rules);
     }
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
@@ -223,7 +246,7 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
                          (ImgParam *)ctx->params.p,
                          make_double3(c->dx, c->dy, c->dz),
-                         (unsigned *)ctx->layout_used.p, s));
+                         (unsigned *)ctx->layout_used.p, rules, s));
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_ray_setup((const Frame *)ctx->frames.p,
                             (const double *)ctx->tan_u.p,
@@ -240,6 +263,8 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     }
     CUDA_TRY(ctx, cudaEventRecord(ctx->setup_done, s));
     ctx->key = h;
+    ctx->hint_key = hh;
+    ctx->cached_n_img = g->n_img;
     ctx->key_valid = true;
     return TOMO_OK;
 }
@@ -266,6 +291,16 @@ Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
     return ctx->tiling;
 }
 
+tomo_plane_rules rules_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                           const tomo_image_geom *g)
+{
+    for (const Tuned &t : ctx->tuned)
+        if (t.nx == c->nx && t.ny == c->ny && t.nz == c->nz && t.nu == g->nu &&
+            t.nv == g->nv)
+            return t.rules;
+    return ctx->rules;
+}
+
 cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
                         const ImgParam *prm, const Frame *frames,
                         const tomo_pointing *ptg, const float *images,
@@ -290,15 +325,17 @@ cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
 
 // The device's rules (setup.cu) evaluated from the boresight, with margins
 // towards "may"; the pixel pitch with the smallest voxel side.
-bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c)
+bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c,
+                    const tomo_plane_rules &r)
 {
     const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
-    return p.d_obs * fabs(tan(p.cdelt_u)) / dmin >= 0.9 * kPlaneMinPitch;
+    return p.d_obs * fabs(tan(p.cdelt_u)) / dmin >= 0.9 * r.min_pitch;
 }
 
-bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c)
+bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c,
+                            const tomo_plane_rules &r)
 {
-    if (!plane_estimate(p, c)) return false;
+    if (!plane_estimate(p, c, r)) return false;
     const double cl = cos(p.lat);
     const double w[3] = { fabs(cl * cos(p.lon)), fabs(cl * sin(p.lon)),
                           fabs(sin(p.lat)) };
@@ -306,7 +343,7 @@ bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c)
     const double lo = fmin(w[0], fmin(w[1], w[2])) / hi;
     const double dmin = fmin(c->dx, fmin(c->dy, c->dz));
     const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dmin;
-    return pitch >= 0.9 * kPlaneFwdMinPitch || lo < 1.5 * kPlaneFwdMaxRatio;
+    return pitch >= 0.9 * r.fwd_min_pitch || lo < 1.5 * r.fwd_max_ratio;
 }
 
 bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
@@ -331,6 +368,24 @@ tomo_status ensure_plane(tomo_ctx *ctx, const tomo_cube_geom *c,
     return TOMO_OK;
 }
 
+// Two-value buffers for layouts 0, 1, 2: T - 1 frame pairs (or one pair)
+// of 8 bytes per voxel.
+tomo_status ensure_pairs(tomo_ctx *ctx, const tomo_cube_geom *c,
+                         int32_t n_frames)
+{
+    const size_t npairs = n_frames > 1 ? (size_t)(n_frames - 1) : 1;
+    const size_t bytes = 8 * (size_t)c->nx * c->ny * c->nz * npairs;
+    tomo_status st;
+    for (int L = 0; L < 3; ++L)
+        if ((st = ensure(ctx, ctx->pr[L], bytes))) return st;
+    return TOMO_OK;
+}
+
+bool use_time_pairs(const tomo_ctx *ctx, int32_t n_frames)
+{
+    return n_frames > 1 && (ctx->channels & 1);
+}
+
 tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                         int32_t n_frames, const uint8_t *mask, float *out,
                         const tomo_cube_geom *c, const tomo_image_geom *g,
@@ -342,6 +397,30 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
     // bit 1: every image plane-synchronous; else (bit 2) the images whose
     // hint marks the plane forward as faster, the rest per ray
     const bool all = (ctx->plane_sync & 2) != 0;
+    if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible) &&
+        use_time_pairs(ctx, n_frames)) {
+        // frame pairs side by side in every layout in use (layout 0 too)
+        tomo_status st;
+        if ((st = ensure_pairs(ctx, c, n_frames))) return st;
+        const unsigned *used = (const unsigned *)ctx->layout_used.p;
+        for (int L = 0; L <= 2; ++L)
+            LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                   launch_to_pairs(cube_dev, dtype, ctx->pr[L].p, L, c,
+                                   n_frames, used,
+                                   all ? 1u << L : 1u << (8 + L), done,
+                                   ctx->num_sms, s));
+        PlaneCubes pc = { { ctx->pr[0].p, ctx->pr[1].p, ctx->pr[2].p } };
+        if (!all)
+            LAUNCH(ctx, TOMO_K_FORWARD, s,
+                   launch_forward(rays, prm, cube_dev, dtype, fstride, true,
+                                  mask, out, g->n_img, g->nu, g->nv, c->nx,
+                                  c->nx * c->ny, t, done, s, true));
+        LAUNCH(ctx, TOMO_K_FORWARD, s,
+               launch_forward_plane_pair(rays, prm, pc, cube_dev, dtype,
+                                         fstride, mask, out, g->n_img, g->nu,
+                                         g->nv, c, done, s, !all));
+        return TOMO_OK;
+    }
     if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible)) {
         const unsigned *used = (const unsigned *)ctx->layout_used.p;
         for (int L = 1; L <= 2; ++L)
@@ -377,6 +456,31 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
 {
     const RayRec *rays = (const RayRec *)ctx->rays.p;
     const ImgParam *prm = (const ImgParam *)ctx->params.p;
+    if (use_plane(ctx, c, t, false) && ctx->plane_possible &&
+        use_time_pairs(ctx, n_frames)) {
+        // frame-pair accumulators in every layout in use, added into the
+        // frames after the walk
+        tomo_status st;
+        if ((st = ensure_pairs(ctx, c, n_frames))) return st;
+        const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
+        const unsigned *used = (const unsigned *)ctx->layout_used.p;
+        for (int L = 0; L <= 2; ++L)
+            LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                   launch_zero_layout((float *)ctx->pr[L].p, L,
+                                      2 * fstride * (n_frames - 1), used,
+                                      done, ctx->num_sms, s));
+        PlaneAcc pa = { { (float *)ctx->pr[0].p, (float *)ctx->pr[1].p,
+                          (float *)ctx->pr[2].p } };
+        LAUNCH(ctx, TOMO_K_ADJOINT, s,
+               launch_adjoint_plane_pair(rays, prm, images, mask, pa, cube,
+                                         fstride, g->n_img, g->nu, g->nv, c,
+                                         done, s));
+        for (int L = 0; L <= 2; ++L)
+            LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                   launch_add_pairs(ctx->pr[L].p, cube, L, c, n_frames, used,
+                                    done, ctx->num_sms, s));
+        return TOMO_OK;
+    }
     if (use_plane(ctx, c, t, false) && ctx->plane_possible) {
         const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
         const unsigned *used = (const unsigned *)ctx->layout_used.p;
@@ -441,14 +545,39 @@ tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
     const int64_t n = (int64_t)c->nx * c->ny * c->nz;
     const int64_t npix = (int64_t)g->n_img * g->nu * g->nv;
     tomo_status st;
+    const float2 *mf = (const float2 *)ctx->thf.p;
+    const float *rho2 = (const float *)ctx->rho2.p;
+    const bool bf16 = dtype == TOMO_BF16;
+    if (g->kind == TOMO_KIND_B && n_frames == 1 && (ctx->channels & 2)) {
+        // one walk on (m' K x, m K x) pairs: y = g s' - rho^2 g s
+        if ((st = ensure_pairs(ctx, c, 1))) return st;
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_thomson_weight2(src, bf16, mf, mm, n,
+                                      (float2 *)ctx->pr[0].p, done, s));
+        const bool all = (ctx->plane_sync & 2) != 0;
+        const bool plane = use_plane(ctx, c, t, true) &&
+                           (all || ctx->fwd_plane_possible);
+        if (plane) {
+            const unsigned *used = (const unsigned *)ctx->layout_used.p;
+            for (int L = 1; L <= 2; ++L)
+                LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                       launch_b_to_layout(ctx->pr[0].p, ctx->pr[L].p, L, c,
+                                          used, all ? 1u << L : 1u << (8 + L),
+                                          done, s));
+        }
+        PlaneCubes pc = { { ctx->pr[0].p, ctx->pr[1].p, ctx->pr[2].p } };
+        LAUNCH(ctx, TOMO_K_FORWARD, s,
+               launch_forward_b((const RayRec *)ctx->rays.p,
+                                (const ImgParam *)ctx->params.p, pc, rho2,
+                                mask, out, g->n_img, g->nu, g->nv, c, done,
+                                plane ? (all ? 2 : 1) : 0, s));
+        return TOMO_OK;
+    }
     if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
         (g->kind == TOMO_KIND_B &&
          (st = ensure(ctx, ctx->thimg, sizeof(float) * (npix > 0 ? npix : 1)))))
         return st;
-    const float2 *mf = (const float2 *)ctx->thf.p;
-    const float *rho2 = (const float *)ctx->rho2.p;
     float *c1 = (float *)ctx->th1.p;
-    const bool bf16 = dtype == TOMO_BF16;
     // pB: M x; B: first M' x, then M x (the scratch is reused in order)
     LAUNCH(ctx, TOMO_K_VECTOR, s,
            launch_thomson_weight(src, bf16, mf, g->kind == TOMO_KIND_B ? 1 : 0,
@@ -485,12 +614,41 @@ tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
     const int64_t npix = (int64_t)g->n_img * g->nu * g->nv;
     const bool b = g->kind == TOMO_KIND_B;
     tomo_status st;
+    const float2 *mf = (const float2 *)ctx->thf.p;
+    const float *rho2 = (const float *)ctx->rho2.p;
+    if (b && n_frames == 1 && (ctx->channels & 2)) {
+        // one walk scattering (g y, rho^2 g y) into pair accumulators, then
+        // dst += K (m' a - m b)
+        if ((st = ensure_pairs(ctx, c, 1))) return st;
+        const bool plane = use_plane(ctx, c, t, false) && ctx->plane_possible;
+        const unsigned *used = (const unsigned *)ctx->layout_used.p;
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->pr[0].p, 0, 8 * (size_t)n, s));
+        if (plane)
+            for (int L = 1; L <= 2; ++L)
+                LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                       launch_zero_layout((float *)ctx->pr[L].p, L, 2 * n,
+                                          used, done, ctx->num_sms, s));
+        PlaneAcc pa = { { (float *)ctx->pr[0].p, (float *)ctx->pr[1].p,
+                          (float *)ctx->pr[2].p } };
+        LAUNCH(ctx, TOMO_K_ADJOINT, s,
+               launch_adjoint_b((const RayRec *)ctx->rays.p,
+                                (const ImgParam *)ctx->params.p, images, rho2,
+                                mask, pa, g->n_img, g->nu, g->nv, c, done,
+                                plane, s));
+        if (plane)
+            for (int L = 1; L <= 2; ++L)
+                LAUNCH(ctx, TOMO_K_LAYOUT, s,
+                       launch_add_b_layout(ctx->pr[L].p, ctx->pr[0].p, L, c,
+                                           used, done, s));
+        LAUNCH(ctx, TOMO_K_VECTOR, s,
+               launch_thomson_add2(dst, (const float2 *)ctx->pr[0].p, mf, mm,
+                                   n, done, s));
+        return TOMO_OK;
+    }
     if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
         (b && (st = ensure(ctx, ctx->th2, sizeof(float) * n * n_frames))) ||
         (st = ensure(ctx, ctx->thimg, sizeof(float) * (npix > 0 ? npix : 1))))
         return st;
-    const float2 *mf = (const float2 *)ctx->thf.p;
-    const float *rho2 = (const float *)ctx->rho2.p;
     float *c1 = (float *)ctx->th1.p, *c2 = (float *)ctx->th2.p;
     float *ti = (float *)ctx->thimg.p;
     LAUNCH(ctx, TOMO_K_VECTOR, s,
@@ -600,7 +758,8 @@ void tomo_destroy(tomo_ctx *ctx)
                        &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
                        &ctx->counter, &ctx->count64, &ctx->layout_used,
                        &ctx->lay1, &ctx->lay2, &ctx->mcube, &ctx->rho2,
-                       &ctx->thf, &ctx->th1, &ctx->th2, &ctx->thimg };
+                       &ctx->thf, &ctx->th1, &ctx->th2, &ctx->thimg,
+                       &ctx->pr[0], &ctx->pr[1], &ctx->pr[2] };
     for (DevBuf *b : bufs)
         if (b->p) cudaFree(b->p);
     free_plan(ctx);
@@ -642,11 +801,41 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
         if (value < 0 || value > 7) break;
         ctx->plane_sync = (int)value;
         return TOMO_OK;
+    case TOMO_OPT_CHANNELS:
+        if (value < 0 || value > 3) break;
+        ctx->channels = (int)value;
+        return TOMO_OK;
     default:
         return fail(ctx, TOMO_ERR_ARG, "unknown option %d", option);
     }
     return fail(ctx, TOMO_ERR_ARG, "option %d: value %lld out of range", option,
                 (long long)value);
+}
+
+tomo_status tomo_walk_plan(tomo_ctx *ctx, int32_t n_img, int32_t *codes_host)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    if (!ctx->key_valid)
+        return fail(ctx, TOMO_ERR_ARG, "no geometry has been set up yet");
+    if (n_img != ctx->cached_n_img || (n_img > 0 && !codes_host))
+        return fail(ctx, TOMO_ERR_ARG, "n_img does not match the geometry");
+    if (n_img == 0) return TOMO_OK;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(ctx, TOMO_ERR_CUDA, "cannot select device");
+    std::vector<ImgParam> prm((size_t)n_img);
+    CUDA_TRY(ctx, cudaStreamWaitEvent(0, ctx->setup_done, 0));
+    CUDA_TRY(ctx, cudaMemcpy(prm.data(), ctx->params.p,
+                             sizeof(ImgParam) * (size_t)n_img,
+                             cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < n_img; ++i) {
+        const int32_t h = prm[i].pad;
+        const bool valid = (h & kPlaneHintValid) != 0;
+        codes_host[i] = (valid ? 1 : 0) | ((valid && (h & kPlaneFwdBit)) ? 2 : 0) |
+                        ((h & kPlaneGeneralBit) ? 4 : 0) | ((h & 3) << 3) |
+                        (((h >> 2) & 3) << 5);
+    }
+    return TOMO_OK;
 }
 
 tomo_status tomo_clear_cache(tomo_ctx *ctx)

@@ -275,7 +275,7 @@ k_to_layout_batched(const LayoutJob *__restrict__ jobs,
 // the plane forward the warps walk plane by plane on the layout copies
 // (irregular lanes per ray on the native cube), otherwise every lane walks
 // its own ray.  All lanes of a warp take part in the plane walk's votes.
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 4)
 k_forward_plane_batched(const WalkDesc *__restrict__ descs,
                         const int64_t *__restrict__ prefix,
                         const int2 *__restrict__ sched, int64_t n_chunks,
@@ -324,7 +324,7 @@ k_forward_plane_batched(const WalkDesc *__restrict__ descs,
                     PlaneGatherOp<float> op;
                     op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.src);
                     op.acc = 0.0f;
-                    plane_walk_for(q.pad, pr, regular, op);
+                    plane_walk_for<4>(q.pad, pr, regular, op);
                     acc = op.acc;
                     if (live && !regular) {
                         GatherOp<float> op2;
@@ -488,15 +488,14 @@ int walk_batched_blocks_per_sm()
     return n < m ? (n > 0 ? n : 1) : (m > 0 ? m : 1);
 }
 
-int plane_batched_blocks_per_sm()
+int plane_batched_blocks_per_sm(bool adjoint)
 {
-    int q = 0, f = 0;
+    int q = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &q, k_adjoint_plane_batched, kThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &f, k_forward_plane_batched, kThreads, 0) != cudaSuccess)
+            &q, adjoint ? (const void *)k_adjoint_plane_batched
+                        : (const void *)k_forward_plane_batched,
+            kThreads, 0) != cudaSuccess)
         return 1;
-    q = q < f ? q : f;
     return q > 0 ? q : 1;
 }
 

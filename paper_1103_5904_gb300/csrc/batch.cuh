@@ -64,7 +64,7 @@ struct VecDesc {
 };
 
 int walk_batched_blocks_per_sm();
-int plane_batched_blocks_per_sm();
+int plane_batched_blocks_per_sm(bool adjoint);
 // sched[c] = (problem, first tile) of chunk c: kSchedGroup consecutive
 // tiles of one problem (tiles past the problem's count are skipped)
 cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,

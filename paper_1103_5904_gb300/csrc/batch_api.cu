@@ -158,6 +158,8 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
         h = fnv1a(h, p.pointing_host, sizeof(tomo_pointing) * (size_t)p.img.n_img);
         const Tiling t = batch_tiling(ctx, &p);
         h = fnv1a(h, &t, sizeof(t));
+        const tomo_plane_rules r = rules_for(ctx, &p.cube, &p.img);
+        h = fnv1a(h, &r, sizeof(r));
     }
     if (!ctx->plan) {
         ctx->plan = new BatchPlan();
@@ -194,8 +196,10 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                               ((g.nv + P->tl[i].tile_v - 1) / P->tl[i].tile_v);
         P->tile_prefix[i + 1] = P->tile_prefix[i] + tiles;
         bool plane_ok = false;
+        const tomo_plane_rules rules = rules_for(ctx, &probs[i].cube, &g);
         for (int32_t k = 0; k < g.n_img; ++k)
-            plane_ok |= plane_estimate(probs[i].pointing_host[k], &probs[i].cube);
+            plane_ok |= plane_estimate(probs[i].pointing_host[k],
+                                       &probs[i].cube, rules);
         P->ptile_prefix[i + 1] =
             P->ptile_prefix[i] + (plane_ok ? (int64_t)g.n_img *
                                      ((g.nu + kPlaneTileU - 1) / kPlaneTileU) *
@@ -245,7 +249,8 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                launch_frames((const tomo_pointing *)P->ptg.p + P->img_off[i],
                              p.img.n_img, p.img.nu, p.img.nv, 1, fr, tu, tv, pr,
                              make_double3(p.cube.dx, p.cube.dy, p.cube.dz),
-                             (unsigned *)P->lay_used.p + i, s));
+                             (unsigned *)P->lay_used.p + i,
+                             rules_for(ctx, &p.cube, &p.img), s));
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_ray_setup(fr, tu, tv, cube_dev(&p.cube), p.img.n_img,
                                 p.img.nu, p.img.nv,
@@ -380,9 +385,10 @@ bool batch_plane_forward(const tomo_ctx *ctx, int32_t n, const tomo_problem *pro
     return true;
 }
 
-int plane_walk_grid(const tomo_ctx *ctx)
+int plane_walk_grid(const tomo_ctx *ctx, bool adjoint)
 {
-    return (ctx->num_sms > 0 ? ctx->num_sms : 152) * plane_batched_blocks_per_sm();
+    return (ctx->num_sms > 0 ? ctx->num_sms : 152) *
+           plane_batched_blocks_per_sm(adjoint);
 }
 
 int combine_grid(const tomo_ctx *ctx)
@@ -431,7 +437,7 @@ tomo_status batched_walk_core(tomo_ctx *ctx, int32_t n,
                                                 (const int64_t *)P->ptpre_dev.p,
                                                 (const int2 *)P->psched_dev.p,
                                                 P->pn_chunks, ctr2,
-                                                plane_walk_grid(ctx), s));
+                                                plane_walk_grid(ctx, true), s));
         if (P->rn_chunks > 0)
             LAUNCH(ctx, TOMO_K_ADJOINT, s,
                    launch_walk_batched(true, (const WalkDesc *)P->call_desc.p,
@@ -460,7 +466,7 @@ tomo_status batched_walk_core(tomo_ctx *ctx, int32_t n,
                                                 (const int64_t *)P->ptpre_dev.p,
                                                 (const int2 *)P->psched_dev.p,
                                                 P->pn_chunks, ctr2,
-                                                plane_walk_grid(ctx), s));
+                                                plane_walk_grid(ctx, false), s));
         if (P->rn_chunks > 0)
             LAUNCH(ctx, TOMO_K_FORWARD, s,
                    launch_walk_batched(false, (const WalkDesc *)P->call_desc.p,
@@ -581,6 +587,61 @@ tomo_status time_tiling(tomo_ctx *ctx, const tomo_problem *p, Tiling t,
     return st;
 }
 
+// Times P and P^T of one problem as the single-problem calls run them
+// (walks chosen per image by the bucket's current rules, layout copies and
+// combines included); best of the last two of three repetitions.
+tomo_status time_schedule(tomo_ctx *ctx, const tomo_problem *p, Tiling t,
+                          float *images_tmp, float *cube_tmp, cudaStream_t s,
+                          float *fwd_ms, float *adj_ms)
+{
+    tomo_status st;
+    if ((st = prepare_rays(ctx, &p->cube, 1, &p->img, p->pointing_host, s)))
+        return st;
+    cudaEvent_t e[3];
+    for (int k = 0; k < 3; ++k)
+        CUDA_TRY(ctx, cudaEventCreate(&e[k]));
+    float best_f = INFINITY, best_a = INFINITY;
+    for (int rep = 0; rep < 3 && st == TOMO_OK; ++rep) {
+        cudaError_t err = cudaEventRecord(e[0], s);
+        if (err == cudaSuccess &&
+            (st = forward_one(ctx, p->cube_dev, TOMO_F32, 1, p->mask_dev,
+                              images_tmp, &p->cube, &p->img, t, nullptr, s)))
+            break;
+        if (err == cudaSuccess) err = cudaEventRecord(e[1], s);
+        if (err == cudaSuccess &&
+            (st = adjoint_one(ctx, p->images_dev, p->mask_dev, cube_tmp,
+                              &p->cube, 1, &p->img, t, nullptr, s)))
+            break;
+        if (err == cudaSuccess) err = cudaEventRecord(e[2], s);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e[2]);
+        float f = 0, a = 0;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&f, e[0], e[1]);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&a, e[1], e[2]);
+        if (err != cudaSuccess) {
+            st = fail(ctx, TOMO_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
+            break;
+        }
+        if (rep > 0) {
+            best_f = f < best_f ? f : best_f;
+            best_a = a < best_a ? a : best_a;
+        }
+    }
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(e[k]);
+    *fwd_ms = best_f;
+    *adj_ms = best_a;
+    return st;
+}
+
+Tuned *bucket_of(tomo_ctx *ctx, const tomo_cube_geom *c,
+                 const tomo_image_geom *g)
+{
+    for (Tuned &e : ctx->tuned)
+        if (e.nx == c->nx && e.ny == c->ny && e.nz == c->nz && e.nu == g->nu &&
+            e.nv == g->nv)
+            return &e;
+    return nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -625,21 +686,116 @@ tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
             best.adj_ms = a;
         }
     }
-    bool replaced = false;
-    for (Tuned &e : ctx->tuned)
-        if (e.nx == best.nx && e.ny == best.ny && e.nz == best.nz &&
-            e.nu == best.nu && e.nv == best.nv) {
-            e = best;
-            replaced = true;
-        }
-    if (!replaced) ctx->tuned.push_back(best);
-    if (best_out) {
-        best_out->tile_u = best.tl.tile_u;
-        best_out->tile_v = best.tl.tile_v;
-        best_out->warp_u = best.tl.warp_u;
-        best_out->fwd_ms = best.fwd_ms;
-        best_out->adj_ms = best.adj_ms;
+    best.rules = rules_for(ctx, &prob->cube, &prob->img);
+    Tuned *entry = bucket_of(ctx, &prob->cube, &prob->img);
+    if (entry)
+        *entry = best;
+    else {
+        ctx->tuned.push_back(best);
+        entry = &ctx->tuned.back();
     }
+
+    // Walk rules, one threshold at a time, each candidate timed on P and
+    // P^T as the single-problem calls run them (the winner of one search
+    // is kept for the next).  A candidate replaces the current rules only
+    // when it is more than 1 % faster (timing noise).
+    const double never = 1e30;
+    float cur_f, cur_a;
+    if ((st = time_schedule(ctx, prob, entry->tl, (float *)ctx->t.p,
+                            (float *)ctx->q.p, s, &cur_f, &cur_a)))
+        return st;
+    struct Search {
+        int field;          // 0 min_pitch, 1 general_ratio, 2 fwd_max_ratio,
+                            // 3 fwd_min_pitch
+        bool forward_only;  // compare P alone (else P + P^T)
+        double cand[5];
+        int n;
+    };
+    const Search searches[] = {
+        { 0, false, { never, 0.10, 0.16, 0.25, 0.40 }, 5 },
+        { 1, false, { 0.0, 0.02, 0.035, 0.06, never }, 5 },
+        { 2, true, { 0.0, 0.01, 0.02, 0.04, never }, 5 },
+        { 3, true, { 0.5, 0.75, 1.0, never, never }, 4 },
+    };
+    for (const Search &q : searches) {
+        for (int k = 0; k < q.n; ++k) {
+            tomo_plane_rules r = entry->rules;
+            double *fld = q.field == 0 ? &r.min_pitch
+                          : q.field == 1 ? &r.general_ratio
+                          : q.field == 2 ? &r.fwd_max_ratio
+                                         : &r.fwd_min_pitch;
+            if (*fld == q.cand[k]) continue;
+            *fld = q.cand[k];
+            const tomo_plane_rules keep = entry->rules;
+            entry->rules = r;
+            float f, a;
+            if ((st = time_schedule(ctx, prob, entry->tl, (float *)ctx->t.p,
+                                    (float *)ctx->q.p, s, &f, &a)))
+                return st;
+            const float now = q.forward_only ? f : f + a;
+            const float was = q.forward_only ? cur_f : cur_f + cur_a;
+            if (now < 0.99f * was) {
+                cur_f = f;
+                cur_a = a;
+            } else {
+                entry->rules = keep;
+            }
+        }
+    }
+    entry->fwd_ms = cur_f;
+    entry->adj_ms = cur_a;
+    // leave the cached hints on the winning rules
+    if ((st = prepare_rays(ctx, &prob->cube, 1, &prob->img,
+                           prob->pointing_host, s)))
+        return st;
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    if (best_out) {
+        best_out->tile_u = entry->tl.tile_u;
+        best_out->tile_v = entry->tl.tile_v;
+        best_out->warp_u = entry->tl.warp_u;
+        best_out->fwd_ms = entry->fwd_ms;
+        best_out->adj_ms = entry->adj_ms;
+        best_out->rules = entry->rules;
+    }
+    return TOMO_OK;
+}
+
+tomo_status tomo_set_plane_rules(tomo_ctx *ctx, const tomo_cube_geom *cube,
+                                 const tomo_image_geom *img,
+                                 const tomo_plane_rules *rules)
+{
+    if (!ctx) return TOMO_ERR_ARG;
+    ctx->err[0] = 0;
+    if ((cube == nullptr) != (img == nullptr))
+        return fail(ctx, TOMO_ERR_ARG, "cube and img must both be given or "
+                                       "both be NULL");
+    const tomo_plane_rules r = rules ? *rules : default_plane_rules();
+    const double v[4] = { r.min_pitch, r.fwd_min_pitch, r.fwd_max_ratio,
+                          r.general_ratio };
+    for (double x : v)
+        if (!(x >= 0.0) || isnan(x))
+            return fail(ctx, TOMO_ERR_ARG, "plane rules must be >= 0");
+    if (!cube) {
+        ctx->rules = r;
+        return TOMO_OK;
+    }
+    tomo_status st;
+    if ((st = check_cube(ctx, cube, 1)) || (st = check_img(ctx, img)))
+        return st;
+    Tuned *e = bucket_of(ctx, cube, img);
+    if (!e) {
+        Tuned t;
+        t.nx = cube->nx;
+        t.ny = cube->ny;
+        t.nz = cube->nz;
+        t.nu = img->nu;
+        t.nv = img->nv;
+        t.tl = ctx->tiling;
+        t.fwd_ms = t.adj_ms = INFINITY;
+        ctx->tuned.push_back(t);
+        e = &ctx->tuned.back();
+    }
+    e->rules = r;
     return TOMO_OK;
 }
 
@@ -861,7 +1017,8 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int64_t *ptile_pre = (const int64_t *)P->ptpre_dev.p;
         const int2 *psch = (const int2 *)P->psched_dev.p;
         const int cgrid = combine_grid(ctx);
-        const int pgrid = plane_walk_grid(ctx);
+        const int pgrid = plane_walk_grid(ctx, true);
+        const int pfgrid = plane_walk_grid(ctx, false);
         const LayoutJob *FJ = (const LayoutJob *)P->solve_fjobs.p;
         const int64_t *rtile_pre = (const int64_t *)P->rtpre_dev.p;
         const int2 *rsch = (const int2 *)P->rsched_dev.p;
@@ -877,7 +1034,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
                 CAP(TOMO_K_FORWARD,                                          \
                     launch_forward_plane_batched(W + (ws) * n, ptile_pre,    \
                                                  psch, P->pn_chunks,         \
-                                                 ctr + next_ctr++, pgrid, c)); \
+                                                 ctr + next_ctr++, pfgrid, c)); \
             if (P->rn_chunks > 0)                                            \
                 CAP(TOMO_K_FORWARD,                                          \
                     launch_walk_batched(false, W + (ws) * n, rtile_pre, rsch, \

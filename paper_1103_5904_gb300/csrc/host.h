@@ -19,11 +19,14 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-// A tile shape chosen by the autotuner for one problem size.
+// The schedule of one size bucket (cube voxel counts, image size): the
+// per-ray tile shape and the walk rules, set by the autotuner (or the
+// rules by tomo_set_plane_rules).
 struct Tuned {
     int32_t nx, ny, nz, nu, nv;
     Tiling tl;
     float fwd_ms, adj_ms;
+    tomo_plane_rules rules;
 };
 
 struct BatchPlan;  // batch_api.cu
@@ -41,10 +44,17 @@ struct tomo_ctx {
     // image; bit 2: P plane-synchronous for the images whose hint marks it
     // as the faster walk (coarse pixels), per ray for the others
     int plane_sync = 5;
+    // bit 0: time-interpolated plane walks on frame pairs stored side by
+    // side; bit 1: Thomson B in one walk on (m' x, m x) pairs
+    int channels = 3;
     tomo::Tiling tiling = { 32, 8, 8 };
+    // walk rules of size buckets without their own
+    tomo_plane_rules rules = tomo::default_plane_rules();
     // geometry cache
     bool key_valid = false;
-    uint64_t key = 0;
+    uint64_t key = 0;       // geometry of the cached ray records
+    uint64_t hint_key = 0;  // geometry and walk rules of the cached hints
+    int32_t cached_n_img = 0;  // images of the cached geometry
     cudaEvent_t setup_done = nullptr;
     // per-geometry buffers
     tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
@@ -58,6 +68,10 @@ struct tomo_ctx {
     bool plane_possible = true;
     // cube copies (forward) / accumulators (transpose) in layouts 1 and 2
     tomo::host::DevBuf lay1, lay2;
+    // two-value buffers (8 bytes per voxel) in layouts 0, 1, 2: frame pairs
+    // of the time-interpolated plane walks, (m' x, m x) pairs of the
+    // single-walk Thomson B operator
+    tomo::host::DevBuf pr[3];
     // solver workspace
     tomo::host::DevBuf b, r, p, q, t, p16, S, partials, counter, count64;
     // map-masked cube copy (forward) / transpose scratch (accumulate)
@@ -99,6 +113,9 @@ int reduce_grid(const tomo_ctx *ctx, int64_t n);
 // context's option.
 Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
                   const tomo_image_geom *g);
+// Walk rules for a problem: its size bucket's, else the context's.
+tomo_plane_rules rules_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                           const tomo_image_geom *g);
 void free_plan(tomo_ctx *ctx);
 // Launches the transpose of one problem with the context's adjoint mode
 // (windowed when possible, plain atomics otherwise).
@@ -141,8 +158,10 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
 // the boresight: whether an image may get a valid hint, and whether it may
 // select the plane forward.  Only speed depends on them: the kernel that
 // runs when an estimate says no walks every ray per ray.
-bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c);
-bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c);
+bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c,
+                    const tomo_plane_rules &r);
+bool plane_forward_estimate(const tomo_pointing &p, const tomo_cube_geom *c,
+                            const tomo_plane_rules &r);
 tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          int32_t n_frames, const tomo_image_geom *g,
                          const tomo_pointing *ptg, cudaStream_t s);

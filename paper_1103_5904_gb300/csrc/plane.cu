@@ -89,13 +89,13 @@ k_forward_plane(const RayRec *__restrict__ rays,
     const CubeT *native = static_cast<const CubeT *>(cubes.c[0]);
     const CubeT *lay = static_cast<const CubeT *>(
         L == 1 ? cubes.c[1] : (L == 2 ? cubes.c[2] : cubes.c[0]));
-    const int64_t f0 = kTime ? (int64_t)q.frame * frame_stride : 0;
+    const int64_t f0 = kTime ? (int64_t)img_frame(q) * frame_stride : 0;
     float acc = 0.0f;
     if (kTime) {
         PlaneGatherTimeOp<CubeT> op;
         op.c0 = lay + f0;
         op.c1 = op.c0 + frame_stride;
-        op.w0 = 1.0f - q.w;
+        op.w0 = q.w0;
         op.w1 = q.w;
         op.acc = 0.0f;
         plane_walk_for<kFwdTimeUnroll>(q.pad, p, regular, op);
@@ -154,12 +154,12 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
     const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
     const int L = (q.pad >> 2) & 3;
     float *lay = L == 1 ? acc.c[1] : (L == 2 ? acc.c[2] : acc.c[0]);
-    const int64_t f0 = kTime ? (int64_t)q.frame * frame_stride : 0;
+    const int64_t f0 = kTime ? (int64_t)img_frame(q) * frame_stride : 0;
     if (kTime) {
         PlaneScatterTimeOp op;
         op.c0 = lay + f0;
         op.c1 = op.c0 + frame_stride;
-        op.y0 = yv * (1.0f - q.w);
+        op.y0 = yv * q.w0;
         op.y1 = yv * q.w;
         plane_walk_for<kAdjUnroll>(q.pad, p, regular, op);
         if (live && !regular) {

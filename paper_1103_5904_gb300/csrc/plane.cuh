@@ -259,8 +259,12 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
                     slab_fast(p, sM, s, regular, te, o + u * kSlots,
                               id + u * kSlots, ln + u * kSlots);
             }
+            // all loads of the U slabs first, then the additions in order
+            typename Op::Val v[U * kSlots];
 #pragma unroll
-            for (int k = 0; k < U * kSlots; ++k) op(o[k], id[k], ln[k]);
+            for (int k = 0; k < U * kSlots; ++k) v[k] = op.fetch(o[k], id[k]);
+#pragma unroll
+            for (int k = 0; k < U * kSlots; ++k) op.apply(o[k], id[k], ln[k], v[k]);
         }
         for (; i < m_end; ++i) {
             bool o[kSlots];
@@ -326,13 +330,28 @@ __device__ __forceinline__ void plane_walk_for(int hint, const PlaneRay &p,
         plane_walk<false, U>(p, regular, op);
 }
 
+// Plane ops: fetch(on, idx) loads what the segment needs (nothing for the
+// scatters), apply(on, idx, len, v) adds it; the walk's middle range issues
+// the fetches of several slabs before their applies.  op(on, idx, len) does
+// both at once.
+struct NoVal {};
+
 template <typename CubeT>
 struct PlaneGatherOp {
     const CubeT *c;
     float acc;
+    using Val = float;
+    __device__ __forceinline__ float fetch(bool on, int idx) const
+    {
+        return on ? load_voxel(c, idx) : 0.0f;
+    }
+    __device__ __forceinline__ void apply(bool on, int, float len, float v)
+    {
+        if (on) acc = fmaf(len, v, acc);
+    }
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
-        if (on) acc = fmaf(len, load_voxel(c, idx), acc);
+        apply(on, idx, len, fetch(on, idx));
     }
 };
 
@@ -341,21 +360,34 @@ struct PlaneGatherTimeOp {
     const CubeT *c0;
     const CubeT *c1;
     float w0, w1, acc;
+    using Val = float2;
+    __device__ __forceinline__ float2 fetch(bool on, int idx) const
+    {
+        return on ? make_float2(load_voxel(c0, idx), load_voxel(c1, idx))
+                  : make_float2(0.0f, 0.0f);
+    }
+    __device__ __forceinline__ void apply(bool on, int, float len, float2 v)
+    {
+        if (on) acc = fmaf(len, fmaf(w0, v.x, w1 * v.y), acc);
+    }
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
-        if (on) {
-            const float v = fmaf(w0, load_voxel(c0, idx), w1 * load_voxel(c1, idx));
-            acc = fmaf(len, v, acc);
-        }
+        apply(on, idx, len, fetch(on, idx));
     }
 };
 
 struct PlaneScatterOp {
     float *c;
     float y;
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    using Val = NoVal;
+    __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
+    __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
     {
         if (on) red_add(c + idx, len * y);
+    }
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        apply(on, idx, len, NoVal());
     }
 };
 
@@ -363,12 +395,18 @@ struct PlaneScatterTimeOp {
     float *c0;
     float *c1;
     float y0, y1;
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    using Val = NoVal;
+    __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
+    __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
     {
         if (on) {
             red_add(c0 + idx, len * y0);
             red_add(c1 + idx, len * y1);
         }
+    }
+    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    {
+        apply(on, idx, len, NoVal());
     }
 };
 

@@ -27,11 +27,13 @@ namespace {
 // of a row move at a fixed M plane.  Moving along the row turns the
 // direction by ~e1; at a fixed M plane the ray through u + e1 d is displaced
 // along e1 - u e1_M / u_M.  The hint is marked valid only when neighbouring
-// pixels are at least kPlaneMinPitch voxels of L apart at the distance of
-// Sun centre; the forward and walk-variant bits follow the measured rules
-// in tomo_internal.cuh.  Only the walks' speed depends on the hint.
+// pixels are at least rules.min_pitch voxels of L apart at the distance of
+// Sun centre; the forward and walk-variant bits follow the other rules
+// (defaults: the measured thresholds in tomo_internal.cuh; tomo_autotune
+// can tune them per size bucket).  Only the walks' speed depends on the
+// hint.
 __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
-                              int nv, double3 vox)
+                              int nv, double3 vox, const tomo_plane_rules &rules)
 {
     const double tu = tan((0.5 * (nu - 1) - p.crpix_u) * p.cdelt_u + p.crval_u);
     const double tv = tan((0.5 * (nv - 1) - p.crpix_v) * p.cdelt_v + p.crval_v);
@@ -52,13 +54,13 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
     }
     const double dL = L == 0 ? vox.x : (L == 1 ? vox.y : vox.z);
     const double pitch = p.d_obs * fabs(tan(p.cdelt_u)) / dL;
-    const bool valid = pitch >= kPlaneMinPitch;
+    const bool valid = pitch >= rules.min_pitch;
     double lo = INFINITY;  // the less steep minor component
     for (int a = 0; a < 3; ++a)
         if (a != M) lo = fmin(lo, fabs(u[a]));
     lo /= fabs(u[M]);
-    const bool general = lo >= kPlaneGeneralRatio;
-    const bool fwd = valid && (pitch >= kPlaneFwdMinPitch || lo < kPlaneFwdMaxRatio);
+    const bool general = lo >= rules.general_ratio;
+    const bool fwd = valid && (pitch >= rules.fwd_min_pitch || lo < rules.fwd_max_ratio);
     return (valid ? kPlaneHintValid : 0) | (fwd ? kPlaneFwdBit : 0) |
            (general ? kPlaneGeneralBit : 0) | M | (L << 2) |
            ((u[M] < 0.0) ? 16 : 0);
@@ -69,7 +71,8 @@ __device__ int32_t plane_hint(const tomo_pointing &p, const Frame &f, int nu,
 __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
                          int32_t nv, int32_t n_frames, Frame *frames,
                          double *tan_u, double *tan_v, ImgParam *params,
-                         double3 vox, unsigned *layout_used)
+                         double3 vox, unsigned *layout_used,
+                         tomo_plane_rules rules)
 {
     const int img = blockIdx.x;
     const tomo_pointing p = ptg[img];
@@ -97,7 +100,7 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
         frames[img] = f;
         ImgParam q;
         q.gain = (float)p.gain;
-        q.pad = plane_hint(p, f, nu, nv, vox);
+        q.pad = plane_hint(p, f, nu, nv, vox, rules);
         if (layout_used && (q.pad & kPlaneHintValid)) {
             // bit L: a plane transpose uses layout L; bit 8 + L: so does a
             // plane forward
@@ -109,11 +112,13 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
             int k = (int)floor(p.time);
             if (k > n_frames - 2) k = n_frames - 2;
             if (k < 0) k = 0;
-            q.frame = k;
-            q.w = (float)(p.time - k);
+            const double w = p.time - k;
+            q.pad |= k << 8;
+            q.w = (float)w;
+            q.w0 = (float)(1.0 - w);
         } else {
-            q.frame = 0;
             q.w = 0.0f;
+            q.w0 = 1.0f;
         }
         params[img] = q;
     }
@@ -232,11 +237,12 @@ cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
                           ImgParam *params, double3 vox,
-                          unsigned *layout_used, cudaStream_t s)
+                          unsigned *layout_used, const tomo_plane_rules &rules,
+                          cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
     k_frames<<<n_img, 128, 0, s>>>(ptg_dev, nu, nv, n_frames, frames, tan_u,
-                                   tan_v, params, vox, layout_used);
+                                   tan_v, params, vox, layout_used, rules);
     return cudaGetLastError();
 }
 

@@ -41,9 +41,9 @@ k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
             const ImgParam q = prm[img];
             if (kTime) {
                 GatherTimeOp<CubeT> op;
-                op.c0 = cube + (int64_t)q.frame * frame_stride;
+                op.c0 = cube + (int64_t)img_frame(q) * frame_stride;
                 op.c1 = op.c0 + frame_stride;
-                op.w0 = 1.0f - q.w;
+                op.w0 = q.w0;
                 op.w1 = q.w;
                 op.acc = 0.0f;
                 siddon_walk(r, nx, nxny, op);
@@ -80,9 +80,9 @@ k_adjoint(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
     if (!(r.chord > 0.0f)) return;
     if (kTime) {
         ScatterTimeOp op;
-        op.c0 = cube + (int64_t)q.frame * frame_stride;
+        op.c0 = cube + (int64_t)img_frame(q) * frame_stride;
         op.c1 = op.c0 + frame_stride;
-        op.y0 = yv * (1.0f - q.w);
+        op.y0 = yv * q.w0;
         op.y1 = yv * q.w;
         siddon_walk(r, nx, nxny, op);
     } else {

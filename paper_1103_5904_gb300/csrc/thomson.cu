@@ -140,6 +140,47 @@ __global__ void k_thomson_add(float *__restrict__ dst,
     }
 }
 
+// dst[v] = (m' K src, m K src) for one frame (src float or bf16): the pair
+// the single-walk B forward gathers
+template <bool kBf16>
+__global__ void k_thomson_weight2(const void *__restrict__ src,
+                                  const float2 *__restrict__ mf,
+                                  const uint8_t *__restrict__ mm, int64_t n,
+                                  float2 *__restrict__ dst,
+                                  const double *__restrict__ done)
+{
+    if (is_done(done)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool out = mm != nullptr && mm[i] != 0;
+        const float2 m = mf[i];
+        float x;
+        if (kBf16)
+            x = __uint_as_float((unsigned)((const uint16_t *)src)[i] << 16);
+        else
+            x = ((const float *)src)[i];
+        dst[i] = out ? make_float2(0.0f, 0.0f) : make_float2(m.y * x, m.x * x);
+    }
+}
+
+// dst += K (m' a.x - m a.y) for one frame (a: the single-walk B transpose's
+// pair accumulator)
+__global__ void k_thomson_add2(float *__restrict__ dst,
+                               const float2 *__restrict__ a,
+                               const float2 *__restrict__ mf,
+                               const uint8_t *__restrict__ mm, int64_t n,
+                               const double *__restrict__ done)
+{
+    if (is_done(done)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (mm != nullptr && mm[i] != 0) continue;
+        const float2 m = mf[i];
+        const float2 v = a[i];
+        dst[i] += fmaf(m.y, v.x, -m.x * v.y);
+    }
+}
+
 // out = rho^2 y (t == NULL; out may be y), or out = y - rho^2 t
 __global__ void k_rho2_apply(const float *__restrict__ rho2, const float *y,
                              const float *__restrict__ t, float *out,
@@ -196,6 +237,30 @@ cudaError_t launch_thomson_add(float *dst, const float *a, const float *b,
     if (n <= 0 || frames <= 0) return cudaSuccess;
     k_thomson_add<<<grid_for(n), kThreads, 0, s>>>(dst, a, b, mf, mm, n, frames,
                                                    done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thomson_weight2(const void *src, bool bf16,
+                                   const float2 *mf, const uint8_t *mm,
+                                   int64_t n, float2 *dst, const double *done,
+                                   cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (bf16)
+        k_thomson_weight2<true><<<grid_for(n), kThreads, 0, s>>>(src, mf, mm, n,
+                                                                 dst, done);
+    else
+        k_thomson_weight2<false><<<grid_for(n), kThreads, 0, s>>>(src, mf, mm, n,
+                                                                  dst, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thomson_add2(float *dst, const float2 *a, const float2 *mf,
+                                const uint8_t *mm, int64_t n,
+                                const double *done, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_thomson_add2<<<grid_for(n), kThreads, 0, s>>>(dst, a, mf, mm, n, done);
     return cudaGetLastError();
 }
 

@@ -31,13 +31,21 @@ static_assert(sizeof(RayRec) == 32, "RayRec must stay 32 bytes");
 
 struct __align__(16) ImgParam {
     float gain;     // image gain g_n
-    float w;        // weight of frame k + 1
-    int32_t frame;  // k (0 when T == 1)
-    int32_t pad;    // plane-walk hint: bits 0-1 major axis M, bits 2-3
-                    // lateral axis L (the layout), bit 4 M direction < 0,
-                    // bit 5 set when the hint is valid, bit 6 set when the
-                    // plane forward is the faster one (kPlaneFwdBit)
+    float w;        // weight w of frame k + 1
+    float w0;       // weight 1 - w of frame k (formed in FP64: a float
+                    // 1 - w would lose the digits of a w close to 1)
+    int32_t pad;    // bits 0-7 plane-walk hint: bits 0-1 major axis M,
+                    // bits 2-3 lateral axis L (the layout), bit 4 M
+                    // direction < 0, bit 5 set when the hint is valid, bit 6
+                    // set when the plane forward is chosen (kPlaneFwdBit),
+                    // bit 7 every-slab variant (kPlaneGeneralBit); bits
+                    // 8-30 the frame index k (0 when T == 1)
 };
+
+__host__ __device__ __forceinline__ int32_t img_frame(const ImgParam &q)
+{
+    return q.pad >> 8;
+}
 
 constexpr int32_t kPlaneHintValid = 32;
 constexpr int32_t kPlaneMaxSide = 16384;
@@ -67,6 +75,17 @@ constexpr double kPlaneFwdMinPitch = 0.75;
 constexpr double kPlaneFwdMaxRatio = 0.02;
 constexpr int32_t kPlaneGeneralBit = 128;
 constexpr double kPlaneGeneralRatio = 0.035;
+// The thresholds above as walk rules (the default of every size bucket that
+// tomo_autotune or tomo_set_plane_rules has not set).
+inline tomo_plane_rules default_plane_rules()
+{
+    tomo_plane_rules r;
+    r.min_pitch = kPlaneMinPitch;
+    r.fwd_min_pitch = kPlaneFwdMinPitch;
+    r.fwd_max_ratio = kPlaneFwdMaxRatio;
+    r.general_ratio = kPlaneGeneralRatio;
+    return r;
+}
 
 // Cube pointers per layout (0 = native x-fastest, 1 = y-fastest,
 // 2 = z-fastest) for the plane-synchronous walk (plane.cu).
@@ -118,7 +137,7 @@ cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
                           ImgParam *params, double3 vox, unsigned *layout_used,
-                          cudaStream_t s);
+                          const tomo_plane_rules &rules, cudaStream_t s);
 cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
                              const double *tan_v, CubeDev cube, int32_t n_img,
                              int32_t nu, int32_t nv, RayRec *rays,
@@ -255,6 +274,69 @@ cudaError_t launch_thomson_add(float *dst, const float *a, const float *b,
 cudaError_t launch_rho2_apply(const float *rho2, const float *y, const float *t,
                               float *out, int64_t n, const double *done,
                               cudaStream_t s);
+
+// dst[v] = (m' K src, m K src), one frame (the single-walk B forward's pairs)
+cudaError_t launch_thomson_weight2(const void *src, bool bf16,
+                                   const float2 *mf, const uint8_t *mm,
+                                   int64_t n, float2 *dst, const double *done,
+                                   cudaStream_t s);
+// dst += K (m' a.x - m a.y), one frame
+cudaError_t launch_thomson_add2(float *dst, const float2 *a, const float2 *mf,
+                                const uint8_t *mm, int64_t n,
+                                const double *done, cudaStream_t s);
+
+// ---- plane2.cu: two-value plane walks (frame pairs; Thomson B pairs).
+// Pair buffers hold two floats per voxel (8 bytes; a bf16 frame pair packs
+// into 4 bytes), T - 1 frame pairs or one B pair of n voxels, in layout L.
+// Layout passes return at once unless bit `bit` (or bit L) of *used is set.
+cudaError_t launch_to_pairs(const void *cube, tomo_dtype dtype, void *out,
+                            int L, const tomo_cube_geom *c, int32_t n_frames,
+                            const unsigned *used, unsigned bit,
+                            const double *done, int num_sms, cudaStream_t s);
+// frames += pair accumulators of layout L (frame f: pair f's first value and
+// pair f - 1's second)
+cudaError_t launch_add_pairs(const void *acc, float *cube, int L,
+                             const tomo_cube_geom *c, int32_t n_frames,
+                             const unsigned *used, const double *done,
+                             int num_sms, cudaStream_t s);
+// float2 native buffer -> layout L (1 or 2), and native += layout L
+cudaError_t launch_b_to_layout(const void *in, void *out, int L,
+                               const tomo_cube_geom *c, const unsigned *used,
+                               unsigned bit, const double *done,
+                               cudaStream_t s);
+cudaError_t launch_add_b_layout(const void *acc, void *out, int L,
+                                const tomo_cube_geom *c, const unsigned *used,
+                                const double *done, cudaStream_t s);
+cudaError_t launch_forward_plane_pair(const RayRec *rays, const ImgParam *prm,
+                                      PlaneCubes pairs, const void *native,
+                                      tomo_dtype dtype, int64_t fstride,
+                                      const uint8_t *mask, float *out,
+                                      int32_t n_img, int32_t nu, int32_t nv,
+                                      const tomo_cube_geom *c,
+                                      const double *done, cudaStream_t s,
+                                      bool only_marked);
+cudaError_t launch_adjoint_plane_pair(const RayRec *rays, const ImgParam *prm,
+                                      const float *images, const uint8_t *mask,
+                                      PlaneAcc acc, float *cube,
+                                      int64_t fstride, int32_t n_img,
+                                      int32_t nu, int32_t nv,
+                                      const tomo_cube_geom *c,
+                                      const double *done, cudaStream_t s);
+// plane_mode: 0 every image per ray, 1 the images whose hint has the
+// plane-forward bit, 2 every image plane by plane (where the hint allows)
+cudaError_t launch_forward_b(const RayRec *rays, const ImgParam *prm,
+                             PlaneCubes pairs, const float *rho2,
+                             const uint8_t *mask, float *out, int32_t n_img,
+                             int32_t nu, int32_t nv, const tomo_cube_geom *c,
+                             const double *done, int plane_mode,
+                             cudaStream_t s);
+// plane_on false: every image per ray into acc.c[0]
+cudaError_t launch_adjoint_b(const RayRec *rays, const ImgParam *prm,
+                             const float *images, const float *rho2,
+                             const uint8_t *mask, PlaneAcc acc, int32_t n_img,
+                             int32_t nu, int32_t nv, const tomo_cube_geom *c,
+                             const double *done, bool plane_on,
+                             cudaStream_t s);
 
 // ---- mapmask.cu (map mask K = diag(1 - mask), same mask for every frame)
 // dst = K src over `frames` frames of n voxels (float32 or bf16 bits)

@@ -28,6 +28,7 @@ TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3,
 TOMO_OPT_PROFILE = 5
 TOMO_OPT_ADJOINT = 6
 TOMO_OPT_PLANE_SYNC = 7
+TOMO_OPT_CHANNELS = 8
 TOMO_BATCH_AUTOTUNE = 8
 KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector", "layout")
 
@@ -78,15 +79,25 @@ class Problem(C.Structure):
                 ("prior_weight_dev", C.c_void_p)]
 
 
+class PlaneRules(C.Structure):
+    _fields_ = [("min_pitch", C.c_double), ("fwd_min_pitch", C.c_double),
+                ("fwd_max_ratio", C.c_double), ("general_ratio", C.c_double)]
+
+
 class TilingResult(C.Structure):
     _fields_ = [("tile_u", C.c_int32), ("tile_v", C.c_int32),
                 ("warp_u", C.c_int32), ("fwd_ms", C.c_float),
-                ("adj_ms", C.c_float)]
+                ("adj_ms", C.c_float), ("rules", PlaneRules)]
+
+
+RULE_FIELDS = ("min_pitch", "fwd_min_pitch", "fwd_max_ratio", "general_ratio")
+NEVER = 1e30  # a walk-rule threshold that is never reached
 
 
 assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
 assert C.sizeof(ImageGeom) == 24
 assert C.sizeof(Problem) == 160
+assert C.sizeof(PlaneRules) == 32 and C.sizeof(TilingResult) == 56
 
 
 class TomoError(RuntimeError):
@@ -130,6 +141,10 @@ _SIGNATURES = {
                                       C.POINTER(C.c_int64), _VP]),
     "tomo_autotune": (C.c_int, [_VP, C.POINTER(Problem),
                                 C.POINTER(TilingResult), _VP]),
+    "tomo_set_plane_rules": (C.c_int, [_VP, C.POINTER(CubeGeom),
+                                       C.POINTER(ImageGeom),
+                                       C.POINTER(PlaneRules)]),
+    "tomo_walk_plan": (C.c_int, [_VP, C.c_int32, C.POINTER(C.c_int32)]),
     "tomo_project_batched": (C.c_int, [_VP, C.c_int32, C.POINTER(Problem),
                                        _VP]),
     "tomo_backproject_batched": (C.c_int, [_VP, C.c_int32, C.POINTER(Problem),
@@ -578,7 +593,43 @@ def tomo_autotune(cube, images, geom, pointing, mask=None, ctx=None,
                                            _stream_ptr(stream, cube.device)))
     return {"tile_u": best.tile_u, "tile_v": best.tile_v,
             "warp_u": best.warp_u, "fwd_ms": best.fwd_ms,
-            "adj_ms": best.adj_ms}
+            "adj_ms": best.adj_ms,
+            "rules": {f: getattr(best.rules, f) for f in RULE_FIELDS}}
+
+
+def tomo_set_plane_rules(rules=None, geom=None, nu=None, nv=None,
+                         n_img=1, ctx=None):
+    """Walk rules (dict with the keys of ``RULE_FIELDS``; missing keys take
+    the built-in defaults, ``None`` all of them) for the size bucket of
+    ``geom`` and ``nu`` x ``nv`` images, or the context's default when
+    ``geom`` is None."""
+    ctx = _ctx(ctx)
+    r = None
+    if rules is not None:
+        d = {"min_pitch": 0.16, "fwd_min_pitch": 0.75, "fwd_max_ratio": 0.02,
+             "general_ratio": 0.035}
+        unknown = set(rules) - set(RULE_FIELDS)
+        if unknown:
+            raise ValueError("unknown rule(s) %s" % sorted(unknown))
+        d.update(rules)
+        r = PlaneRules(*[float(d[f]) for f in RULE_FIELDS])
+    cg = ig = None
+    if geom is not None:
+        cg = C.byref(cube_geom_struct(geom))
+        ig = C.byref(ImageGeom(int(n_img), int(nu), int(nv)))
+    ctx.check(load_library().tomo_set_plane_rules(
+        ctx.handle, cg, ig, None if r is None else C.byref(r)))
+
+
+def tomo_walk_plan(n_img, ctx=None):
+    """Per image of the context's most recent geometry: the walk code of
+    ``tomo_walk_plan`` (bit 0 plane-synchronous P^T, bit 1 plane P, bit 2
+    every-slab body, bits 3-4 major axis, bits 5-6 lateral axis)."""
+    ctx = _ctx(ctx)
+    out = np.zeros(int(n_img), dtype=np.int32)
+    ctx.check(load_library().tomo_walk_plan(
+        ctx.handle, int(n_img), out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out
 
 
 # short aliases

@@ -60,12 +60,14 @@ def test_struct_layout_matches_header(tmp_path):
 #include <stddef.h>
 #include "tomo.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tomo_cube_geom),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n",
+         sizeof(tomo_cube_geom),
          offsetof(tomo_cube_geom, x0), offsetof(tomo_cube_geom, dz),
          offsetof(tomo_cube_geom, r_obs),
          sizeof(tomo_image_geom), sizeof(tomo_pointing), sizeof(tomo_profile),
          sizeof(tomo_problem), offsetof(tomo_problem, lambda),
-         offsetof(tomo_problem, prior_weight_dev));
+         offsetof(tomo_problem, prior_weight_dev), sizeof(tomo_plane_rules),
+         sizeof(tomo_tiling), offsetof(tomo_tiling, rules));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -77,7 +79,8 @@ int main(void) {
             C.sizeof(tomo.ImageGeom),
             C.sizeof(tomo.Pointing), C.sizeof(tomo.Profile),
             C.sizeof(tomo.Problem), tomo.Problem.lam.offset,
-            tomo.Problem.prior_weight_dev.offset]
+            tomo.Problem.prior_weight_dev.offset, C.sizeof(tomo.PlaneRules),
+            C.sizeof(tomo.TilingResult), tomo.TilingResult.rules.offset]
     assert got == want
 
 
