@@ -383,7 +383,7 @@ struct PlaneScatterOp {
     __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
     __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
     {
-        if (on) red_add(c + idx, len * y);
+        red_add_if(on, c + idx, len * y);
     }
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
@@ -399,10 +399,8 @@ struct PlaneScatterTimeOp {
     __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
     __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
     {
-        if (on) {
-            red_add(c0 + idx, len * y0);
-            red_add(c1 + idx, len * y1);
-        }
+        red_add_if(on, c0 + idx, len * y0);
+        red_add_if(on, c1 + idx, len * y1);
     }
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {

@@ -47,12 +47,16 @@ __device__ __forceinline__ float2 load_pair(const uint32_t *c, int idx)
 }
 
 // Fire-and-forget addition of two adjacent floats (8-byte aligned) in
-// global memory, one vector reduction.
-__device__ __forceinline__ void red_add2(float2 *p, float a, float b)
+// global memory, one vector reduction, under a predicate (see red_add_if).
+__device__ __forceinline__ void red_add2_if(bool on, float2 *p, float a,
+                                            float b)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};"
+    asm volatile("{\n\t.reg .pred q;\n\t"
+                 "setp.ne.b32 q, %3, 0;\n\t"
+                 "@q red.global.add.v2.f32 [%0], {%1, %2};\n\t}"
                  :
-                 : "l"(__cvta_generic_to_global(p)), "f"(a), "f"(b)
+                 : "l"(__cvta_generic_to_global(p)), "f"(a), "f"(b),
+                   "r"((int)on)
                  : "memory");
 }
 
@@ -127,7 +131,7 @@ struct PlaneScatterPairOp {
     __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
     __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
     {
-        if (on) red_add2(c + idx, len * y0, len * y1);
+        red_add2_if(on, c + idx, len * y0, len * y1);
     }
     __device__ __forceinline__ void operator()(bool on, int idx, float len)
     {
@@ -140,7 +144,7 @@ struct ScatterPairOp {
     float y0, y1;
     __device__ __forceinline__ void operator()(int idx, float len)
     {
-        if (len > 0.0f) red_add2(c + idx, len * y0, len * y1);
+        red_add2_if(len > 0.0f, c + idx, len * y0, len * y1);
     }
 };
 

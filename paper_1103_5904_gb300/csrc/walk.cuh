@@ -97,6 +97,19 @@ __device__ __forceinline__ void red_add(float *p, float v)
                  : "memory");
 }
 
+// red_add under a predicate, as one predicated instruction: a lane-varying
+// `if (on) red_add(...)` compiles to a divergent branch around the
+// reduction, which the plane walks would pay for every segment slot.
+__device__ __forceinline__ void red_add_if(bool on, float *p, float v)
+{
+    asm volatile("{\n\t.reg .pred q;\n\t"
+                 "setp.ne.b32 q, %2, 0;\n\t"
+                 "@q red.global.add.f32 [%0], %1;\n\t}"
+                 :
+                 : "l"(__cvta_generic_to_global(p)), "f"(v), "r"((int)on)
+                 : "memory");
+}
+
 __device__ __forceinline__ float load_voxel(const float *c, int idx)
 {
     return __ldg(c + idx);
@@ -162,7 +175,7 @@ struct ScatterOp {
                 }
             }
         }
-        if (v != 0.0f) red_add(c + idx, v);
+        red_add_if(v != 0.0f, c + idx, v);
     }
 };
 
@@ -172,10 +185,8 @@ struct ScatterTimeOp {
     float y0, y1;
     __device__ __forceinline__ void operator()(int idx, float len)
     {
-        if (len > 0.0f) {
-            red_add(c0 + idx, len * y0);
-            red_add(c1 + idx, len * y1);
-        }
+        red_add_if(len > 0.0f, c0 + idx, len * y0);
+        red_add_if(len > 0.0f, c1 + idx, len * y1);
     }
 };
 
