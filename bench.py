@@ -48,6 +48,12 @@ WORKLOAD_TEXT = {
     "single": ("single: cube 128^3 f32; 60 images 256x256, lon 0-177 deg, "
                "lat jitter +-7 deg; 6 streamers; occulter r<1; SNR 50; "
                "lambda 1e-2"),
+    "temporal": ("temporal: 8 frames of 256^3 f32 over [-1.5,1.5]^3 R_sun; "
+                 "240 images 512x512, time stamps U[0,7]; two observer "
+                 "groups 40 deg apart"),
+    "coronagraph": ("coronagraph: cube 512^3 f32 over [-4,4]^3 R_sun; 360 "
+                    "images 1024x1024 from two groups 86 deg apart; occulter "
+                    "r<1.5 and field edge r>4 masks; SNR 30; lambda 1e-2"),
     "batched": ("batched: 32 independent problems (seeds 100-131), cube side "
                 "from {32,48,64,96,128}, 16-120 images of side "
                 "{64,128,256,512}, observers evenly spaced on the ecliptic; "
@@ -300,6 +306,7 @@ def run_gpu(args, rank, local_rank, world):
     dev = torch.device("cuda", local_rank)
     c = make_workload(args.workload, args.images)
     g, ptg, nu, nv = c["geom"], c["pointing"], c["nu"], c["nv"]
+    tf = c.get("n_frames", 1)  # time frames (the temporal workload)
     n_img = ptg.shape[0]
     ctx = T.Context(local_rank)
     if args.adjoint_mode is not None:
@@ -310,11 +317,13 @@ def run_gpu(args, rank, local_rank, world):
     mask = torch.from_numpy(mask_h).to(dev) if mask_h is not None else None
     x_true = torch.from_numpy(c["cube"]).to(dev)
     # data: P x + Gaussian noise (seeded draws, SNR of the workload)
-    y0 = T.tomo_project(x_true, g, ptg, nu, nv, mask=mask, ctx=ctx)
+    y0 = T.tomo_project(x_true, g, ptg, nu, nv, mask=mask, n_frames=tf,
+                        ctx=ctx)
     keep = (mask == 0) if mask is not None else torch.ones_like(y0, dtype=bool)
     rms = torch.sqrt(torch.mean(y0[keep].double() ** 2)).item()
     z = torch.from_numpy(synth.noise_draw(c["noise_seed"] or 0, y0.shape)).to(dev)
     y = (y0.double() + (rms / (c["snr"] or 50.0)) * z).float()
+    lam = c["lam"] or 1e-2
     if mask is not None:
         y[mask != 0] = 0.0
     del z, y0
@@ -328,14 +337,14 @@ def run_gpu(args, rank, local_rank, world):
 
     def step():
         ctx.clear_cache()  # every step redoes the FP64 ray setup
-        T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"], max_iter=args.iters,
-                     out=x, report=False, ctx=ctx)
+        T.tomo_solve(y, g, ptg, mask=mask, lam=lam, max_iter=args.iters,
+                     out=x, report=False, n_frames=tf, ctx=ctx)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    _, info = T.tomo_solve(y, g, ptg, mask=mask, lam=c["lam"],
-                           max_iter=args.iters, out=x, ctx=ctx)
+    _, info = T.tomo_solve(y, g, ptg, mask=mask, lam=lam,
+                           max_iter=args.iters, out=x, n_frames=tf, ctx=ctx)
     ctx.set_option(T.tomo.TOMO_OPT_PROFILE, 1)
     ctx.profile(reset=True)
     clocks = ClockSampler(local_rank)
@@ -396,6 +405,9 @@ def run_gpu(args, rank, local_rank, world):
              "adjoint": ("k_adjoint_plane<false>" if mode == 0 and plane & 1
                          else {0: "k_adjoint<false>", 1: "k_adjoint_window",
                                2: "k_adjoint_tiled"}[mode])}
+    if tf > 1:  # time frames: the frame-pair plane walks
+        kname = {"forward": "k_forward_plane_pair<float,float2>",
+                 "adjoint": "k_adjoint_plane_pair"}
     roofline = {"bound": "hbm", "kernel": kname[dom],
                 "achieved": kern[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
@@ -424,8 +436,9 @@ def run_gpu(args, rank, local_rank, world):
             if m_h is not None:
                 m_d.copy_(m_h, non_blocking=True)
             ctx.clear_cache()
-            T.tomo_solve(y_d, g, ptg, mask=m_d, lam=c["lam"],
-                         max_iter=args.iters, out=x, report=False, ctx=ctx)
+            T.tomo_solve(y_d, g, ptg, mask=m_d, lam=lam,
+                         max_iter=args.iters, out=x, report=False,
+                         n_frames=tf, ctx=ctx)
             x_h.copy_(x, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -678,7 +691,7 @@ def run_extras(ctx, dev, c, y, mask, iters, flush):
                        "P_bf16_ms": tpb,
                        "P_segments_per_s": st / (tp / 1e3),
                        "PT_segments_per_s": st / (ta / 1e3),
-                       "what": WORKLOAD_TEXT_TEMPORAL}
+                       "what": WORKLOAD_TEXT["temporal"]}
     Xg = Xt.clone().requires_grad_(True)
 
     def fwd_bwd():
@@ -696,11 +709,6 @@ def run_extras(ctx, dev, c, y, mask, iters, flush):
     torch.cuda.empty_cache()
     out["batched"] = batched_compare(T, ctx, dev, flush, steps=3, warmup=1)
     return out
-
-
-WORKLOAD_TEXT_TEMPORAL = (
-    "temporal: 8 frames of 256^3 f32 over [-1.5,1.5]^3 R_sun; 240 images "
-    "512x512, time stamps U[0,7]; two observer groups 40 deg apart")
 
 
 def batched_compare(T, ctx, dev, flush, steps, warmup, iters=10):
