@@ -930,6 +930,16 @@ def run_sweep(args, local_rank):
                     ctx=ctx), reps)
                 del yk
             del yo, mm
+        if T_frames == 1:
+            # the autotuner's schedule for this size bucket (tile shape and
+            # walk rules), P and P^T timed again under it
+            best = T.tomo_autotune(X, y, g, ptg, mask=mask, ctx=ctx)
+            line["tuned_rules"] = best["rules"]
+            line["P_tuned_ms"] = med_ms(lambda: T.tomo_project(
+                X, g, ptg, nu, nv, mask=mask, out=y, ctx=ctx), reps)
+            line["PT_tuned_ms"] = med_ms(lambda: T.tomo_backproject(
+                y, g, ptg, mask=mask, out=out, ctx=ctx), reps)
+            T.tomo_set_plane_rules(None, g, nu, nv, ctx=ctx)
         # the oracle on one core and on all host cores (seeded ray sample)
         c_host = dict(c)
         nthreads = siddon.get_threads()

@@ -30,7 +30,11 @@ namespace tomo {
 
 namespace {
 
-constexpr int kPairFwdUnroll = 2;
+// Slabs per iteration of the forward's middle range (loads in flight), as
+// measured on GB300: 8-frame 256^3 temporal P 22.7 ms at 2 slabs, 16.6 ms
+// at 4, 18.6 ms at 6, 20.7 ms at 8 (3 CTAs per SM); Thomson B forward on
+// the 256^3 cube 14.8, 11.6, 12.5, 13.2 ms.
+constexpr int kPairFwdUnroll = 4;
 constexpr int kPairFwdMinBlocks = 4;
 constexpr int kPairAdjMinBlocks = 5;
 
