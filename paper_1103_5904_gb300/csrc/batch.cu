@@ -102,7 +102,7 @@ k_walk_batched(const WalkDesc *__restrict__ descs,
                         GatherOp<float> op;
                         op.c = d.src;
                         op.acc = 0.0f;
-                        siddon_walk(r, d.nx, d.nxny, op);
+                        siddon_gather(r, d.nx, d.nxny, op);
                         y = gain * op.acc;
                     }
                 }
@@ -330,14 +330,14 @@ k_forward_plane_batched(const WalkDesc *__restrict__ descs,
                         GatherOp<float> op2;
                         op2.c = d.src;
                         op2.acc = 0.0f;
-                        siddon_walk(r, d.nx, d.nxny, op2);
+                        siddon_gather(r, d.nx, d.nxny, op2);
                         acc = op2.acc;
                     }
                 } else if (live) {
                     GatherOp<float> op2;
                     op2.c = d.src;
                     op2.acc = 0.0f;
-                    siddon_walk(r, d.nx, d.nxny, op2);
+                    siddon_gather(r, d.nx, d.nxny, op2);
                     acc = op2.acc;
                 }
                 if (in_img) d.dst[id] = q.gain * acc;

@@ -107,7 +107,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
             op2.w0 = op.w0;
             op2.w1 = op.w1;
             op2.acc = 0.0f;
-            siddon_walk(r, nx, nx * ny, op2);
+            siddon_gather(r, nx, nx * ny, op2);
             acc = op2.acc;
         }
     } else {
@@ -120,7 +120,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
             GatherOp<CubeT> op2;
             op2.c = native;
             op2.acc = 0.0f;
-            siddon_walk(r, nx, nx * ny, op2);
+            siddon_gather(r, nx, nx * ny, op2);
             acc = op2.acc;
         }
     }

@@ -120,6 +120,16 @@ struct PlaneGatherBOp {
 struct GatherBOp {
     const float2 *c;
     float s1, s2;
+    using Val = float2;
+    __device__ __forceinline__ float2 fetch(int idx) const
+    {
+        return load_pair(c, idx);
+    }
+    __device__ __forceinline__ void apply(float len, float2 v)
+    {
+        s1 = fmaf(len, v.x, s1);
+        s2 = fmaf(len, v.y, s2);
+    }
     __device__ __forceinline__ void operator()(int idx, float len)
     {
         const float2 v = load_pair(c, idx);
@@ -195,7 +205,7 @@ k_forward_plane_pair(const RayRec *__restrict__ rays,
         op2.w0 = op.w0;
         op2.w1 = op.w1;
         op2.acc = 0.0f;
-        siddon_walk(r, nx, nx * ny, op2);
+        siddon_gather(r, nx, nx * ny, op2);
         acc = op2.acc;
     }
     if (in_img) out[id] = q.gain * acc;
@@ -243,7 +253,7 @@ k_forward_b(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
         op2.c = static_cast<const float2 *>(pairs.c[0]);
         op2.s1 = 0.0f;
         op2.s2 = 0.0f;
-        siddon_walk(r, nx, nx * ny, op2);
+        siddon_gather(r, nx, nx * ny, op2);
         s1 = op2.s1;
         s2 = op2.s2;
     }

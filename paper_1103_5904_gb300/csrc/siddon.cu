@@ -46,13 +46,13 @@ k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
                 op.w0 = q.w0;
                 op.w1 = q.w;
                 op.acc = 0.0f;
-                siddon_walk(r, nx, nxny, op);
+                siddon_gather(r, nx, nxny, op);
                 y = q.gain * op.acc;
             } else {
                 GatherOp<CubeT> op;
                 op.c = cube;
                 op.acc = 0.0f;
-                siddon_walk(r, nx, nxny, op);
+                siddon_gather(r, nx, nxny, op);
                 y = q.gain * op.acc;
             }
         }

@@ -82,6 +82,52 @@ __device__ __forceinline__ void siddon_walk(const RayRec &r, int nx, int nxny,
     }
 }
 
+// siddon_walk for gathering ops, with the load of each segment's voxel
+// issued before the previous segment's product is added: op.fetch(idx)
+// loads, op.apply(len, v) adds.  Same segments and the same order of
+// additions as siddon_walk (so the same sums, bit for bit); one load is
+// always in flight while the walk computes the next crossing.
+template <class Op>
+__device__ __forceinline__ void siddon_gather(const RayRec &r, int nx, int nxny,
+                                              Op &op)
+{
+    const float chord = r.chord;
+    const float ax = fabsf(r.dtx), ay = fabsf(r.dty), az = fabsf(r.dtz);
+    const int sx = signbit(r.dtx) ? -1 : 1;
+    const int sy = signbit(r.dty) ? -nx : nx;
+    const int sz = signbit(r.dtz) ? -nxny : nxny;
+    float kx = 0.0f, ky = 0.0f, kz = 0.0f;
+    float tx = r.t0x, ty = r.t0y, tz = r.t0z;
+    int idx = r.idx0;
+    float tm = fminf(tx, fminf(ty, tz));
+    float te = fminf(tm, chord);
+    typename Op::Val v = op.fetch(idx);
+    float len = te;
+    while (te < chord) {
+        const float t = te;
+        if (tx == tm) {
+            kx += 1.0f;
+            tx = fmaf(kx, ax, r.t0x);
+            idx += sx;
+        } else if (ty == tm) {
+            ky += 1.0f;
+            ty = fmaf(ky, ay, r.t0y);
+            idx += sy;
+        } else {
+            kz += 1.0f;
+            tz = fmaf(kz, az, r.t0z);
+            idx += sz;
+        }
+        tm = fminf(tx, fminf(ty, tz));
+        te = fminf(tm, chord);
+        const typename Op::Val vn = op.fetch(idx);
+        op.apply(len, v);
+        v = vn;
+        len = te - t;
+    }
+    op.apply(len, v);
+}
+
 // Fire-and-forget float addition into global memory (PTX red.global).
 // atomicAdd through a pointer whose address space the compiler cannot infer
 // (one read from a descriptor in global memory, as in the batched kernels)
@@ -125,6 +171,15 @@ template <typename CubeT>
 struct GatherOp {
     const CubeT *c;
     float acc;
+    using Val = float;
+    __device__ __forceinline__ float fetch(int idx) const
+    {
+        return load_voxel(c, idx);
+    }
+    __device__ __forceinline__ void apply(float len, float v)
+    {
+        acc = fmaf(len, v, acc);
+    }
     __device__ __forceinline__ void operator()(int idx, float len)
     {
         acc = fmaf(len, load_voxel(c, idx), acc);
@@ -136,6 +191,15 @@ struct GatherTimeOp {
     const CubeT *c0;
     const CubeT *c1;
     float w0, w1, acc;
+    using Val = float2;
+    __device__ __forceinline__ float2 fetch(int idx) const
+    {
+        return make_float2(load_voxel(c0, idx), load_voxel(c1, idx));
+    }
+    __device__ __forceinline__ void apply(float len, float2 v)
+    {
+        acc = fmaf(len, fmaf(w0, v.x, w1 * v.y), acc);
+    }
     __device__ __forceinline__ void operator()(int idx, float len)
     {
         const float v = fmaf(w0, load_voxel(c0, idx), w1 * load_voxel(c1, idx));
