@@ -271,3 +271,66 @@ def test_backproject_batched_layouts_1_and_2_in_one_problem(T):
     cw = siddon.crossing_weights(g, y, ptg, 37, 41)
     assert_transpose_close(dp[0]["cube"].cpu().numpy(), want, cw, g,
                            "batched P^T layouts 1 + 2")
+
+
+def test_full_batched_workload_against_single_calls_and_oracle(T):
+    """The whole 32-problem batched workload (cubes 32-128^3, 16-120 images
+    of 64-512^2): the batched forward equals the single-problem forward bit
+    for bit on every problem; the batched transpose agrees with the
+    single-problem transpose on every voxel of every problem, and with the
+    FP64 oracle per voxel on four problems (the largest images among them);
+    10 graph-replayed CG iterations match the sequential solver."""
+    ctx = T.Context()
+    confs = synth.configs.batched()
+    probs, ims, singles = [], [], []
+    rng = np.random.default_rng(3232)
+    for c in confs:
+        cube = to_dev(c["cube"])
+        n_img = c["pointing"].shape[0]
+        probs.append({"geom": c["geom"], "pointing": c["pointing"],
+                      "nu": c["nu"], "nv": c["nv"], "cube": cube,
+                      "images": torch.zeros((n_img, c["nv"], c["nu"]),
+                                            device="cuda"),
+                      "lam": c["lam"]})
+        ims.append(rng.random((n_img, c["nv"], c["nu"])).astype(np.float32))
+    T.tomo_project_batched(probs, ctx=ctx)
+    for p in probs:
+        single = T.tomo_project(p["cube"], p["geom"], p["pointing"], p["nu"],
+                                p["nv"], ctx=ctx)
+        assert torch.equal(p["images"], single)
+    adj = [dict(p, images=to_dev(y), cube=torch.zeros_like(p["cube"]))
+           for p, y in zip(probs, ims)]
+    T.tomo_backproject_batched(adj, ctx=ctx)
+    for p, d, y in zip(probs, adj, ims):
+        single = T.tomo_backproject(d["images"], p["geom"], p["pointing"],
+                                    ctx=ctx)
+        torch.testing.assert_close(d["cube"], single, rtol=1e-5,
+                                   atol=1e-6 * float(single.abs().max()))
+    # oracle per voxel: the two problems with the largest images and two
+    # with the largest cubes
+    by_px = sorted(range(len(confs)), key=lambda i: -confs[i]["nu"])
+    by_vox = sorted(range(len(confs)), key=lambda i: -confs[i]["geom"]["nx"])
+    pick = []
+    for i in by_px[:2] + by_vox:
+        if i not in pick:
+            pick.append(i)
+        if len(pick) == 4:
+            break
+    for i in pick:
+        c, y = confs[i], ims[i]
+        want = siddon.backproject(c["geom"], y, c["pointing"], c["nu"], c["nv"])
+        cw = siddon.crossing_weights(c["geom"], y, c["pointing"], c["nu"],
+                                     c["nv"])
+        assert_transpose_close(adj[i]["cube"].cpu().numpy(), want, cw,
+                               c["geom"], "batched P^T full workload %d" % i)
+    # CG: data = the batched forward of the cube
+    cg = [dict(p, cube=torch.zeros_like(p["cube"])) for p in probs]
+    infos = T.tomo_solve_batched(cg, 10, ctx=ctx)
+    for p, d, info in zip(probs, cg, infos):
+        x_seq, inf_seq = T.tomo_solve(p["images"], p["geom"], p["pointing"],
+                                      lam=p["lam"], max_iter=10, ctx=ctx)
+        np.testing.assert_allclose(info["J"], inf_seq["J"], rtol=1e-3)
+        rel = float(torch.linalg.norm(d["cube"] - x_seq) /
+                    torch.linalg.norm(x_seq))
+        assert rel <= 1e-3, rel
+    ctx.close()
