@@ -416,13 +416,17 @@ tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
 /* Sets the walk rules of a size bucket (cube voxel counts and image size,
  * both non-NULL), or the context's default for buckets without their own
  * (cube and img NULL).  rules NULL: the built-in defaults.  Takes effect at
- * the next call on a geometry of that bucket. */
+ * the next call on a geometry of that bucket.  A schedule control with no
+ * counterpart in the paper: every walk it selects computes the same
+ * operator (Section 3.3.1, Eq. lo).  Returns TOMO_ERR_ARG for a negative or
+ * NaN threshold, or for only one of cube / img given. */
 tomo_status tomo_set_plane_rules(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                  const tomo_image_geom *img,
                                  const tomo_plane_rules *rules);
 
 /* The walk chosen for each image of the most recent single-problem
- * geometry (synchronises the legacy default stream):
+ * geometry (a report of the schedule, no counterpart in the paper;
+ * synchronises the legacy default stream):
  *   bit 0: P^T (and P when bit 1) walk plane by plane (else per ray)
  *   bit 1: P walks plane by plane
  *   bit 2: the plane walks cross every slab with the general body
