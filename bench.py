@@ -81,9 +81,6 @@ def parse_args(argv=None):
                     help="walk of P / P^T (TOMO_OPT_PLANE_SYNC bit mask: "
                          "bit 0 P^T, bit 1 P on every image, bit 2 P on the "
                          "images where it is faster; library default 5)")
-    ap.add_argument("--adjoint-mode", type=int, default=None,
-                    help="transpose kernel (TOMO_OPT_ADJOINT): 0 float "
-                         "atomics, 1 bundle window, 2 voxel tiles")
     ap.add_argument("--sweep", action="store_true",
                     help="measurement table instead of the benchmark line: "
                          "P, P^T (f32 / bf16), CG s/iter and the oracle's "
@@ -309,8 +306,6 @@ def run_gpu(args, rank, local_rank, world):
     tf = c.get("n_frames", 1)  # time frames (the temporal workload)
     n_img = ptg.shape[0]
     ctx = T.Context(local_rank)
-    if args.adjoint_mode is not None:
-        ctx.set_option(T.tomo.TOMO_OPT_ADJOINT, args.adjoint_mode)
     if args.plane_sync is not None:
         ctx.set_option(T.tomo.TOMO_OPT_PLANE_SYNC, args.plane_sync)
     mask_h = c["mask"]
@@ -398,13 +393,11 @@ def run_gpu(args, rank, local_rank, world):
                               "uses their layout)"}
     peak, peak_src = peak_hbm()
     plane = 5 if args.plane_sync is None else args.plane_sync
-    mode = args.adjoint_mode or 0
     kname = {"forward": ("k_forward_plane<float,false>" if plane & 2 else
                          "k_forward<float,false>+k_forward_plane<float,false>"
                          if plane & 4 else "k_forward<float,false>"),
-             "adjoint": ("k_adjoint_plane<false>" if mode == 0 and plane & 1
-                         else {0: "k_adjoint<false>", 1: "k_adjoint_window",
-                               2: "k_adjoint_tiled"}[mode])}
+             "adjoint": ("k_adjoint_plane<false>" if plane & 1
+                         else "k_adjoint<false>")}
     if tf > 1:  # time frames: the frame-pair plane walks
         kname = {"forward": "k_forward_plane_pair<float,float2>",
                  "adjoint": "k_adjoint_plane_pair"}

@@ -133,17 +133,11 @@ typedef struct tomo_ctx tomo_ctx;
 #define TOMO_OPT_TILE_V     3  /* pixel tile height of one CTA (default 8) */
 #define TOMO_OPT_WARP_U     4  /* pixel tile width of one warp (default 8) */
 #define TOMO_OPT_PROFILE    5  /* 1: time every kernel launch with CUDA events */
-#define TOMO_OPT_ADJOINT    6  /* transpose kernel: 0 (default) adds every
-                                  segment with a float atomic; 1 accumulates
-                                  each ray bundle in a shared-memory window
-                                  first; 2 gives every 16^3 voxel tile to one
-                                  CTA that walks the rays crossing it (no
-                                  global atomics).  Time-interpolated
-                                  transposes always use 0, and 1 needs tiles
-                                  of 256 pixels. */
+/* (option 6 is not used: it chose among transpose kernels that were
+ * measured slower and removed) */
 #define TOMO_OPT_PLANE_SYNC 7  /* bit mask (default 5) choosing the Siddon
                                   walk of single-problem calls: bit 0 for
-                                  P^T (with TOMO_OPT_ADJOINT 0); bit 1 for P
+                                  P^T; bit 1 for P
                                   on every image; bit 2 for P on the images
                                   where it measured faster: views within
                                   ~1 degree of a cube-axis plane, or pixels

@@ -301,28 +301,6 @@ tomo_plane_rules rules_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
     return ctx->rules;
 }
 
-cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
-                        const ImgParam *prm, const Frame *frames,
-                        const tomo_pointing *ptg, const float *images,
-                        const uint8_t *mask, float *cube,
-                        const tomo_cube_geom *c, int32_t n_frames,
-                        const tomo_image_geom *g, Tiling t, const double *done,
-                        cudaStream_t s)
-{
-    if (ctx->adjoint_mode == 2 && n_frames == 1)
-        return launch_adjoint_tiled(rays, prm, frames, ptg, images, mask, cube,
-                                    cube_dev(c), g->n_img, g->nu, g->nv, done,
-                                    s);
-    if (ctx->adjoint_mode == 1 && n_frames == 1 && adjoint_window_supported(t))
-        return launch_adjoint_window(rays, prm, images, mask, cube, g->n_img,
-                                     g->nu, g->nv, c->nx, c->ny, c->nz, t,
-                                     done, s);
-    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
-    return launch_adjoint(rays, prm, images, mask, cube, fstride, n_frames > 1,
-                          g->n_img, g->nu, g->nv, c->nx, c->nx * c->ny, t,
-                          done, s);
-}
-
 // The device's rules (setup.cu) evaluated from the boresight, with margins
 // towards "may"; the pixel pitch with the smallest voxel side.
 bool plane_estimate(const tomo_pointing &p, const tomo_cube_geom *c,
@@ -350,7 +328,6 @@ bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
                bool forward)
 {
     const int bits = forward ? (2 | 4) : 1;
-    if (!forward && ctx->adjoint_mode != 0) return false;
     (void)t;
     return (ctx->plane_sync & bits) != 0 && plane_supported(c);
 }
@@ -502,10 +479,11 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                launch_add_from_layout(a2, cube, 2, c, n_frames, used, done, s));
         return TOMO_OK;
     }
+    const int64_t fstride = (int64_t)c->nx * c->ny * c->nz;
     LAUNCH(ctx, TOMO_K_ADJOINT, s,
-           run_adjoint(ctx, rays, prm, (const Frame *)ctx->frames.p,
-                       (const tomo_pointing *)ctx->ptg.p, images, mask, cube,
-                       c, n_frames, g, t, done, s));
+           launch_adjoint(rays, prm, images, mask, cube, fstride, n_frames > 1,
+                          g->n_img, g->nu, g->nv, c->nx, c->nx * c->ny, t,
+                          done, s));
     return TOMO_OK;
 }
 
@@ -792,10 +770,6 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
         return TOMO_OK;
     case TOMO_OPT_PROFILE:
         ctx->profile = value != 0;
-        return TOMO_OK;
-    case TOMO_OPT_ADJOINT:
-        if (value < 0 || value > 2) break;
-        ctx->adjoint_mode = (int)value;
         return TOMO_OK;
     case TOMO_OPT_PLANE_SYNC:
         if (value < 0 || value > 7) break;

@@ -364,11 +364,11 @@ std::vector<LayoutJob> layout_jobs(const BatchPlan *P, int32_t n,
     return jobs;
 }
 
-// Plane-synchronous transposes for this batch: enabled for P^T, float
+// Plane-synchronous transposes for this batch: enabled for P^T
 // atomics mode, and every cube within the plane walk's limits.
 bool batch_plane(const tomo_ctx *ctx, int32_t n, const tomo_problem *probs)
 {
-    if (!(ctx->plane_sync & 1) || ctx->adjoint_mode != 0) return false;
+    if (!(ctx->plane_sync & 1)) return false;
     for (int32_t i = 0; i < n; ++i)
         if (!plane_supported(&probs[i].cube)) return false;
     return true;

@@ -39,7 +39,6 @@ struct tomo_ctx {
     int num_sms = 0;
     char err[512] = { 0 };
     bool ray_cache = true;
-    int adjoint_mode = 0;  // 0: float atomics; 1: bundle window; 2: tiles
     // bit 0: P^T plane-synchronous; bit 1: P plane-synchronous for every
     // image; bit 2: P plane-synchronous for the images whose hint marks it
     // as the faster walk (coarse pixels), per ray for the others
@@ -117,15 +116,6 @@ Tiling tiling_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
 tomo_plane_rules rules_for(const tomo_ctx *ctx, const tomo_cube_geom *c,
                            const tomo_image_geom *g);
 void free_plan(tomo_ctx *ctx);
-// Launches the transpose of one problem with the context's adjoint mode
-// (windowed when possible, plain atomics otherwise).
-cudaError_t run_adjoint(const tomo_ctx *ctx, const RayRec *rays,
-                        const ImgParam *prm, const Frame *frames,
-                        const tomo_pointing *ptg, const float *images,
-                        const uint8_t *mask, float *cube,
-                        const tomo_cube_geom *c, int32_t n_frames,
-                        const tomo_image_geom *g, Tiling t, const double *done,
-                        cudaStream_t s);
 // Single-problem P and P^T with the context's walk: plane-synchronous
 // (layout copies + plane kernels) when enabled and supported, else the
 // per-ray kernels.  ensure_plane must have succeeded for the problem first.

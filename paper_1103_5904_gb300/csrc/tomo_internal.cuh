@@ -159,23 +159,6 @@ cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
                            bool time_interp, int32_t n_img, int32_t nu,
                            int32_t nv, int32_t nx, int32_t nxny, Tiling t,
                            const double *done, cudaStream_t s);
-// adjoint_window.cu: transpose with per-bundle shared-memory accumulation
-// (static frames only; the CTA must have 256 threads)
-bool adjoint_window_supported(Tiling t);
-cudaError_t launch_adjoint_window(const RayRec *rays, const ImgParam *prm,
-                                  const float *images, const uint8_t *mask,
-                                  float *cube, int32_t n_img, int32_t nu,
-                                  int32_t nv, int32_t nx, int32_t ny,
-                                  int32_t nz, Tiling t, const double *done,
-                                  cudaStream_t s);
-// adjoint_tiled.cu: transpose with one CTA per cube tile, no global atomics
-// (static frames only)
-cudaError_t launch_adjoint_tiled(const RayRec *rays, const ImgParam *prm,
-                                 const Frame *frames, const tomo_pointing *ptg,
-                                 const float *images, const uint8_t *mask,
-                                 float *cube, CubeDev c, int32_t n_img,
-                                 int32_t nu, int32_t nv, const double *done,
-                                 cudaStream_t s);
 // plane.cu: plane-synchronous walk on lateral-axis-fastest cube copies.
 // The walk kernels use their own tiling: CTAs of 32 x 8 pixels, one image
 // row of 32 pixels per warp.  Layout kernels return at once unless bit L of

@@ -26,7 +26,6 @@ TOMO_F32, TOMO_BF16 = 0, 1
 TOMO_ACCUMULATE, TOMO_SOLVE_X0, TOMO_SOLVE_BF16 = 1, 2, 4
 TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3, 4
 TOMO_OPT_PROFILE = 5
-TOMO_OPT_ADJOINT = 6
 TOMO_OPT_PLANE_SYNC = 7
 TOMO_OPT_CHANNELS = 8
 TOMO_BATCH_AUTOTUNE = 8

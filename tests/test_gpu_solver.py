@@ -157,16 +157,16 @@ def test_cg_bf16_direction_reaches_same_residual(T):
     assert i16["J"][-1] < i32["J"][30]
 
 
-def test_cg_with_tiled_transpose(T):
-    """The solver on the voxel-tile transpose matches FP64 CG like the
-    atomic one."""
+def test_cg_with_per_ray_walks(T):
+    """The solver on the per-ray walks (TOMO_OPT_PLANE_SYNC 0) matches FP64
+    CG like the default plane-synchronous ones."""
     c = synth.make_config("single", scale=2)
     y = _data(c)
     pb = solver.Problem(c["geom"], c["pointing"], c["nu"], c["nv"], y,
                         c["mask"], lam=c["lam"])
     x_o, rep_o = solver.cg(pb, 10)
     ctx = T.Context()
-    ctx.set_option(T.tomo.TOMO_OPT_ADJOINT, 2)
+    ctx.set_option(T.tomo.TOMO_OPT_PLANE_SYNC, 0)
     x_g, info = T.tomo_solve(to_dev(y), c["geom"], c["pointing"],
                              mask=mask_dev(c["mask"]), lam=c["lam"],
                              max_iter=10, ctx=ctx)
