@@ -407,6 +407,20 @@ def run_gpu(args, rank, local_rank, world):
                 "traffic": ncu_traffic(kname[dom]),
                 "peak_source": peak_src + " HBM copy bandwidth",
                 "bytes_model": "4 B/segment + 37 B/live ray + 1 B/pixel"}
+    if dom == "adjoint":
+        # the transpose read-modify-write model: 8 B per segment (each
+        # reduction reads and writes its voxel), same per-ray bytes
+        per_launch_s = kern["adjoint"]["ms_per_projection"] / 1e3
+        rmw = (algorithmic_bytes(n_rays, n_live, segments, "adjoint") +
+               4.0 * segments)
+        roofline["achieved_rmw"] = rmw / per_launch_s / 1e9
+        roofline["frac_rmw"] = roofline["achieved_rmw"] / peak
+    # compulsory bytes of one projection: the cube and the images once (and
+    # the mask), far below the gather model
+    comp = 4.0 * x_true.numel() + 4.0 * n_rays + (n_rays if mask is not None
+                                                 else 0)
+    roofline["compulsory_bytes"] = comp
+    roofline["compulsory_ms_at_peak"] = comp / (peak * 1e9) * 1e3
     launches = int(sum(v[0] for v in prof.values()))
 
     # end to end through the C ABI with host buffers: H2D of y and mask from
