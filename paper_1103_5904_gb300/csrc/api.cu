@@ -329,7 +329,7 @@ bool use_plane(const tomo_ctx *ctx, const tomo_cube_geom *c, Tiling t,
 {
     const int bits = forward ? (2 | 4) : 1;
     (void)t;
-    return (ctx->plane_sync & bits) != 0 && plane_supported(c);
+    return (ctx->plane_sync & bits) != 0 && plane_supported(c, 4);
 }
 
 tomo_status ensure_plane(tomo_ctx *ctx, const tomo_cube_geom *c,
@@ -358,9 +358,10 @@ tomo_status ensure_pairs(tomo_ctx *ctx, const tomo_cube_geom *c,
     return TOMO_OK;
 }
 
-bool use_time_pairs(const tomo_ctx *ctx, int32_t n_frames)
+bool use_time_pairs(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                    int32_t n_frames)
 {
-    return n_frames > 1 && (ctx->channels & 1);
+    return n_frames > 1 && (ctx->channels & 1) && plane_supported(c, 8);
 }
 
 tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
@@ -375,7 +376,7 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
     // hint marks the plane forward as faster, the rest per ray
     const bool all = (ctx->plane_sync & 2) != 0;
     if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible) &&
-        use_time_pairs(ctx, n_frames)) {
+        use_time_pairs(ctx, c, n_frames)) {
         // frame pairs side by side in every layout in use (layout 0 too)
         tomo_status st;
         if ((st = ensure_pairs(ctx, c, n_frames))) return st;
@@ -434,7 +435,7 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
     const RayRec *rays = (const RayRec *)ctx->rays.p;
     const ImgParam *prm = (const ImgParam *)ctx->params.p;
     if (use_plane(ctx, c, t, false) && ctx->plane_possible &&
-        use_time_pairs(ctx, n_frames)) {
+        use_time_pairs(ctx, c, n_frames)) {
         // frame-pair accumulators in every layout in use, added into the
         // frames after the walk
         tomo_status st;
@@ -534,6 +535,7 @@ tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
                                       (float2 *)ctx->pr[0].p, done, s));
         const bool all = (ctx->plane_sync & 2) != 0;
         const bool plane = use_plane(ctx, c, t, true) &&
+                           plane_supported(c, 8) &&
                            (all || ctx->fwd_plane_possible);
         if (plane) {
             const unsigned *used = (const unsigned *)ctx->layout_used.p;
@@ -598,7 +600,8 @@ tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
         // one walk scattering (g y, rho^2 g y) into pair accumulators, then
         // dst += K (m' a - m b)
         if ((st = ensure_pairs(ctx, c, 1))) return st;
-        const bool plane = use_plane(ctx, c, t, false) && ctx->plane_possible;
+        const bool plane = use_plane(ctx, c, t, false) &&
+                           plane_supported(c, 8) && ctx->plane_possible;
         const unsigned *used = (const unsigned *)ctx->layout_used.p;
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->pr[0].p, 0, 8 * (size_t)n, s));
         if (plane)

@@ -174,7 +174,8 @@ k_adjoint_plane_batched(const WalkDesc *__restrict__ descs,
                 const bool live = r.chord > 0.0f;
                 PlaneRay pr;
                 const bool regular =
-                    live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr);
+                    live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr,
+                                         sizeof(float));
                 const int L = (q.pad >> 2) & 3;
                 PlaneScatterOp op;
                 op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.dst);
@@ -319,7 +320,8 @@ k_forward_plane_batched(const WalkDesc *__restrict__ descs,
                 if (q.pad & kPlaneFwdBit) {
                     PlaneRay pr;
                     const bool regular =
-                        live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr);
+                        live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr,
+                                         sizeof(float));
                     const int L = (q.pad >> 2) & 3;
                     PlaneGatherOp<float> op;
                     op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.src);

@@ -370,7 +370,7 @@ bool batch_plane(const tomo_ctx *ctx, int32_t n, const tomo_problem *probs)
 {
     if (!(ctx->plane_sync & 1)) return false;
     for (int32_t i = 0; i < n; ++i)
-        if (!plane_supported(&probs[i].cube)) return false;
+        if (!plane_supported(&probs[i].cube, 4)) return false;
     return true;
 }
 
@@ -381,7 +381,7 @@ bool batch_plane_forward(const tomo_ctx *ctx, int32_t n, const tomo_problem *pro
 {
     if (!(ctx->plane_sync & (2 | 4))) return false;
     for (int32_t i = 0; i < n; ++i)
-        if (!plane_supported(&probs[i].cube)) return false;
+        if (!plane_supported(&probs[i].cube, 4)) return false;
     return true;
 }
 

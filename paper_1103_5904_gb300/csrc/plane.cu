@@ -84,7 +84,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
     if (in_img && (mask == nullptr || mask[id] == 0)) r = load_ray(rays + id);
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(CubeT));
     const int L = (q.pad >> 2) & 3;
     const CubeT *native = static_cast<const CubeT *>(cubes.c[0]);
     const CubeT *lay = static_cast<const CubeT *>(
@@ -151,7 +151,7 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
     }
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(float));
     const int L = (q.pad >> 2) & 3;
     float *lay = L == 1 ? acc.c[1] : (L == 2 ? acc.c[2] : acc.c[0]);
     const int64_t f0 = kTime ? (int64_t)img_frame(q) * frame_stride : 0;
@@ -297,11 +297,14 @@ dim3 layout_grid(const LayoutMap &m)
 
 }  // namespace
 
-bool plane_supported(const tomo_cube_geom *c)
+bool plane_supported(const tomo_cube_geom *c, int esize)
 {
-    // layout copies index (x, b) tiles with a grid of at most 65535 in y and z
+    // layout copies index (x, b) tiles with a grid of at most 65535 in y and
+    // z; the walk addresses one buffer of esize-byte voxels with 32-bit byte
+    // offsets
+    const uint64_t bytes = (uint64_t)c->nx * c->ny * c->nz * (uint64_t)esize;
     return c->nx <= kPlaneMaxSide && c->ny <= kPlaneMaxSide &&
-           c->nz <= kPlaneMaxSide;
+           c->nz <= kPlaneMaxSide && bytes <= (1ull << 32);
 }
 
 cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,

@@ -7,20 +7,37 @@
 #include <limits.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "walk.cuh"
 
 namespace tomo {
 
 // One ray, re-expressed for the plane walk: M first, then the two minor
 // axes, a1 the one with the smaller crossing spacing (crossed more often).
+// Voxel positions are byte offsets from the walked buffer's base, held as
+// unsigned 32-bit numbers (a step in the negative direction adds the
+// stride's two's complement, which wraps to the right offset); a gather or
+// reduction then needs no 64-bit index arithmetic, only the base plus a
+// 32-bit offset.  The walked buffer (one cube or one frame pair of it) must
+// therefore span at most 2^32 bytes: plane_supported() checks that.
 struct PlaneRay {
     float t0M, t01, t02;  // first crossings
     float AM, A1, A2;     // crossing spacings
     float chord;
-    int sM, s1, s2;       // signed strides in the image's layout
-    int idx;              // entry voxel in the image's layout
+    uint32_t sM, s1, s2;  // signed strides in the image's layout, in bytes
+    uint32_t idx;         // entry voxel in the image's layout, in bytes
     int key;              // entry M coordinate, signed by the M direction
 };
+
+// base + off bytes (off: a plane-walk voxel offset)
+template <typename T>
+__device__ __forceinline__ T *byte_at(T *base, uint32_t off)
+{
+    using B = typename std::conditional<std::is_const<T>::value, const char,
+                                        char>::type;
+    return reinterpret_cast<T *>(reinterpret_cast<B *>(base) + off);
+}
 
 __device__ __forceinline__ void layout_strides(int L, int nx, int ny, int nz,
                                                int &stx, int &sty, int &stz)
@@ -40,9 +57,11 @@ __device__ __forceinline__ void layout_strides(int L, int nx, int ny, int nz,
     }
 }
 
-// Fills p and returns true when the ray fits the plane walk of its image.
+// Fills p and returns true when the ray fits the plane walk of its image;
+// esize is the size in bytes of one voxel of the walked buffer.
 __device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
-                                          int ny, int nz, PlaneRay &p)
+                                          int ny, int nz, PlaneRay &p,
+                                          uint32_t esize)
 {
     if (!(hint & kPlaneHintValid)) return false;
     const int M = hint & 3, L = (hint >> 2) & 3;
@@ -50,11 +69,13 @@ __device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
     const int cx = r.idx0 % nx;
     const int rest = r.idx0 / nx;
     const int cy = rest % ny, cz = rest / ny;
-    int stx, sty, stz;
-    layout_strides(L, nx, ny, nz, stx, sty, stz);
-    const int gx = signbit(r.dtx) ? -stx : stx;
-    const int gy = signbit(r.dty) ? -sty : sty;
-    const int gz = signbit(r.dtz) ? -stz : stz;
+    int lx, ly, lz;
+    layout_strides(L, nx, ny, nz, lx, ly, lz);
+    const uint32_t stx = (uint32_t)lx * esize, sty = (uint32_t)ly * esize,
+                   stz = (uint32_t)lz * esize;
+    const uint32_t gx = signbit(r.dtx) ? 0u - stx : stx;
+    const uint32_t gy = signbit(r.dty) ? 0u - sty : sty;
+    const uint32_t gz = signbit(r.dtz) ? 0u - stz : stz;
     const float dM = M == 0 ? r.dtx : (M == 1 ? r.dty : r.dtz);
     p.t0M = M == 0 ? r.t0x : (M == 1 ? r.t0y : r.t0z);
     p.t01 = M == 0 ? r.t0y : r.t0x;
@@ -73,12 +94,12 @@ __device__ __forceinline__ bool plane_ray(const RayRec &r, int hint, int nx,
         f = p.A1;
         p.A1 = p.A2;
         p.A2 = f;
-        const int g = p.s1;
+        const uint32_t g = p.s1;
         p.s1 = p.s2;
         p.s2 = g;
     }
     p.chord = r.chord;
-    p.idx = cx * stx + cy * sty + cz * stz;
+    p.idx = (uint32_t)cx * stx + (uint32_t)cy * sty + (uint32_t)cz * stz;
     const int cM = M == 0 ? cx : (M == 1 ? cy : cz);
     p.key = neg ? -cM : cM;
     // Two crossings of a minor axis in one slab need its crossing spacing,
@@ -116,14 +137,14 @@ __device__ __forceinline__ int slab_past(float AM, float t0M, float x, bool reac
 // t1, t2 of the two minor axes and their crossing counts, current voxel.
 struct PlaneState {
     float t, t1, t2, k1, k2;
-    int idx;
+    uint32_t idx;
 };
 
 // The fast slab body: at most one crossing, of a1, inside the slab that ends
 // at te.  Emits two segment slots; `go` says whether the lane walks this slab.
-__device__ __forceinline__ void slab_fast(const PlaneRay &p, int sM, PlaneState &s,
-                                          bool go, float te, bool *o, int *id,
-                                          float *ln)
+__device__ __forceinline__ void slab_fast(const PlaneRay &p, uint32_t sM,
+                                          PlaneState &s, bool go, float te,
+                                          bool *o, uint32_t *id, float *ln)
 {
     const bool c1 = go && s.t1 < te;
     o[0] = go;
@@ -134,20 +155,20 @@ __device__ __forceinline__ void slab_fast(const PlaneRay &p, int sM, PlaneState 
     ln[1] = te - s.t1;
     s.k1 = c1 ? s.k1 + 1.0f : s.k1;
     s.t1 = c1 ? fmaf(s.k1, p.A1, p.t01) : s.t1;
-    s.idx += (c1 ? p.s1 : 0) + (go ? sM : 0);
+    s.idx += (c1 ? p.s1 : 0u) + (go ? sM : 0u);
     s.t = go ? te : s.t;
 }
 
 // The general slab body: up to one crossing of each minor axis, in either
 // order.  Emits three segment slots.
-__device__ __forceinline__ void slab_general(const PlaneRay &p, int sM,
+__device__ __forceinline__ void slab_general(const PlaneRay &p, uint32_t sM,
                                              PlaneState &s, bool go, float te,
-                                             bool *o, int *id, float *ln)
+                                             bool *o, uint32_t *id, float *ln)
 {
     const bool first1 = s.t1 <= s.t2;
     const float ta = first1 ? s.t1 : s.t2;
     const float tb = first1 ? s.t2 : s.t1;
-    const int sa = first1 ? p.s1 : p.s2;
+    const uint32_t sa = first1 ? p.s1 : p.s2;
     o[0] = go;
     id[0] = s.idx;
     ln[0] = fminf(ta, te) - s.t;
@@ -162,13 +183,13 @@ __device__ __forceinline__ void slab_general(const PlaneRay &p, int sM,
     s.k2 = c2 ? s.k2 + 1.0f : s.k2;
     s.t1 = c1 ? fmaf(s.k1, p.A1, p.t01) : s.t1;
     s.t2 = c2 ? fmaf(s.k2, p.A2, p.t02) : s.t2;
-    s.idx += (c1 ? p.s1 : 0) + (c2 ? p.s2 : 0) + (go ? sM : 0);
+    s.idx += (c1 ? p.s1 : 0u) + (c2 ? p.s2 : 0u) + (go ? sM : 0u);
     s.t = go ? te : s.t;
 }
 
-// Walks the regular lanes of the warp plane by plane; op(on, idx, len) is
+// Walks the regular lanes of the warp plane by plane; op(on, off, len) is
 // called for every segment with on == true (len may be 0 at ties, which adds
-// an exact zero) and, with on == false, for slots without a segment (idx
+// an exact zero) and, with on == false, for slots without a segment (off
 // then may lie outside the cube and must not be touched).  Every lane of the
 // warp must call this (it uses warp-wide reductions); lanes with regular ==
 // false only take part in those.
@@ -213,7 +234,7 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
     const int lo_all = __reduce_max_sync(full, regular ? j0 : 0);
     const int hi_all = __reduce_min_sync(full, regular ? j0 + jend - 1 : INT_MAX);
     // non-regular lanes never advance (their slots are all off)
-    const int sM = regular ? p.sM : 0;
+    const uint32_t sM = regular ? p.sM : 0u;
     PlaneState s;
     s.t = 0.0f;
     s.k1 = 0.0f;
@@ -228,7 +249,7 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
         const bool go = (unsigned)j < (unsigned)jend;
         const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
         bool o[3];
-        int id[3];
+        uint32_t id[3];
         float ln[3];
         if (general) {
             slab_general(p, sM, s, go, te, o, id, ln);
@@ -246,7 +267,7 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
         float jf = (float)(i - j0);
         for (; i + U <= m_end; i += U) {
             bool o[U * kSlots];
-            int id[U * kSlots];
+            uint32_t id[U * kSlots];
             float ln[U * kSlots];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -268,7 +289,7 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
         }
         for (; i < m_end; ++i) {
             bool o[kSlots];
-            int id[kSlots];
+            uint32_t id[kSlots];
             float ln[kSlots];
             const float te = fmaf(jf, p.AM, p.t0M);
             jf += 1.0f;
@@ -306,7 +327,7 @@ __device__ __forceinline__ void plane_walk(const PlaneRay &p, bool regular,
         const float te = fminf(fmaf((float)j, p.AM, p.t0M), p.chord);
         const bool c2 = go && s.t2 < te;
         bool o[3];
-        int id[3];
+        uint32_t id[3];
         float ln[3];
         slab_general(p, sM, s, go, te, o, id, ln);
         op(o[0], id[0], ln[0]);
@@ -330,10 +351,10 @@ __device__ __forceinline__ void plane_walk_for(int hint, const PlaneRay &p,
         plane_walk<false, U>(p, regular, op);
 }
 
-// Plane ops: fetch(on, idx) loads what the segment needs (nothing for the
-// scatters), apply(on, idx, len, v) adds it; the walk's middle range issues
-// the fetches of several slabs before their applies.  op(on, idx, len) does
-// both at once.
+// Plane ops: fetch(on, off) loads what the segment needs (nothing for the
+// scatters), apply(on, off, len, v) adds it; the walk's middle range issues
+// the fetches of several slabs before their applies.  op(on, off, len) does
+// both at once.  off is the voxel's byte offset from the op's buffer.
 struct NoVal {};
 
 template <typename CubeT>
@@ -341,17 +362,17 @@ struct PlaneGatherOp {
     const CubeT *c;
     float acc;
     using Val = float;
-    __device__ __forceinline__ float fetch(bool on, int idx) const
+    __device__ __forceinline__ float fetch(bool on, uint32_t off) const
     {
-        return on ? load_voxel(c, idx) : 0.0f;
+        return on ? load_voxel(byte_at(c, off), 0) : 0.0f;
     }
-    __device__ __forceinline__ void apply(bool on, int, float len, float v)
+    __device__ __forceinline__ void apply(bool on, uint32_t, float len, float v)
     {
         if (on) acc = fmaf(len, v, acc);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, fetch(on, idx));
+        apply(on, off, len, fetch(on, off));
     }
 };
 
@@ -361,18 +382,19 @@ struct PlaneGatherTimeOp {
     const CubeT *c1;
     float w0, w1, acc;
     using Val = float2;
-    __device__ __forceinline__ float2 fetch(bool on, int idx) const
+    __device__ __forceinline__ float2 fetch(bool on, uint32_t off) const
     {
-        return on ? make_float2(load_voxel(c0, idx), load_voxel(c1, idx))
+        return on ? make_float2(load_voxel(byte_at(c0, off), 0),
+                                load_voxel(byte_at(c1, off), 0))
                   : make_float2(0.0f, 0.0f);
     }
-    __device__ __forceinline__ void apply(bool on, int, float len, float2 v)
+    __device__ __forceinline__ void apply(bool on, uint32_t, float len, float2 v)
     {
         if (on) acc = fmaf(len, fmaf(w0, v.x, w1 * v.y), acc);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, fetch(on, idx));
+        apply(on, off, len, fetch(on, off));
     }
 };
 
@@ -380,14 +402,14 @@ struct PlaneScatterOp {
     float *c;
     float y;
     using Val = NoVal;
-    __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
-    __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
+    __device__ __forceinline__ NoVal fetch(bool, uint32_t) const { return NoVal(); }
+    __device__ __forceinline__ void apply(bool on, uint32_t off, float len, NoVal)
     {
-        red_add_if(on, c + idx, len * y);
+        red_add_if(on, byte_at(c, off), len * y);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, NoVal());
+        apply(on, off, len, NoVal());
     }
 };
 
@@ -396,15 +418,15 @@ struct PlaneScatterTimeOp {
     float *c1;
     float y0, y1;
     using Val = NoVal;
-    __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
-    __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
+    __device__ __forceinline__ NoVal fetch(bool, uint32_t) const { return NoVal(); }
+    __device__ __forceinline__ void apply(bool on, uint32_t off, float len, NoVal)
     {
-        red_add_if(on, c0 + idx, len * y0);
-        red_add_if(on, c1 + idx, len * y1);
+        red_add_if(on, byte_at(c0, off), len * y0);
+        red_add_if(on, byte_at(c1, off), len * y1);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, NoVal());
+        apply(on, off, len, NoVal());
     }
 };
 

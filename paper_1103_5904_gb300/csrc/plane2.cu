@@ -76,22 +76,23 @@ __device__ __forceinline__ float *pick(const PlaneAcc &c, int L)
     return L == 1 ? c.c[1] : (L == 2 ? c.c[2] : c.c[0]);
 }
 
+// Plane ops (byte offsets, see plane.cuh)
 template <typename PairT>
 struct PlaneGatherPairOp {
     const PairT *c;
     float w0, w1, acc;
     using Val = float2;
-    __device__ __forceinline__ float2 fetch(bool on, int idx) const
+    __device__ __forceinline__ float2 fetch(bool on, uint32_t off) const
     {
-        return on ? load_pair(c, idx) : make_float2(0.0f, 0.0f);
+        return on ? load_pair(byte_at(c, off), 0) : make_float2(0.0f, 0.0f);
     }
-    __device__ __forceinline__ void apply(bool on, int, float len, float2 v)
+    __device__ __forceinline__ void apply(bool on, uint32_t, float len, float2 v)
     {
         if (on) acc = fmaf(len, fmaf(w0, v.x, w1 * v.y), acc);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, fetch(on, idx));
+        apply(on, off, len, fetch(on, off));
     }
 };
 
@@ -99,20 +100,20 @@ struct PlaneGatherBOp {
     const float2 *c;
     float s1, s2;
     using Val = float2;
-    __device__ __forceinline__ float2 fetch(bool on, int idx) const
+    __device__ __forceinline__ float2 fetch(bool on, uint32_t off) const
     {
-        return on ? load_pair(c, idx) : make_float2(0.0f, 0.0f);
+        return on ? load_pair(byte_at(c, off), 0) : make_float2(0.0f, 0.0f);
     }
-    __device__ __forceinline__ void apply(bool on, int, float len, float2 v)
+    __device__ __forceinline__ void apply(bool on, uint32_t, float len, float2 v)
     {
         if (on) {
             s1 = fmaf(len, v.x, s1);
             s2 = fmaf(len, v.y, s2);
         }
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, fetch(on, idx));
+        apply(on, off, len, fetch(on, off));
     }
 };
 
@@ -142,14 +143,14 @@ struct PlaneScatterPairOp {
     float2 *c;
     float y0, y1;
     using Val = NoVal;
-    __device__ __forceinline__ NoVal fetch(bool, int) const { return NoVal(); }
-    __device__ __forceinline__ void apply(bool on, int idx, float len, NoVal)
+    __device__ __forceinline__ NoVal fetch(bool, uint32_t) const { return NoVal(); }
+    __device__ __forceinline__ void apply(bool on, uint32_t off, float len, NoVal)
     {
-        red_add2_if(on, c + idx, len * y0, len * y1);
+        red_add2_if(on, byte_at(c, off), len * y0, len * y1);
     }
-    __device__ __forceinline__ void operator()(bool on, int idx, float len)
+    __device__ __forceinline__ void operator()(bool on, uint32_t off, float len)
     {
-        apply(on, idx, len, NoVal());
+        apply(on, off, len, NoVal());
     }
 };
 
@@ -188,7 +189,7 @@ k_forward_plane_pair(const RayRec *__restrict__ rays,
     if (in_img && (mask == nullptr || mask[id] == 0)) r = load_ray(rays + id);
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(PairT));
     const int L = (q.pad >> 2) & 3;
     const int64_t f0 = (int64_t)img_frame(q) * fstride;
     PlaneGatherPairOp<PairT> op;
@@ -236,7 +237,8 @@ k_forward_b(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
     if (in_img && (mask == nullptr || mask[id] == 0)) r = load_ray(rays + id);
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = plane && live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular =
+        plane && live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(float2));
     const int L = (q.pad >> 2) & 3;
     float s1 = 0.0f, s2 = 0.0f;
     if (plane) {
@@ -288,7 +290,7 @@ k_adjoint_plane_pair(const RayRec *__restrict__ rays,
     }
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular = live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(float2));
     const int L = (q.pad >> 2) & 3;
     const int64_t f0 = (int64_t)img_frame(q) * fstride;
     PlaneScatterPairOp op;
@@ -333,7 +335,8 @@ k_adjoint_b(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
     }
     const bool live = r.chord > 0.0f;
     PlaneRay p;
-    const bool regular = plane_on && live && plane_ray(r, q.pad, nx, ny, nz, p);
+    const bool regular =
+        plane_on && live && plane_ray(r, q.pad, nx, ny, nz, p, sizeof(float2));
     const int L = (q.pad >> 2) & 3;
     PlaneScatterPairOp op;
     op.c = reinterpret_cast<float2 *>(pick(acc, L));

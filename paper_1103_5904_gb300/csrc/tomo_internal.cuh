@@ -163,7 +163,9 @@ cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
 // The walk kernels use their own tiling: CTAs of 32 x 8 pixels, one image
 // row of 32 pixels per warp.  Layout kernels return at once unless bit L of
 // *used is set.
-bool plane_supported(const tomo_cube_geom *c);
+// esize: bytes per voxel of the buffers the plane walk addresses (4 for
+// float or bf16 cubes, 8 for the two-value pair buffers)
+bool plane_supported(const tomo_cube_geom *c, int esize);
 // (copies for the forward: runs when bit `bit` of *used is set)
 cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
                              int L, const tomo_cube_geom *c, int32_t n_frames,
