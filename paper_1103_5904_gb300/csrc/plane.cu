@@ -52,15 +52,16 @@ namespace {
 // Slabs per iteration of the middle range (plane_walk) and resident CTAs per
 // SM the register allocation targets, measured on GB300 (256^3 cube, 240
 // views of 512^2): the static forward keeps the loads of four slabs in
-// flight (8.72 ms against 9.25 ms one slab at a time; two slabs at five
-// CTAs 10.7 ms, eight slabs at three CTAs 9.71 ms); the transpose, bound by
-// instruction issue and L2 reductions, walks one slab per iteration (9.75
-// ms against 10.0 ms with two slabs and 10.2 ms before the middle range).
+// flight (8.15 ms; three slabs 8.47, five 8.66, six at three CTAs 9.68, two
+// at five CTAs 10.7); the transpose, bound by the rate at which an SM sends
+// reduction sectors to L2, walks one slab per iteration at six CTAs (9.19
+// ms; five CTAs 9.31, two slabs per iteration 9.52).
 constexpr int kFwdUnroll = 4;
 constexpr int kFwdTimeUnroll = 1;
 constexpr int kFwdMinBlocks = 4;
 constexpr int kAdjUnroll = 1;
-constexpr int kAdjMinBlocks = 5;
+constexpr int kAdjMinBlocks = 6;
+constexpr int kAdjTimeMinBlocks = 5;
 
 template <typename CubeT, bool kTime>
 __global__ void __launch_bounds__(256, kFwdMinBlocks)
@@ -128,7 +129,7 @@ k_forward_plane(const RayRec *__restrict__ rays,
 }
 
 template <bool kTime>
-__global__ void __launch_bounds__(256, kAdjMinBlocks)
+__global__ void __launch_bounds__(256, kTime ? kAdjTimeMinBlocks : kAdjMinBlocks)
 k_adjoint_plane(const RayRec *__restrict__ rays,
                 const ImgParam *__restrict__ prm,
                 const float *__restrict__ images,
