@@ -99,8 +99,9 @@ def test_frame_pairs(T, case):
 def test_single_walk_b(T, case):
     """Thomson B: the single walk on (m' x, m x) pairs gives the two-walk
     images bit for bit (per-ray, plane on every image, the default choice;
-    float32 and bf16 cubes); its transpose meets the oracle's bound and
-    agrees with the two-walk transpose."""
+    float32 and bf16 cubes); its transpose agrees with the two-walk
+    transpose, with and without a map mask and when accumulating, and meets
+    the oracle's bound."""
     name, g, ptg, mask, nu, nv = case
     g = dict(g)
     g["r_obs"] = 0.0
@@ -120,12 +121,20 @@ def test_single_walk_b(T, case):
                 b = T.tomo_project(X, g, ptg, nu, nv, mask=md, kind="B",
                                    limb_u=u, map_mask=map_mask, ctx=two)
                 assert torch.equal(a, b), (name, ps, dt)
-        a = T.tomo_backproject(to_dev(y), g, ptg, mask=md, kind="B",
-                               limb_u=u, ctx=one)
         b = T.tomo_backproject(to_dev(y), g, ptg, mask=md, kind="B",
                                limb_u=u, ctx=two)
         scale = float(b.abs().max())
-        torch.testing.assert_close(a, b, rtol=1e-5, atol=1e-6 * scale)
+        for map_mask in (None, mask_dev(mm)):
+            a = T.tomo_backproject(to_dev(y), g, ptg, mask=md, kind="B",
+                                   limb_u=u, map_mask=map_mask, ctx=one)
+            w = T.tomo_backproject(to_dev(y), g, ptg, mask=md, kind="B",
+                                   limb_u=u, map_mask=map_mask, ctx=two)
+            torch.testing.assert_close(a, w, rtol=1e-5, atol=1e-6 * scale)
+        # accumulate: adds onto what the cube holds
+        acc = torch.ones_like(b)
+        T.tomo_backproject(to_dev(y), g, ptg, mask=md, kind="B", limb_u=u,
+                           out=acc, accumulate=True, ctx=one)
+        torch.testing.assert_close(acc - 1.0, b, rtol=1e-5, atol=1e-6 * scale)
         one.close()
         two.close()
     # against the oracle (the transpose bound of the Thomson tests: the
