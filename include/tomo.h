@@ -419,9 +419,12 @@ tomo_status tomo_set_plane_rules(tomo_ctx *ctx, const tomo_cube_geom *cube,
                                  const tomo_plane_rules *rules);
 
 /* The walk chosen for each image of the most recent single-problem
- * geometry (a report of the schedule, no counterpart in the paper;
- * synchronises the legacy default stream):
- *   bit 0: P^T (and P when bit 1) walk plane by plane (else per ray)
+ * geometry by the single-value P and P^T (a report of the schedule, no
+ * counterpart in the paper; synchronises the legacy default stream).  It
+ * follows the per-image hints and the context's TOMO_OPT_PLANE_SYNC, and
+ * reports per-ray walks for a cube of more than 2^32 bytes, which the plane
+ * walk does not address:
+ *   bit 0: P^T walks plane by plane (else per ray)
  *   bit 1: P walks plane by plane
  *   bit 2: the plane walks cross every slab with the general body
  *   bits 3-4: the major axis (0 x, 1 y, 2 z); bits 5-6: the lateral axis

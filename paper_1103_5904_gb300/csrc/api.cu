@@ -265,6 +265,7 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     ctx->key = h;
     ctx->hint_key = hh;
     ctx->cached_n_img = g->n_img;
+    ctx->cached_cube = *c;
     ctx->key_valid = true;
     return TOMO_OK;
 }
@@ -805,10 +806,19 @@ tomo_status tomo_walk_plan(tomo_ctx *ctx, int32_t n_img, int32_t *codes_host)
     CUDA_TRY(ctx, cudaMemcpy(prm.data(), ctx->params.p,
                              sizeof(ImgParam) * (size_t)n_img,
                              cudaMemcpyDeviceToHost));
+    // what the single-value walks of P and P^T run (Section 3.3.1): the
+    // device hint, gated as the host gates the launches (option bits, the
+    // host estimates, the plane walk's buffer-size bound)
+    const bool fits = plane_supported(&ctx->cached_cube, 4);
+    const bool adj_on = fits && (ctx->plane_sync & 1) && ctx->plane_possible;
+    const bool all = (ctx->plane_sync & 2) != 0;
+    const bool fwd_on = fits && (ctx->plane_sync & (2 | 4)) &&
+                        (all || ctx->fwd_plane_possible);
     for (int32_t i = 0; i < n_img; ++i) {
         const int32_t h = prm[i].pad;
         const bool valid = (h & kPlaneHintValid) != 0;
-        codes_host[i] = (valid ? 1 : 0) | ((valid && (h & kPlaneFwdBit)) ? 2 : 0) |
+        const bool fwd = valid && fwd_on && (all || (h & kPlaneFwdBit));
+        codes_host[i] = ((valid && adj_on) ? 1 : 0) | (fwd ? 2 : 0) |
                         ((h & kPlaneGeneralBit) ? 4 : 0) | ((h & 3) << 3) |
                         (((h >> 2) & 3) << 5);
     }

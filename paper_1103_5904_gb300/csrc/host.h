@@ -54,6 +54,7 @@ struct tomo_ctx {
     uint64_t key = 0;       // geometry of the cached ray records
     uint64_t hint_key = 0;  // geometry and walk rules of the cached hints
     int32_t cached_n_img = 0;  // images of the cached geometry
+    tomo_cube_geom cached_cube = {};  // cube of the cached geometry
     cudaEvent_t setup_done = nullptr;
     // per-geometry buffers
     tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
