@@ -213,6 +213,19 @@ def peak_hbm():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def ncu_reduction_sectors(kernel):
+    """Reduction sectors that `kernel` sends from L1 to the crossbar per
+    Siddon segment, recorded in profiles/, or None."""
+    path = os.path.join(ROOT, "profiles", "reduction_sectors.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    return None if rec is None else rec.get(
+        "l1_to_crossbar_reduction_sectors_per_segment")
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` recorded in profiles/, or None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -415,6 +428,22 @@ def run_gpu(args, rank, local_rank, world):
                4.0 * segments)
         roofline["achieved_rmw"] = rmw / per_launch_s / 1e9
         roofline["frac_rmw"] = roofline["achieved_rmw"] / peak
+    # the resource that binds the plane transpose: each SM's L1 sends at
+    # most one 32-byte reduction sector per cycle to the crossbar; sectors
+    # per segment from the committed capture, time from this run, clock the
+    # median sampled during the timed region
+    red = ncu_reduction_sectors(kname[dom]) if dom == "adjoint" else None
+    if red is not None and clk.get("sm_mhz"):
+        per_launch_s = kern["adjoint"]["ms_per_projection"] / 1e3
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_sec = sms * clk["sm_mhz"] * 1e6
+        got_sec = red * segments / per_launch_s
+        roofline["binding"] = {
+            "resource": "L1 -> crossbar reduction sectors (32 B, one per "
+                        "cycle per SM)",
+            "achieved": got_sec, "peak": peak_sec, "unit": "sectors/s",
+            "frac": got_sec / peak_sec, "sectors_per_segment": red,
+            "source": "profiles/k_plane_cg256_24img.md"}
     # compulsory bytes of one projection: the cube and the images once (and
     # the mask), far below the gather model
     comp = 4.0 * x_true.numel() + 4.0 * n_rays + (n_rays if mask is not None

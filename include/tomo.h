@@ -158,9 +158,11 @@ typedef struct tomo_ctx tomo_ctx;
                                   tiling (32 x 8 pixels per CTA, one image
                                   row per warp) whatever the tile options
                                   say.  Needs cubes of at most 16384 voxels
-                                  per side, else the per-ray walk is used.
-                                  Costs two cube-sized float buffers (times
-                                  the frames) of workspace. */
+                                  per side and 2^32 bytes as float32 (it
+                                  addresses voxels by 32-bit byte offsets),
+                                  else the per-ray walk is used.  Costs two
+                                  cube-sized float buffers (times the
+                                  frames) of workspace. */
 #define TOMO_OPT_CHANNELS   8  /* bit mask (default 3) of the two-value
                                   plane walks: bit 0, time-interpolated P
                                   and P^T walk frame pairs (X[k], X[k+1])
@@ -171,7 +173,9 @@ typedef struct tomo_ctx tomo_ctx;
                                   operator of a single frame runs one walk
                                   on (m' x, m x) pairs instead of two walks.
                                   Costs three buffers of 8 bytes per voxel
-                                  (times T - 1 frame pairs) of workspace. */
+                                  (times T - 1 frame pairs) of workspace.
+                                  Cubes of more than 2^29 voxels take the
+                                  one-value walks instead. */
 
 /* Kernel classes of tomo_profile */
 enum {
