@@ -174,8 +174,10 @@ typedef struct tomo_ctx tomo_ctx;
                                   on (m' x, m x) pairs instead of two walks.
                                   Costs three buffers of 8 bytes per voxel
                                   (times T - 1 frame pairs) of workspace.
-                                  Cubes of more than 2^29 voxels take the
-                                  one-value walks instead. */
+                                  Above 2^29 voxels (pair buffers of more
+                                  than 2^32 bytes) time interpolation walks
+                                  separate frames and the B pairs are walked
+                                  per ray. */
 
 /* Kernel classes of tomo_profile */
 enum {
