@@ -51,12 +51,14 @@ namespace {
 
 // Slabs per iteration of the middle range (plane_walk) and resident CTAs per
 // SM the register allocation targets, measured on GB300 (256^3 cube, 240
-// views of 512^2): the static forward keeps the loads of four slabs in
-// flight (8.15 ms; three slabs 8.47, five 8.66, six at three CTAs 9.68, two
-// at five CTAs 10.7); the transpose, bound by the rate at which an SM sends
-// reduction sectors to L2, walks one slab per iteration at six CTAs (9.19
-// ms; five CTAs 9.31, two slabs per iteration 9.52).
-constexpr int kFwdUnroll = 4;
+// views of 512^2; 512^3 cube, 360 views of 1024^2): the static forward keeps
+// the loads of six slabs in flight (7.49 / 114.8 ms; four slabs 7.72 /
+// 129.9, seven 7.60 / 129.0, eight 7.53 / 124.1, twelve 7.44 / 122.7, all at
+// four CTAs; three slabs 7.78, five 8.09, two at five CTAs 10.5 on the 256^3
+// cube); the transpose, bound by the rate at which an SM sends reduction
+// sectors to L2, walks one slab per iteration at six CTAs (9.19 ms; five
+// CTAs 9.31, two slabs per iteration 9.52).
+constexpr int kFwdUnroll = 6;
 constexpr int kFwdTimeUnroll = 1;
 constexpr int kFwdMinBlocks = 4;
 constexpr int kAdjUnroll = 1;

@@ -33,7 +33,9 @@ namespace {
 // Slabs per iteration of the forward's middle range (loads in flight), as
 // measured on GB300: 8-frame 256^3 temporal P 22.7 ms at 2 slabs, 16.6 ms
 // at 4, 18.6 ms at 6, 20.7 ms at 8 (3 CTAs per SM); Thomson B forward on
-// the 256^3 cube 14.8, 11.6, 12.5, 13.2 ms.
+// the 256^3 cube 14.8, 11.6, 12.5, 13.2 ms.  At 4 CTAs per SM with byte
+// offsets: temporal 15.9 ms at 4 slabs, 17.1 at 6, 15.7 at 8; B 10.9, 12.1,
+// 11.3 ms.
 constexpr int kPairFwdUnroll = 4;
 constexpr int kPairFwdMinBlocks = 4;
 constexpr int kPairAdjMinBlocks = 5;
