@@ -179,6 +179,19 @@ typedef struct tomo_ctx tomo_ctx;
                                   separate frames and the B pairs are walked
                                   per ray. */
 
+#define TOMO_OPT_GROUP_FWD  9  /* CTA order of the plane-synchronous P: 0
+                                  (default) chosen from the bytes the walk
+                                  gathers from; n >= 1: images are taken in
+                                  groups of n, and inside a group the CTAs of
+                                  one 8-pixel row band of every image run
+                                  before the next band (1: image after
+                                  image), so that the CTAs resident at once
+                                  read one band of the cube.  Same results
+                                  whatever the order (P bit-identical). */
+#define TOMO_OPT_GROUP_ADJ  10 /* the same for the plane-synchronous P^T
+                                  (results differ only by the order of
+                                  float additions) */
+
 /* Kernel classes of tomo_profile */
 enum {
     TOMO_K_SETUP = 0,   /* pointing -> ray records (FP64) */

@@ -359,6 +359,31 @@ tomo_status ensure_pairs(tomo_ctx *ctx, const tomo_cube_geom *c,
     return TOMO_OK;
 }
 
+// Images per group of a plane walk's CTA order (plane_cta): the option if
+// set, else chosen from the bytes of the buffers the walk gathers from or
+// adds into (all frames or frame pairs of one layout) against L2, as
+// measured on GB300 (times against image-after-image order):
+//  - P: every image in one group once the cube reaches a quarter of L2
+//    (256^3 cube -3 %, 512^3 -10 %, 8 frame pairs -22 %, Thomson B pairs
+//    -17 %; a 128^3 cube +4 %);
+//  - P^T: image after image while the accumulators fit twice in L2 (one
+//    group of every image: 256^3 +7 %, B pairs +2 %: the CTAs of many images
+//    then add into the same lines), else groups of 8 images into a single
+//    accumulator (512^3: -7 %; 32 images -6 %, every image -5 %) and one
+//    group of every image when the images spread over several frame or
+//    frame-pair accumulators (8 frames, 7 pairs: -14 %; 32 images -13 %,
+//    8 images -8 %).
+int plane_group(const tomo_ctx *ctx, bool adjoint, int64_t walked_bytes,
+                int n_acc, int32_t n_img)
+{
+    const int opt = adjoint ? ctx->group_adj : ctx->group_fwd;
+    if (opt > 0) return opt;
+    const int64_t l2 = ctx->l2_bytes > 0 ? ctx->l2_bytes : (int64_t)126 << 20;
+    if (!adjoint) return walked_bytes >= l2 / 4 ? n_img : 1;
+    if (walked_bytes <= 2 * l2) return 1;
+    return n_acc > 1 ? n_img : 8;
+}
+
 bool use_time_pairs(const tomo_ctx *ctx, const tomo_cube_geom *c,
                     int32_t n_frames)
 {
@@ -395,9 +420,11 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                                   mask, out, g->n_img, g->nu, g->nv, c->nx,
                                   c->nx * c->ny, t, done, s, true));
         LAUNCH(ctx, TOMO_K_FORWARD, s,
-               launch_forward_plane_pair(rays, prm, pc, cube_dev, dtype,
-                                         fstride, mask, out, g->n_img, g->nu,
-                                         g->nv, c, done, s, !all));
+               launch_forward_plane_pair(
+                   rays, prm, pc, cube_dev, dtype, fstride, mask, out,
+                   g->n_img, g->nu, g->nv, c, done, s, !all,
+                   plane_group(ctx, false, 8 * fstride * (n_frames - 1),
+                               n_frames - 1, g->n_img)));
         return TOMO_OK;
     }
     if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible)) {
@@ -415,9 +442,12 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                                   g->nv, c->nx, c->nx * c->ny, t, done, s,
                                   true));
         LAUNCH(ctx, TOMO_K_FORWARD, s,
-               launch_forward_plane(rays, prm, pc, dtype, fstride, n_frames > 1,
-                                    mask, out, g->n_img, g->nu, g->nv, c,
-                                    done, s, !all));
+               launch_forward_plane(
+                   rays, prm, pc, dtype, fstride, n_frames > 1, mask, out,
+                   g->n_img, g->nu, g->nv, c, done, s, !all,
+                   plane_group(ctx, false,
+                               (dtype == TOMO_BF16 ? 2 : 4) * fstride * n_frames,
+                               n_frames, g->n_img)));
         return TOMO_OK;
     }
     LAUNCH(ctx, TOMO_K_FORWARD, s,
@@ -451,9 +481,11 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
         PlaneAcc pa = { { (float *)ctx->pr[0].p, (float *)ctx->pr[1].p,
                           (float *)ctx->pr[2].p } };
         LAUNCH(ctx, TOMO_K_ADJOINT, s,
-               launch_adjoint_plane_pair(rays, prm, images, mask, pa, cube,
-                                         fstride, g->n_img, g->nu, g->nv, c,
-                                         done, s));
+               launch_adjoint_plane_pair(
+                   rays, prm, images, mask, pa, cube, fstride, g->n_img,
+                   g->nu, g->nv, c, done, s,
+                   plane_group(ctx, true, 8 * fstride * (n_frames - 1),
+                               n_frames - 1, g->n_img)));
         for (int L = 0; L <= 2; ++L)
             LAUNCH(ctx, TOMO_K_LAYOUT, s,
                    launch_add_pairs(ctx->pr[L].p, cube, L, c, n_frames, used,
@@ -472,9 +504,11 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                                   ctx->num_sms, s));
         PlaneAcc pa = { { cube, a1, a2 } };
         LAUNCH(ctx, TOMO_K_ADJOINT, s,
-               launch_adjoint_plane(rays, prm, images, mask, pa, fstride,
-                                    n_frames > 1, g->n_img, g->nu, g->nv, c,
-                                    done, s));
+               launch_adjoint_plane(
+                   rays, prm, images, mask, pa, fstride, n_frames > 1,
+                   g->n_img, g->nu, g->nv, c, done, s,
+                   plane_group(ctx, true, 4 * fstride * n_frames, n_frames,
+                               g->n_img)));
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
                launch_add_from_layout(a1, cube, 1, c, n_frames, used, done, s));
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
@@ -551,7 +585,8 @@ tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
                launch_forward_b((const RayRec *)ctx->rays.p,
                                 (const ImgParam *)ctx->params.p, pc, rho2,
                                 mask, out, g->n_img, g->nu, g->nv, c, done,
-                                plane ? (all ? 2 : 1) : 0, s));
+                                plane ? (all ? 2 : 1) : 0, s,
+                                plane_group(ctx, false, 8 * n, 1, g->n_img)));
         return TOMO_OK;
     }
     if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
@@ -616,7 +651,8 @@ tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
                launch_adjoint_b((const RayRec *)ctx->rays.p,
                                 (const ImgParam *)ctx->params.p, images, rho2,
                                 mask, pa, g->n_img, g->nu, g->nv, c, done,
-                                plane, s));
+                                plane, s,
+                                plane_group(ctx, true, 8 * n, 1, g->n_img)));
         if (plane)
             for (int L = 1; L <= 2; ++L)
                 LAUNCH(ctx, TOMO_K_LAYOUT, s,
@@ -722,6 +758,7 @@ tomo_status tomo_create(tomo_ctx **out, int32_t device)
     tomo_ctx *ctx = new tomo_ctx();
     ctx->device = device;
     ctx->num_sms = prop.multiProcessorCount;
+    ctx->l2_bytes = prop.l2CacheSize;
     if (cudaEventCreateWithFlags(&ctx->setup_done, cudaEventDisableTiming) !=
         cudaSuccess) {
         delete ctx;
@@ -782,6 +819,12 @@ tomo_status tomo_set_option(tomo_ctx *ctx, int32_t option, int64_t value)
     case TOMO_OPT_CHANNELS:
         if (value < 0 || value > 3) break;
         ctx->channels = (int)value;
+        return TOMO_OK;
+    case TOMO_OPT_GROUP_FWD:
+    case TOMO_OPT_GROUP_ADJ:
+        if (value < 0 || value > 65535) break;
+        (option == TOMO_OPT_GROUP_FWD ? ctx->group_fwd : ctx->group_adj) =
+            (int)value;
         return TOMO_OK;
     default:
         return fail(ctx, TOMO_ERR_ARG, "unknown option %d", option);

@@ -37,6 +37,10 @@ struct BatchPlan;  // batch_api.cu
 struct tomo_ctx {
     int device = 0;
     int num_sms = 0;
+    int64_t l2_bytes = 0;
+    // images per group of the plane walks' CTA order (TOMO_OPT_GROUP_FWD /
+    // TOMO_OPT_GROUP_ADJ); 0: chosen from the bytes a walk touches
+    int group_fwd = 0, group_adj = 0;
     char err[512] = { 0 };
     bool ray_cache = true;
     // bit 0: P^T plane-synchronous; bit 1: P plane-synchronous for every

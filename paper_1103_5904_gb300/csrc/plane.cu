@@ -72,15 +72,16 @@ k_forward_plane(const RayRec *__restrict__ rays,
                 int64_t frame_stride, const uint8_t *__restrict__ mask,
                 float *__restrict__ out, int nu, int nv, int nx, int ny,
                 int nz, Tiling tl, const double *__restrict__ done,
-                bool only_marked)
+                bool only_marked, int n_img, int group)
 {
     if (done != nullptr && *done != 0.0) return;
-    const int img = blockIdx.z;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     const ImgParam q = prm[img];
     // the whole CTA covers one image: this return is uniform
     if (only_marked && !(q.pad & kPlaneFwdBit)) return;
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     RayRec r;
     r.chord = -1.0f;
@@ -137,12 +138,14 @@ k_adjoint_plane(const RayRec *__restrict__ rays,
                 const float *__restrict__ images,
                 const uint8_t *__restrict__ mask, PlaneAcc acc,
                 int64_t frame_stride, int nu, int nv, int nx, int ny, int nz,
-                Tiling tl, const double *__restrict__ done)
+                Tiling tl, const double *__restrict__ done, int n_img,
+                int group)
 {
     if (done != nullptr && *done != 0.0) return;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
-    const int img = blockIdx.z;
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     const ImgParam q = prm[img];
     RayRec r;
@@ -285,11 +288,13 @@ k_zero_layout(float *__restrict__ p, int64_t n, const unsigned *__restrict__ use
 // 32 x 8 pixels per CTA, one row of 32 pixels per warp
 constexpr Tiling kPlaneTiling = { 32, 8, 32 };
 
-dim3 plane_grid(int nu, int nv, int n_img)
+dim3 plane_grid(int nu, int nv, int n_img, int group)
 {
     const Tiling t = kPlaneTiling;
+    const int tiles_v = (nv + t.tile_v - 1) / t.tile_v;
     return dim3((unsigned)((nu + t.tile_u - 1) / t.tile_u),
-                (unsigned)((nv + t.tile_v - 1) / t.tile_v), (unsigned)n_img);
+                (unsigned)(tiles_v * group),
+                (unsigned)((n_img + group - 1) / group));
 }
 
 dim3 layout_grid(const LayoutMap &m)
@@ -299,6 +304,15 @@ dim3 layout_grid(const LayoutMap &m)
 }
 
 }  // namespace
+
+int plane_group_clamp(int group, int n_img, int tiles_v)
+{
+    // the grid's y extent (tile rows x group) stays within 65535
+    const int cap = tiles_v > 0 ? 65535 / tiles_v : 1;
+    if (group > n_img) group = n_img;
+    if (group > cap) group = cap;
+    return group < 1 ? 1 : group;
+}
 
 bool plane_supported(const tomo_cube_geom *c, int esize)
 {
@@ -359,31 +373,32 @@ cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
                                  const uint8_t *mask, float *out,
                                  int32_t n_img, int32_t nu, int32_t nv,
                                  const tomo_cube_geom *c, const double *done,
-                                 cudaStream_t s, bool only_marked)
+                                 cudaStream_t s, bool only_marked, int group)
 {
     if (n_img <= 0) return cudaSuccess;
     const Tiling t = kPlaneTiling;
-    const dim3 grid = plane_grid(nu, nv, n_img);
+    group = plane_group_clamp(group, n_img, (nv + t.tile_v - 1) / t.tile_v);
+    const dim3 grid = plane_grid(nu, nv, n_img, group);
     const int block = t.tile_u * t.tile_v;
     const bool om = only_marked;
     if (dtype == TOMO_BF16) {
         if (time_interp)
             k_forward_plane<uint16_t, true><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done, om);
+                c->ny, c->nz, t, done, om, n_img, group);
         else
             k_forward_plane<uint16_t, false><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done, om);
+                c->ny, c->nz, t, done, om, n_img, group);
     } else {
         if (time_interp)
             k_forward_plane<float, true><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done, om);
+                c->ny, c->nz, t, done, om, n_img, group);
         else
             k_forward_plane<float, false><<<grid, block, 0, s>>>(
                 rays, prm, cubes, frame_stride, mask, out, nu, nv, c->nx,
-                c->ny, c->nz, t, done, om);
+                c->ny, c->nz, t, done, om, n_img, group);
     }
     return cudaGetLastError();
 }
@@ -393,20 +408,21 @@ cudaError_t launch_adjoint_plane(const RayRec *rays, const ImgParam *prm,
                                  PlaneAcc acc, int64_t frame_stride,
                                  bool time_interp, int32_t n_img, int32_t nu,
                                  int32_t nv, const tomo_cube_geom *c,
-                                 const double *done, cudaStream_t s)
+                                 const double *done, cudaStream_t s, int group)
 {
     if (n_img <= 0) return cudaSuccess;
     const Tiling t = kPlaneTiling;
-    const dim3 grid = plane_grid(nu, nv, n_img);
+    group = plane_group_clamp(group, n_img, (nv + t.tile_v - 1) / t.tile_v);
+    const dim3 grid = plane_grid(nu, nv, n_img, group);
     const int block = t.tile_u * t.tile_v;
     if (time_interp)
         k_adjoint_plane<true><<<grid, block, 0, s>>>(
             rays, prm, images, mask, acc, frame_stride, nu, nv, c->nx, c->ny,
-            c->nz, t, done);
+            c->nz, t, done, n_img, group);
     else
         k_adjoint_plane<false><<<grid, block, 0, s>>>(
             rays, prm, images, mask, acc, frame_stride, nu, nv, c->nx, c->ny,
-            c->nz, t, done);
+            c->nz, t, done, n_img, group);
     return cudaGetLastError();
 }
 

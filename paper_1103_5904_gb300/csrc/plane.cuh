@@ -13,6 +13,21 @@
 
 namespace tomo {
 
+// The CTA's image and pixel-tile row.  The grid is (tile columns, tile rows
+// x group, image groups): inside a group of `group` consecutive images the
+// CTAs of one tile row of every image run before those of the next row, so
+// the CTAs resident at one time gather from or add into one band of the
+// cube (the rays of one pixel row of views taken near a common plane cross
+// few planes of the cube) rather than the whole cube of one image.  Returns
+// false for the padding images of the last group (uniform over the CTA).
+__device__ __forceinline__ bool plane_cta(int n_img, int group, int &img,
+                                          int &tile_v)
+{
+    tile_v = (int)blockIdx.y / group;
+    img = (int)blockIdx.z * group + (int)blockIdx.y % group;
+    return img < n_img;
+}
+
 // One ray, re-expressed for the plane walk: M first, then the two minor
 // axes, a1 the one with the smaller crossing spacing (crossed more often).
 // Voxel positions are byte offsets from the walked buffer's base, held as

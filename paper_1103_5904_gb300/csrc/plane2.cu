@@ -188,14 +188,16 @@ k_forward_plane_pair(const RayRec *__restrict__ rays,
                      const CubeT *__restrict__ native, int64_t fstride,
                      const uint8_t *__restrict__ mask, float *__restrict__ out,
                      int nu, int nv, int nx, int ny, int nz, Tiling tl,
-                     const double *__restrict__ done, bool only_marked)
+                     const double *__restrict__ done, bool only_marked,
+                     int n_img, int group)
 {
     if (done != nullptr && *done != 0.0) return;
-    const int img = blockIdx.z;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     const ImgParam q = prm[img];
     if (only_marked && !(q.pad & kPlaneFwdBit)) return;  // uniform per CTA
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     RayRec r;
     r.chord = -1.0f;
@@ -235,15 +237,17 @@ k_forward_b(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
             PlaneCubes pairs, const float *__restrict__ rho2,
             const uint8_t *__restrict__ mask, float *__restrict__ out, int nu,
             int nv, int nx, int ny, int nz, Tiling tl,
-            const double *__restrict__ done, int plane_mode)
+            const double *__restrict__ done, int plane_mode, int n_img,
+            int group)
 {
     if (done != nullptr && *done != 0.0) return;
-    const int img = blockIdx.z;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     const ImgParam q = prm[img];
     // uniform per CTA
     const bool plane = plane_mode == 2 || (plane_mode == 1 && (q.pad & kPlaneFwdBit));
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     RayRec r;
     r.chord = -1.0f;
@@ -286,12 +290,14 @@ k_adjoint_plane_pair(const RayRec *__restrict__ rays,
                      const float *__restrict__ images,
                      const uint8_t *__restrict__ mask, PlaneAcc acc,
                      float *cube, int64_t fstride, int nu, int nv, int nx,
-                     int ny, int nz, Tiling tl, const double *__restrict__ done)
+                     int ny, int nz, Tiling tl, const double *__restrict__ done,
+                     int n_img, int group)
 {
     if (done != nullptr && *done != 0.0) return;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
-    const int img = blockIdx.z;
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     const ImgParam q = prm[img];
     RayRec r;
@@ -330,12 +336,13 @@ k_adjoint_b(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
             const float *__restrict__ images, const float *__restrict__ rho2,
             const uint8_t *__restrict__ mask, PlaneAcc acc, int nu, int nv,
             int nx, int ny, int nz, Tiling tl, const double *__restrict__ done,
-            bool plane_on)
+            bool plane_on, int n_img, int group)
 {
     if (done != nullptr && *done != 0.0) return;
+    int img, tile_v;
+    if (!plane_cta(n_img, group, img, tile_v)) return;
     int iu, iv;
-    const bool in_img = pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv);
-    const int img = blockIdx.z;
+    const bool in_img = pixel_of_thread(tl, blockIdx.x, tile_v, nu, nv, iu, iv);
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     const ImgParam q = prm[img];
     RayRec r;
@@ -564,10 +571,12 @@ k_b_to_layout(const float2 *__restrict__ in, float2 *__restrict__ out,
 
 constexpr Tiling kPlaneTiling2 = { 32, 8, 32 };
 
-dim3 plane_grid2(int nu, int nv, int n_img)
+dim3 plane_grid2(int nu, int nv, int n_img, int &group)
 {
-    return dim3((unsigned)((nu + 31) / 32), (unsigned)((nv + 7) / 8),
-                (unsigned)n_img);
+    const int tiles_v = (nv + 7) / 8;
+    group = plane_group_clamp(group, n_img, tiles_v);
+    return dim3((unsigned)((nu + 31) / 32), (unsigned)(tiles_v * group),
+                (unsigned)((n_img + group - 1) / group));
 }
 
 dim3 pair_grid(const PairMap &m)
@@ -665,20 +674,20 @@ cudaError_t launch_forward_plane_pair(const RayRec *rays, const ImgParam *prm,
                                       int32_t n_img, int32_t nu, int32_t nv,
                                       const tomo_cube_geom *c,
                                       const double *done, cudaStream_t s,
-                                      bool only_marked)
+                                      bool only_marked, int group)
 {
     if (n_img <= 0) return cudaSuccess;
-    const dim3 grid = plane_grid2(nu, nv, n_img);
+    const dim3 grid = plane_grid2(nu, nv, n_img, group);
     if (dtype == TOMO_BF16)
         k_forward_plane_pair<uint16_t, uint32_t><<<grid, 256, 0, s>>>(
             rays, prm, pairs, static_cast<const uint16_t *>(native), fstride,
             mask, out, nu, nv, c->nx, c->ny, c->nz, kPlaneTiling2, done,
-            only_marked);
+            only_marked, n_img, group);
     else
         k_forward_plane_pair<float, float2><<<grid, 256, 0, s>>>(
             rays, prm, pairs, static_cast<const float *>(native), fstride,
             mask, out, nu, nv, c->nx, c->ny, c->nz, kPlaneTiling2, done,
-            only_marked);
+            only_marked, n_img, group);
     return cudaGetLastError();
 }
 
@@ -688,12 +697,14 @@ cudaError_t launch_adjoint_plane_pair(const RayRec *rays, const ImgParam *prm,
                                       int64_t fstride, int32_t n_img,
                                       int32_t nu, int32_t nv,
                                       const tomo_cube_geom *c,
-                                      const double *done, cudaStream_t s)
+                                      const double *done, cudaStream_t s,
+                                      int group)
 {
     if (n_img <= 0) return cudaSuccess;
-    k_adjoint_plane_pair<<<plane_grid2(nu, nv, n_img), 256, 0, s>>>(
+    const dim3 grid = plane_grid2(nu, nv, n_img, group);
+    k_adjoint_plane_pair<<<grid, 256, 0, s>>>(
         rays, prm, images, mask, acc, cube, fstride, nu, nv, c->nx, c->ny,
-        c->nz, kPlaneTiling2, done);
+        c->nz, kPlaneTiling2, done, n_img, group);
     return cudaGetLastError();
 }
 
@@ -702,12 +713,13 @@ cudaError_t launch_forward_b(const RayRec *rays, const ImgParam *prm,
                              const uint8_t *mask, float *out, int32_t n_img,
                              int32_t nu, int32_t nv, const tomo_cube_geom *c,
                              const double *done, int plane_mode,
-                             cudaStream_t s)
+                             cudaStream_t s, int group)
 {
     if (n_img <= 0) return cudaSuccess;
-    k_forward_b<<<plane_grid2(nu, nv, n_img), 256, 0, s>>>(
+    const dim3 grid = plane_grid2(nu, nv, n_img, group);
+    k_forward_b<<<grid, 256, 0, s>>>(
         rays, prm, pairs, rho2, mask, out, nu, nv, c->nx, c->ny, c->nz,
-        kPlaneTiling2, done, plane_mode);
+        kPlaneTiling2, done, plane_mode, n_img, group);
     return cudaGetLastError();
 }
 
@@ -716,12 +728,13 @@ cudaError_t launch_adjoint_b(const RayRec *rays, const ImgParam *prm,
                              const uint8_t *mask, PlaneAcc acc, int32_t n_img,
                              int32_t nu, int32_t nv, const tomo_cube_geom *c,
                              const double *done, bool plane_on,
-                             cudaStream_t s)
+                             cudaStream_t s, int group)
 {
     if (n_img <= 0) return cudaSuccess;
-    k_adjoint_b<<<plane_grid2(nu, nv, n_img), 256, 0, s>>>(
+    const dim3 grid = plane_grid2(nu, nv, n_img, group);
+    k_adjoint_b<<<grid, 256, 0, s>>>(
         rays, prm, images, rho2, mask, acc, nu, nv, c->nx, c->ny, c->nz,
-        kPlaneTiling2, done, plane_on);
+        kPlaneTiling2, done, plane_on, n_img, group);
     return cudaGetLastError();
 }
 

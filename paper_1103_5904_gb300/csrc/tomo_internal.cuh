@@ -166,6 +166,9 @@ cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
 // esize: bytes per voxel of the buffers the plane walk addresses (4 for
 // float or bf16 cubes, 8 for the two-value pair buffers)
 bool plane_supported(const tomo_cube_geom *c, int esize);
+// Images per group of the plane walks' CTA order (plane_cta in plane.cuh),
+// clamped to [1, n_img] and to the grid's y extent (tiles_v tile rows).
+int plane_group_clamp(int group, int n_img, int tiles_v);
 // (copies for the forward: runs when bit `bit` of *used is set)
 cudaError_t launch_to_layout(const void *cube, tomo_dtype dtype, void *out,
                              int L, const tomo_cube_geom *c, int32_t n_frames,
@@ -184,13 +187,14 @@ cudaError_t launch_forward_plane(const RayRec *rays, const ImgParam *prm,
                                  const uint8_t *mask, float *out,
                                  int32_t n_img, int32_t nu, int32_t nv,
                                  const tomo_cube_geom *c, const double *done,
-                                 cudaStream_t s, bool only_marked = false);
+                                 cudaStream_t s, bool only_marked, int group);
 cudaError_t launch_adjoint_plane(const RayRec *rays, const ImgParam *prm,
                                  const float *images, const uint8_t *mask,
                                  PlaneAcc acc, int64_t frame_stride,
                                  bool time_interp, int32_t n_img, int32_t nu,
                                  int32_t nv, const tomo_cube_geom *c,
-                                 const double *done, cudaStream_t s);
+                                 const double *done, cudaStream_t s,
+                                 int group);
 cudaError_t launch_count(const RayRec *rays, const uint8_t *mask,
                          int32_t n_img, int32_t nu, int32_t nv, Tiling t,
                          unsigned long long *count, cudaStream_t s);
@@ -299,14 +303,15 @@ cudaError_t launch_forward_plane_pair(const RayRec *rays, const ImgParam *prm,
                                       int32_t n_img, int32_t nu, int32_t nv,
                                       const tomo_cube_geom *c,
                                       const double *done, cudaStream_t s,
-                                      bool only_marked);
+                                      bool only_marked, int group);
 cudaError_t launch_adjoint_plane_pair(const RayRec *rays, const ImgParam *prm,
                                       const float *images, const uint8_t *mask,
                                       PlaneAcc acc, float *cube,
                                       int64_t fstride, int32_t n_img,
                                       int32_t nu, int32_t nv,
                                       const tomo_cube_geom *c,
-                                      const double *done, cudaStream_t s);
+                                      const double *done, cudaStream_t s,
+                                      int group);
 // plane_mode: 0 every image per ray, 1 the images whose hint has the
 // plane-forward bit, 2 every image plane by plane (where the hint allows)
 cudaError_t launch_forward_b(const RayRec *rays, const ImgParam *prm,
@@ -314,14 +319,14 @@ cudaError_t launch_forward_b(const RayRec *rays, const ImgParam *prm,
                              const uint8_t *mask, float *out, int32_t n_img,
                              int32_t nu, int32_t nv, const tomo_cube_geom *c,
                              const double *done, int plane_mode,
-                             cudaStream_t s);
+                             cudaStream_t s, int group);
 // plane_on false: every image per ray into acc.c[0]
 cudaError_t launch_adjoint_b(const RayRec *rays, const ImgParam *prm,
                              const float *images, const float *rho2,
                              const uint8_t *mask, PlaneAcc acc, int32_t n_img,
                              int32_t nu, int32_t nv, const tomo_cube_geom *c,
                              const double *done, bool plane_on,
-                             cudaStream_t s);
+                             cudaStream_t s, int group);
 
 // ---- mapmask.cu (map mask K = diag(1 - mask), same mask for every frame)
 // dst = K src over `frames` frames of n voxels (float32 or bf16 bits)

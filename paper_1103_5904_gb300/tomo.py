@@ -28,6 +28,7 @@ TOMO_OPT_RAY_CACHE, TOMO_OPT_TILE_U, TOMO_OPT_TILE_V, TOMO_OPT_WARP_U = 1, 2, 3,
 TOMO_OPT_PROFILE = 5
 TOMO_OPT_PLANE_SYNC = 7
 TOMO_OPT_CHANNELS = 8
+TOMO_OPT_GROUP_FWD, TOMO_OPT_GROUP_ADJ = 9, 10
 TOMO_BATCH_AUTOTUNE = 8
 KERNEL_CLASSES = ("setup", "forward", "adjoint", "prior", "vector", "layout")
 
