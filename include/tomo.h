@@ -398,6 +398,12 @@ typedef struct {
                               three-segment body when ratio >= this, else
                               they count the slabs to the next crossing of
                               the rarer minor axis (default 0.035) */
+    double fwd_group;      /* images per group of the plane P's CTA order
+                              (TOMO_OPT_GROUP_FWD, which overrides it when
+                              set); 0 (default): chosen from the bytes the
+                              walk gathers from */
+    double adj_group;      /* the same for the plane P^T
+                              (TOMO_OPT_GROUP_ADJ) */
 } tomo_plane_rules;
 
 /* A tile shape, walk rules and measured times (tomo_autotune): the

@@ -373,11 +373,16 @@ tomo_status ensure_pairs(tomo_ctx *ctx, const tomo_cube_geom *c,
 //    group of every image when the images spread over several frame or
 //    frame-pair accumulators (8 frames, 7 pairs: -14 %; 32 images -13 %,
 //    8 images -8 %).
-int plane_group(const tomo_ctx *ctx, bool adjoint, int64_t walked_bytes,
-                int n_acc, int32_t n_img)
+int plane_group(const tomo_ctx *ctx, const tomo_cube_geom *c,
+                const tomo_image_geom *g, bool adjoint, int64_t walked_bytes,
+                int n_acc)
 {
+    const int32_t n_img = g->n_img;
     const int opt = adjoint ? ctx->group_adj : ctx->group_fwd;
     if (opt > 0) return opt;
+    const tomo_plane_rules r = rules_for(ctx, c, g);
+    const double rg = adjoint ? r.adj_group : r.fwd_group;
+    if (rg >= 1.0) return rg >= 65535.0 ? 65535 : (int)rg;
     const int64_t l2 = ctx->l2_bytes > 0 ? ctx->l2_bytes : (int64_t)126 << 20;
     if (!adjoint) return walked_bytes >= l2 / 4 ? n_img : 1;
     if (walked_bytes <= 2 * l2) return 1;
@@ -423,8 +428,8 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                launch_forward_plane_pair(
                    rays, prm, pc, cube_dev, dtype, fstride, mask, out,
                    g->n_img, g->nu, g->nv, c, done, s, !all,
-                   plane_group(ctx, false, 8 * fstride * (n_frames - 1),
-                               n_frames - 1, g->n_img)));
+                   plane_group(ctx, c, g, false, 8 * fstride * (n_frames - 1),
+                               n_frames - 1)));
         return TOMO_OK;
     }
     if (use_plane(ctx, c, t, true) && (all || ctx->fwd_plane_possible)) {
@@ -445,9 +450,9 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                launch_forward_plane(
                    rays, prm, pc, dtype, fstride, n_frames > 1, mask, out,
                    g->n_img, g->nu, g->nv, c, done, s, !all,
-                   plane_group(ctx, false,
+                   plane_group(ctx, c, g, false,
                                (dtype == TOMO_BF16 ? 2 : 4) * fstride * n_frames,
-                               n_frames, g->n_img)));
+                               n_frames)));
         return TOMO_OK;
     }
     LAUNCH(ctx, TOMO_K_FORWARD, s,
@@ -484,8 +489,8 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                launch_adjoint_plane_pair(
                    rays, prm, images, mask, pa, cube, fstride, g->n_img,
                    g->nu, g->nv, c, done, s,
-                   plane_group(ctx, true, 8 * fstride * (n_frames - 1),
-                               n_frames - 1, g->n_img)));
+                   plane_group(ctx, c, g, true, 8 * fstride * (n_frames - 1),
+                               n_frames - 1)));
         for (int L = 0; L <= 2; ++L)
             LAUNCH(ctx, TOMO_K_LAYOUT, s,
                    launch_add_pairs(ctx->pr[L].p, cube, L, c, n_frames, used,
@@ -507,8 +512,8 @@ tomo_status adjoint_one(tomo_ctx *ctx, const float *images,
                launch_adjoint_plane(
                    rays, prm, images, mask, pa, fstride, n_frames > 1,
                    g->n_img, g->nu, g->nv, c, done, s,
-                   plane_group(ctx, true, 4 * fstride * n_frames, n_frames,
-                               g->n_img)));
+                   plane_group(ctx, c, g, true, 4 * fstride * n_frames,
+                               n_frames)));
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
                launch_add_from_layout(a1, cube, 1, c, n_frames, used, done, s));
         LAUNCH(ctx, TOMO_K_LAYOUT, s,
@@ -586,7 +591,7 @@ tomo_status op_forward(tomo_ctx *ctx, const void *src, tomo_dtype dtype,
                                 (const ImgParam *)ctx->params.p, pc, rho2,
                                 mask, out, g->n_img, g->nu, g->nv, c, done,
                                 plane ? (all ? 2 : 1) : 0, s,
-                                plane_group(ctx, false, 8 * n, 1, g->n_img)));
+                                plane_group(ctx, c, g, false, 8 * n, 1)));
         return TOMO_OK;
     }
     if ((st = ensure(ctx, ctx->th1, sizeof(float) * n * n_frames)) ||
@@ -652,7 +657,7 @@ tomo_status op_adjoint(tomo_ctx *ctx, const float *images, const uint8_t *mask,
                                 (const ImgParam *)ctx->params.p, images, rho2,
                                 mask, pa, g->n_img, g->nu, g->nv, c, done,
                                 plane, s,
-                                plane_group(ctx, true, 8 * n, 1, g->n_img)));
+                                plane_group(ctx, c, g, true, 8 * n, 1)));
         if (plane)
             for (int L = 1; L <= 2; ++L)
                 LAUNCH(ctx, TOMO_K_LAYOUT, s,

@@ -706,16 +706,21 @@ tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
         return st;
     struct Search {
         int field;          // 0 min_pitch, 1 general_ratio, 2 fwd_max_ratio,
-                            // 3 fwd_min_pitch
+                            // 3 fwd_min_pitch, 4 fwd_group, 5 adj_group
         bool forward_only;  // compare P alone (else P + P^T)
         double cand[5];
         int n;
     };
+    // group candidates: automatic, image after image, 8 and 32 images, one
+    // group of every image
+    const double all = 65535.0;
     const Search searches[] = {
         { 0, false, { never, 0.10, 0.16, 0.25, 0.40 }, 5 },
         { 1, false, { 0.0, 0.02, 0.035, 0.06, never }, 5 },
         { 2, true, { 0.0, 0.01, 0.02, 0.04, never }, 5 },
         { 3, true, { 0.5, 0.75, 1.0, never, never }, 4 },
+        { 4, true, { 0.0, 1.0, 8.0, 32.0, all }, 5 },
+        { 5, false, { 0.0, 1.0, 8.0, 32.0, all }, 5 },
     };
     for (const Search &q : searches) {
         for (int k = 0; k < q.n; ++k) {
@@ -723,7 +728,9 @@ tomo_status tomo_autotune(tomo_ctx *ctx, const tomo_problem *prob,
             double *fld = q.field == 0 ? &r.min_pitch
                           : q.field == 1 ? &r.general_ratio
                           : q.field == 2 ? &r.fwd_max_ratio
-                                         : &r.fwd_min_pitch;
+                          : q.field == 3 ? &r.fwd_min_pitch
+                          : q.field == 4 ? &r.fwd_group
+                                         : &r.adj_group;
             if (*fld == q.cand[k]) continue;
             *fld = q.cand[k];
             const tomo_plane_rules keep = entry->rules;
@@ -770,8 +777,8 @@ tomo_status tomo_set_plane_rules(tomo_ctx *ctx, const tomo_cube_geom *cube,
         return fail(ctx, TOMO_ERR_ARG, "cube and img must both be given or "
                                        "both be NULL");
     const tomo_plane_rules r = rules ? *rules : default_plane_rules();
-    const double v[4] = { r.min_pitch, r.fwd_min_pitch, r.fwd_max_ratio,
-                          r.general_ratio };
+    const double v[6] = { r.min_pitch, r.fwd_min_pitch, r.fwd_max_ratio,
+                          r.general_ratio, r.fwd_group, r.adj_group };
     for (double x : v)
         if (!(x >= 0.0) || isnan(x))
             return fail(ctx, TOMO_ERR_ARG, "plane rules must be >= 0");

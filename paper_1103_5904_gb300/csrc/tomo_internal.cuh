@@ -84,6 +84,8 @@ inline tomo_plane_rules default_plane_rules()
     r.fwd_min_pitch = kPlaneFwdMinPitch;
     r.fwd_max_ratio = kPlaneFwdMaxRatio;
     r.general_ratio = kPlaneGeneralRatio;
+    r.fwd_group = 0.0;
+    r.adj_group = 0.0;
     return r;
 }
 

@@ -81,7 +81,8 @@ class Problem(C.Structure):
 
 class PlaneRules(C.Structure):
     _fields_ = [("min_pitch", C.c_double), ("fwd_min_pitch", C.c_double),
-                ("fwd_max_ratio", C.c_double), ("general_ratio", C.c_double)]
+                ("fwd_max_ratio", C.c_double), ("general_ratio", C.c_double),
+                ("fwd_group", C.c_double), ("adj_group", C.c_double)]
 
 
 class TilingResult(C.Structure):
@@ -90,14 +91,15 @@ class TilingResult(C.Structure):
                 ("adj_ms", C.c_float), ("rules", PlaneRules)]
 
 
-RULE_FIELDS = ("min_pitch", "fwd_min_pitch", "fwd_max_ratio", "general_ratio")
+RULE_FIELDS = ("min_pitch", "fwd_min_pitch", "fwd_max_ratio", "general_ratio",
+               "fwd_group", "adj_group")
 NEVER = 1e30  # a walk-rule threshold that is never reached
 
 
 assert C.sizeof(CubeGeom) == 72 and C.sizeof(Pointing) == 96
 assert C.sizeof(ImageGeom) == 24
 assert C.sizeof(Problem) == 160
-assert C.sizeof(PlaneRules) == 32 and C.sizeof(TilingResult) == 56
+assert C.sizeof(PlaneRules) == 48 and C.sizeof(TilingResult) == 72
 
 
 class TomoError(RuntimeError):
@@ -607,7 +609,7 @@ def tomo_set_plane_rules(rules=None, geom=None, nu=None, nv=None,
     r = None
     if rules is not None:
         d = {"min_pitch": 0.16, "fwd_min_pitch": 0.75, "fwd_max_ratio": 0.02,
-             "general_ratio": 0.035}
+             "general_ratio": 0.035, "fwd_group": 0.0, "adj_group": 0.0}
         unknown = set(rules) - set(RULE_FIELDS)
         if unknown:
             raise ValueError("unknown rule(s) %s" % sorted(unknown))

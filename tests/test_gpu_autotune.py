@@ -71,6 +71,10 @@ def test_rules_change_the_schedule_not_the_result(T):
                           lambda c: np.all((c & 3) == 3)),
         "per-ray forward": ({"fwd_max_ratio": 0.0, "fwd_min_pitch": NEVER},
                             lambda c: np.all((c & 3) == 1)),
+        # CTA order: groups of 4 images (the last one padded) and one group
+        # of every image change no walk
+        "groups": ({"fwd_group": 4.0, "adj_group": 65535.0},
+                   lambda c: np.array_equal(c, c0)),
     }
     for name, (rules, check) in cases.items():
         T.tomo_set_plane_rules(rules, g, 64, 60, ctx=ctx)
@@ -107,6 +111,8 @@ def test_autotune_tunes_rules_used_by_single_and_batched_calls(T):
     assert r["general_ratio"] in (0.0, 0.02, 0.035, 0.06, NEVER)
     assert r["fwd_max_ratio"] in (0.0, 0.01, 0.02, 0.04, NEVER)
     assert r["fwd_min_pitch"] in (0.5, 0.75, 1.0, NEVER)
+    assert r["fwd_group"] in (0.0, 1.0, 8.0, 32.0, 65535.0)
+    assert r["adj_group"] in (0.0, 1.0, 8.0, 32.0, 65535.0)
     assert best["fwd_ms"] > 0 and best["adj_ms"] > 0
     # the tuned schedule: same images bit for bit, transpose within bound
     P, Pt, codes = _run(T, g, ptg, cube, y, mask, ctx)
