@@ -59,6 +59,9 @@ namespace {
 // sectors to L2, walks one slab per iteration at six CTAs (9.19 ms; five
 // CTAs 9.31, two slabs per iteration 9.52).
 constexpr int kFwdUnroll = 6;
+// bf16 cubes: eight slabs (7.97 / 109.4 ms against 8.11 / 112.0 at six; the
+// predicated slot bodies 9.01 / 125.0)
+constexpr int kFwdBf16Unroll = 8;
 constexpr int kFwdTimeUnroll = 1;
 constexpr int kFwdMinBlocks = 4;
 constexpr int kAdjUnroll = 1;
@@ -118,7 +121,8 @@ k_forward_plane(const RayRec *__restrict__ rays,
         PlaneGatherOp<CubeT> op;
         op.c = lay;
         op.acc = 0.0f;
-        plane_walk_for<kFwdUnroll>(q.pad, p, regular, op);
+        constexpr int kU = sizeof(CubeT) == 2 ? kFwdBf16Unroll : kFwdUnroll;
+        plane_walk_for<kU>(q.pad, p, regular, op);
         acc = op.acc;
         if (live && !regular) {
             GatherOp<CubeT> op2;
