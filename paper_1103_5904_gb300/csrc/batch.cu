@@ -375,13 +375,14 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
         struct { int64_t c0, c1; } c;
         c.c0 = (item - prefix[p]) * kChunk;
         c.c1 = c.c0 + kChunk < len ? c.c0 + kChunk : len;
-        double s0 = 0.0, s1 = 0.0;
+        // per-thread sums in compensated float pairs (SumF2), then FP64
+        SumF2 a0, a1;
         const bool done = d.S[S_DONE] != 0.0;
         if (op == V_SUMSQ) {
             for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x)
                 if (d.mask == nullptr || d.mask[i] == 0) {
-                    const double yi = d.y[i];
-                    s0 += yi * yi;
+                    const float yi = d.y[i];
+                    a0.add_prod(yi, yi);
                 }
         } else if (op == V_ZERO) {
             for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x) {
@@ -398,8 +399,8 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
                 const float ri = out ? 0.0f : (warm ? bi - d.q[i] : bi);
                 d.r[i] = ri;
                 d.p[i] = ri;
-                s0 += (double)ri * ri;
-                if (warm) s1 += (double)d.x[i] * ((double)ri + bi);
+                a0.add_prod(ri, ri);
+                if (warm) a1.add_prod_sum(d.x[i], ri, bi);
             }
         } else if (op == V_PRIOR || op == V_PRIOR_X) {
             if (!done) {
@@ -415,7 +416,7 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
         } else if (op == V_PQ) {
             if (!done)
                 for (int64_t i = c.c0 + threadIdx.x; i < c.c1; i += blockDim.x)
-                    s0 += (double)d.p[i] * d.q[i];
+                    a0.add_prod(d.p[i], d.q[i]);
         } else if (op == V_UPDATE) {
             if (!done) {
                 const float alpha = (float)d.S[S_ALPHA];
@@ -426,8 +427,8 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
                                          : fmaf(-alpha, d.q[i], d.r[i]);
                     d.x[i] = xi;
                     d.r[i] = ri;
-                    s0 += (double)ri * ri;
-                    s1 += (double)xi * ((double)ri + d.b[i]);
+                    a0.add_prod(ri, ri);
+                    a1.add_prod_sum(xi, ri, d.b[i]);
                 }
             }
         } else if (op == V_DIR) {
@@ -438,8 +439,8 @@ k_vec_batched(int op, const VecDesc *__restrict__ descs,
             }
         }
         if (op == V_SUMSQ || op == V_INIT || op == V_PQ || op == V_UPDATE) {
-            s0 = block_sum(s0, sm);
-            s1 = block_sum(s1, sm);
+            const double s0 = block_sum(a0.value(), sm);
+            const double s1 = block_sum(a1.value(), sm);
             if (threadIdx.x == 0) {
                 partials[2 * item] = s0;
                 partials[2 * item + 1] = s1;

@@ -15,6 +15,50 @@
 
 namespace tomo {
 
+// A per-thread partial sum kept as a compensated pair of floats.  A product
+// of two floats is split exactly into p + e (p = fl(a b) with an unfused
+// multiply, e = fmaf(a, b, -p): the FMA-based TwoProduct), and every term
+// is added with Knuth's TwoSum, whose rounding error goes to the second
+// float.  For the few dozen terms of one thread this is as accurate as FP64
+// accumulation of the exact products (the error is of order u^2 times the
+// sum of magnitudes), and it runs on the FP32 pipes: GB300 issues FP64 at a
+// small fraction of its FP32 rate, and converting every element to FP64
+// made the CG vector passes FP64-bound at a third of their memory rate.
+// The pairs are summed across threads in FP64.
+struct SumF2 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float a)
+    {
+        const float s = __fadd_rn(hi, a);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)),
+                                  __fsub_rn(a, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        add(p);
+        lo = __fadd_rn(lo, e);
+    }
+    // adds a (b + c), with b + c split exactly by TwoSum first
+    __device__ __forceinline__ void add_prod_sum(float a, float b, float c)
+    {
+        const float s = __fadd_rn(b, c);
+        const float bb = __fsub_rn(s, b);
+        const float es = __fadd_rn(__fsub_rn(b, __fsub_rn(s, bb)),
+                                   __fsub_rn(c, bb));
+        add_prod(a, s);
+        lo = __fadd_rn(lo, __fmul_rn(a, es));
+    }
+    __device__ __forceinline__ double value() const
+    {
+        return (double)hi + (double)lo;
+    }
+};
+
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);

@@ -10,7 +10,9 @@
 //
 // CG scalars (alpha, beta, r.r, p.q, the criterion) live in device memory in
 // FP64, so the iteration loop needs no host round trip.  Every dot product
-// is a two-stage reduction: each CTA writes its FP64 partial sum, and the
+// sums its elements per thread in compensated float pairs (SumF2, as
+// accurate as FP64 for a thread's share) and then in a two-stage FP64
+// reduction: each CTA writes its FP64 partial sum, and the
 // last CTA to finish (found with one atomic counter, no waiting) adds the
 // partials in a fixed order, which makes the result deterministic, and then
 // applies the scalar update of that CG step.  A "done" flag in the same slot
@@ -124,14 +126,15 @@ __global__ void k_masked_sumsq(const float *__restrict__ y,
                                double *partials, unsigned int *counter,
                                double *S)
 {
-    double v[1] = { 0.0 };
+    SumF2 a;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (mask == nullptr || mask[i] == 0) {
-            const double yi = y[i];
-            v[0] += yi * yi;
+            const float yi = y[i];
+            a.add_prod(yi, yi);
         }
     }
+    double v[1] = { a.value() };
     double tot[1];
     if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0)
         S[S_YMY] = tot[0];
@@ -148,15 +151,15 @@ struct CgInitElem {
     float *r, *p;
     uint16_t *p16;
     __device__ __forceinline__ void operator()(int64_t i, bool out,
-                                               double v[2]) const
+                                               SumF2 v[2]) const
     {
         if (out) b[i] = 0.0f;
         const float bi = out ? 0.0f : b[i];
         const float ri = out ? 0.0f : ((q != nullptr) ? bi - q[i] : bi);
         r[i] = ri;
         p[i] = direction_store(ri, p16, i);
-        v[0] += (double)ri * ri;
-        if (x != nullptr) v[1] += (double)x[i] * ((double)ri + bi);
+        v[0].add_prod(ri, ri);
+        if (x != nullptr) v[1].add_prod_sum(x[i], ri, bi);
     }
 };
 
@@ -165,7 +168,7 @@ struct CgInitElem {
 template <class F>
 __device__ __forceinline__ void masked_elements(const uint8_t *__restrict__ mm,
                                                 int64_t mm_n, int64_t n,
-                                                const F &f, double v[2])
+                                                const F &f, SumF2 v[2])
 {
     const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -186,9 +189,10 @@ __global__ void k_cg_init(float *__restrict__ b, const float *__restrict__ q,
                           int64_t n, double tol2, double *partials,
                           unsigned int *counter, double *S, double *report)
 {
-    double v[2] = { 0.0, 0.0 };
+    SumF2 a[2];
     const CgInitElem f = { b, q, x, r, p, p16 };
-    masked_elements(mm, mm_n, n, f, v);
+    masked_elements(mm, mm_n, n, f, a);
+    double v[2] = { a[0].value(), a[1].value() };
     double tot[2];
     if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
         cg_finalize_init(S, report, tot[0], tot[1], tol2);
@@ -199,10 +203,11 @@ __global__ void k_cg_pq(const float *__restrict__ p, const float *__restrict__ q
                         double *S)
 {
     if (S[S_DONE] != 0.0) return;
-    double v[1] = { 0.0 };
+    SumF2 a;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        v[0] += (double)p[i] * q[i];
+        a.add_prod(p[i], q[i]);
+    double v[1] = { a.value() };
     double tot[1];
     if (grid_sum<1>(v, partials, counter, tot) && threadIdx.x == 0)
         cg_finalize_pq(S, tot[0]);
@@ -215,14 +220,14 @@ struct CgUpdateElem {
     const float *p, *q, *b;
     float alpha;
     __device__ __forceinline__ void operator()(int64_t i, bool out,
-                                               double v[2]) const
+                                               SumF2 v[2]) const
     {
         const float xi = fmaf(alpha, p[i], x[i]);
         const float ri = out ? 0.0f : fmaf(-alpha, q[i], r[i]);
         x[i] = xi;
         r[i] = ri;
-        v[0] += (double)ri * ri;
-        v[1] += (double)xi * ((double)ri + b[i]);
+        v[0].add_prod(ri, ri);
+        v[1].add_prod_sum(xi, ri, b[i]);
     }
 };
 
@@ -235,9 +240,10 @@ __global__ void k_cg_update(float *__restrict__ x, float *__restrict__ r,
                             unsigned int *counter, double *S, double *report)
 {
     if (S[S_DONE] != 0.0) return;
-    double v[2] = { 0.0, 0.0 };
+    SumF2 a[2];
     const CgUpdateElem f = { x, r, p, q, b, (float)S[S_ALPHA] };
-    masked_elements(mm, mm_n, n, f, v);
+    masked_elements(mm, mm_n, n, f, a);
+    double v[2] = { a[0].value(), a[1].value() };
     double tot[2];
     if (grid_sum<2>(v, partials, counter, tot) && threadIdx.x == 0)
         cg_finalize_update(S, report, tot[0], tot[1]);
