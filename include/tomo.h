@@ -425,8 +425,9 @@ typedef struct {
  * walks by pixel pitch, counted or every-slab plane walks by direction
  * ratio, the plane forward by pitch and ratio, the CTA order of the plane
  * P and P^T), searching one rule at a time and keeping the fastest P + P^T
- * (P alone for the rules that concern only P).  Group sizes on the batched
- * calls: the batched kernels keep their own work order.  The problem's cube_dev and
+ * (P alone for the rules that concern only P).  The batched calls use the
+ * bucket's walk rules but keep their own work order (the group sizes do
+ * not apply to them).  The problem's cube_dev and
  * images_dev are read, not written.  The winners are kept in the context
  * for the bucket and returned in best_out (nullable); later single and
  * batched calls on problems of the same size use them.  Synchronises
