@@ -64,7 +64,7 @@ struct VecDesc {
 };
 
 int walk_batched_blocks_per_sm();
-int plane_batched_blocks_per_sm(bool adjoint);
+int plane_batched_blocks_per_sm();  // the persistent plane transpose
 // sched[c] = (problem, first tile) of chunk c: kSchedGroup consecutive
 // tiles of one problem (tiles past the problem's count are skipped)
 cudaError_t launch_walk_batched(bool adjoint, const WalkDesc *descs,
@@ -86,15 +86,14 @@ cudaError_t launch_add_from_layout_batched(const LayoutJob *jobs,
 cudaError_t launch_to_layout_batched(const LayoutJob *jobs,
                                      const int64_t *prefix, int n_jobs,
                                      int grid, cudaStream_t s);
-// Forward projection of every problem over the plane tiles: images whose
-// hint selects the plane forward walk plane-synchronously (on the layout
-// copies in descs[p].lay1 / lay2, made by launch_to_layout_batched), the
-// others per ray.
+// Forward projection of every problem over the plane tiles (prefix[p]:
+// first tile of problem p, prefix[n_probs] = n_tiles), one CTA per tile:
+// images whose hint selects the plane forward walk plane-synchronously (on
+// the layout copies in descs[p].lay1 / lay2, made by
+// launch_to_layout_batched), the others per ray.
 cudaError_t launch_forward_plane_batched(const WalkDesc *descs,
-                                         const int64_t *prefix,
-                                         const int2 *sched, int64_t n_chunks,
-                                         unsigned long long *next_item,
-                                         int grid, cudaStream_t s);
+                                         const int64_t *prefix, int n_probs,
+                                         int64_t n_tiles, cudaStream_t s);
 cudaError_t launch_vec_batched(int op, const VecDesc *descs,
                                const int64_t *prefix, int n_probs, bool warm,
                                double *partials, int grid, cudaStream_t s);

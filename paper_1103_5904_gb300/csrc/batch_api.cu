@@ -385,10 +385,10 @@ bool batch_plane_forward(const tomo_ctx *ctx, int32_t n, const tomo_problem *pro
     return true;
 }
 
-int plane_walk_grid(const tomo_ctx *ctx, bool adjoint)
+int plane_walk_grid(const tomo_ctx *ctx)
 {
     return (ctx->num_sms > 0 ? ctx->num_sms : 152) *
-           plane_batched_blocks_per_sm(adjoint);
+           plane_batched_blocks_per_sm();
 }
 
 int combine_grid(const tomo_ctx *ctx)
@@ -437,7 +437,7 @@ tomo_status batched_walk_core(tomo_ctx *ctx, int32_t n,
                                                 (const int64_t *)P->ptpre_dev.p,
                                                 (const int2 *)P->psched_dev.p,
                                                 P->pn_chunks, ctr2,
-                                                plane_walk_grid(ctx, true), s));
+                                                plane_walk_grid(ctx), s));
         if (P->rn_chunks > 0)
             LAUNCH(ctx, TOMO_K_ADJOINT, s,
                    launch_walk_batched(true, (const WalkDesc *)P->call_desc.p,
@@ -464,9 +464,7 @@ tomo_status batched_walk_core(tomo_ctx *ctx, int32_t n,
             LAUNCH(ctx, TOMO_K_FORWARD, s,
                    launch_forward_plane_batched((const WalkDesc *)P->call_desc.p,
                                                 (const int64_t *)P->ptpre_dev.p,
-                                                (const int2 *)P->psched_dev.p,
-                                                P->pn_chunks, ctr2,
-                                                plane_walk_grid(ctx, false), s));
+                                                n, P->ptile_prefix[n], s));
         if (P->rn_chunks > 0)
             LAUNCH(ctx, TOMO_K_FORWARD, s,
                    launch_walk_batched(false, (const WalkDesc *)P->call_desc.p,
@@ -1024,8 +1022,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
         const int64_t *ptile_pre = (const int64_t *)P->ptpre_dev.p;
         const int2 *psch = (const int2 *)P->psched_dev.p;
         const int cgrid = combine_grid(ctx);
-        const int pgrid = plane_walk_grid(ctx, true);
-        const int pfgrid = plane_walk_grid(ctx, false);
+        const int pgrid = plane_walk_grid(ctx);
         const LayoutJob *FJ = (const LayoutJob *)P->solve_fjobs.p;
         const int64_t *rtile_pre = (const int64_t *)P->rtpre_dev.p;
         const int2 *rsch = (const int2 *)P->rsched_dev.p;
@@ -1040,8 +1037,7 @@ tomo_status tomo_solve_batched(tomo_ctx *ctx, int32_t n,
             if (P->pn_chunks > 0)                                            \
                 CAP(TOMO_K_FORWARD,                                          \
                     launch_forward_plane_batched(W + (ws) * n, ptile_pre,    \
-                                                 psch, P->pn_chunks,         \
-                                                 ctr + next_ctr++, pfgrid, c)); \
+                                                 n, P->ptile_prefix[n], c)); \
             if (P->rn_chunks > 0)                                            \
                 CAP(TOMO_K_FORWARD,                                          \
                     launch_walk_batched(false, W + (ws) * n, rtile_pre, rsch, \
