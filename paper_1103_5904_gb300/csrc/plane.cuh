@@ -285,9 +285,9 @@ struct NoVal {};
 // an exact zero) and, with on == false, for slots without a segment (off
 // then may lie outside the cube and must not be touched).  For an op with
 // kAllSlots set, the middle range calls it with on == true for every slot,
-// a slot without a segment giving the lane's current voxel and length 0.  Every lane of the
-// warp must call this (it uses warp-wide reductions); lanes with regular ==
-// false only take part in those.
+// a slot without a segment giving the lane's current voxel and length 0.
+// Every lane of the warp must call this (it uses warp-wide reductions);
+// lanes with regular == false only take part in those.
 //
 // Warp iteration i handles slab j = i - j0 of every lane (j0: how many M
 // planes after the warp's first one the lane enters).  Each lane knows how
