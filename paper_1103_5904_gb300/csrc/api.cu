@@ -175,7 +175,11 @@ CubeDev cube_dev(const tomo_cube_geom *c)
     d.d[0] = c->dx;
     d.d[1] = c->dy;
     d.d[2] = c->dz;
-    for (int k = 0; k < 3; ++k) d.inv_d[k] = 1.0 / d.d[k];
+    const int32_t n[3] = { c->nx, c->ny, c->nz };
+    for (int k = 0; k < 3; ++k) {
+        d.inv_d[k] = 1.0 / d.d[k];
+        d.hi[k] = d.lo[k] + n[k] * d.d[k];
+    }
     return d;
 }
 

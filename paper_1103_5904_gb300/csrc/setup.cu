@@ -128,6 +128,29 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
         tan_v[(int64_t)img * nv + i] = tan((i - p.crpix_v) * p.cdelt_v + p.crval_v);
 }
 
+// Sign, zero and order tests of doubles on their bits.  This GPU's FP64
+// pipe completes about two operations per clock per SM, and a double compare
+// (also the one inside fmin / fmax) takes a slot of it like an FMA; the ray
+// setup is bound by that pipe, while its integer pipe is nearly idle.  The
+// tests below give the IEEE answer for every non-NaN input.
+__device__ __forceinline__ bool d_sign(double x)  // sign bit (also -0.0)
+{
+    return __double2hiint(x) < 0;
+}
+
+__device__ __forceinline__ bool d_zero(double x)  // x == 0.0
+{
+    return (__double_as_longlong(x) << 1) == 0;
+}
+
+// An integer ordered like the doubles: a < b  <=>  d_key(a) < d_key(b), and
+// -0.0 and +0.0 share a key.
+__device__ __forceinline__ long long d_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 ? -(b & 0x7fffffffffffffffLL) : b;
+}
+
 // One thread per pixel.  Slab clip of the half-line o + a u (a >= 0) in FP64,
 // entry voxel by the half-open rule, then per-axis first crossing and
 // crossing spacing relative to the entry point.
@@ -145,24 +168,41 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
     const double tv = tan_v[(int64_t)img * nv + iv];
     double u[3];
     for (int a = 0; a < 3; ++a) u[a] = f.w[a] + tu * f.e1[a] + tv * f.e2[a];
-    const double inv = 1.0 / sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double inv = rsqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     for (int a = 0; a < 3; ++a) u[a] *= inv;
 
     const int n[3] = { c.nx, c.ny, c.nz };
+    bool zero[3], neg[3];  // u_a == 0, u_a < 0
+    for (int a = 0; a < 3; ++a) {
+        zero[a] = d_zero(u[a]);
+        neg[a] = d_sign(u[a]) && !zero[a];
+    }
     // one FP64 reciprocal per axis serves the clip and the crossing spacing
     double ru[3];
-    for (int a = 0; a < 3; ++a) ru[a] = (u[a] != 0.0) ? 1.0 / u[a] : 0.0;
+    for (int a = 0; a < 3; ++a) ru[a] = zero[a] ? 0.0 : 1.0 / u[a];
+    // amin = max(0, near faces), amax = min(far faces), with their keys; the
+    // near face of an axis is the lower one when u_a > 0 (lo < hi and the
+    // rounded difference and product keep that order)
     double amin = 0.0, amax = INFINITY;
+    long long kmin = d_key(amin), kmax = d_key(amax);
     bool hit = true;
     for (int a = 0; a < 3; ++a) {
-        const double lo = c.lo[a], hi = c.lo[a] + n[a] * c.d[a];
-        if (u[a] == 0.0) {
-            if (f.o[a] < lo || f.o[a] >= hi) hit = false;
+        if (zero[a]) {
+            const long long ko = d_key(f.o[a]);
+            if (ko < d_key(c.lo[a]) || ko >= d_key(c.hi[a])) hit = false;
         } else {
-            const double a0 = (lo - f.o[a]) * ru[a];
-            const double a1 = (hi - f.o[a]) * ru[a];
-            amin = fmax(amin, fmin(a0, a1));
-            amax = fmin(amax, fmax(a0, a1));
+            const double a0 = (c.lo[a] - f.o[a]) * ru[a];
+            const double a1 = (c.hi[a] - f.o[a]) * ru[a];
+            const double near = neg[a] ? a1 : a0, far = neg[a] ? a0 : a1;
+            const long long kn = d_key(near), kf = d_key(far);
+            if (kn > kmin) {
+                amin = near;
+                kmin = kn;
+            }
+            if (kf < kmax) {
+                amax = far;
+                kmax = kf;
+            }
         }
     }
     // Opaque sphere of radius r_obs at the origin (the photosphere): the
@@ -185,7 +225,11 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
             hit = false;
         } else if (pp < r2) {
             const double first = -ou - sqrt(r2 - pp);
-            if (first > 0.0) amax = fmin(amax, first);
+            const long long kf = d_key(first);
+            if (kf > 0 && kf < kmax) {
+                amax = first;
+                kmax = kf;
+            }
         }
     }
     RayRec r;
@@ -193,25 +237,28 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
     r.dtx = r.dty = r.dtz = 0.0f;
     r.idx0 = 0;
     r.chord = -1.0f;
-    if (hit && amin < amax) {
+    if (hit && kmin < kmax) {
         float chord = (float)(amax - amin);
         int idx[3];
         float t0f[3], dtf[3];
         for (int a = 0; a < 3; ++a) {
             const double pa = f.o[a] + amin * u[a];
             const double g = (pa - c.lo[a]) * c.inv_d[a];  // voxel coordinate
-            int ia = (u[a] < 0.0) ? (int)ceil(g) - 1 : (int)floor(g);
+            // half-open voxels: floor(g), or ceil(g) - 1 walking down
+            int ia = neg[a] ? __double2int_ru(g) - 1 : __double2int_rd(g);
             ia = ia < 0 ? 0 : (ia > n[a] - 1 ? n[a] - 1 : ia);
             idx[a] = ia;
-            if (u[a] != 0.0) {
-                const double plane = (u[a] > 0.0) ? ia + 1.0 : (double)ia;
-                const double t0 = fmax((plane - g) * c.d[a] * ru[a], 0.0);
-                const float dt = (float)(c.d[a] * fabs(ru[a]));
-                const int rem = (u[a] > 0.0) ? n[a] - 1 - ia : ia;
-                t0f[a] = (float)t0;
+            if (!zero[a]) {
+                const bool pos = !neg[a];
+                const double plane = (double)(pos ? ia + 1 : ia);
+                const double dr = c.d[a] * ru[a];  // d_a / u_a
+                const double t0 = (plane - g) * dr;
+                const float dt = (float)fabs(dr);
+                const int rem = pos ? n[a] - 1 - ia : ia;
+                t0f[a] = d_sign(t0) ? 0.0f : (float)t0;
                 // last in-cube plane of this axis, in the walk's arithmetic
                 chord = fminf(chord, fmaf((float)rem, dt, t0f[a]));
-                dtf[a] = (u[a] > 0.0) ? dt : -dt;
+                dtf[a] = pos ? dt : -dt;
             } else {
                 t0f[a] = 1e30f;
                 dtf[a] = 0.0f;

@@ -105,6 +105,7 @@ struct Frame {
 struct CubeDev {
     int32_t nx, ny, nz;
     double lo[3], d[3];
+    double hi[3];     // lo + n d: the upper faces
     double inv_d[3];  // 1 / d
     double r_obs;     // opaque sphere at the origin (0: none)
 };
