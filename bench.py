@@ -213,27 +213,33 @@ def peak_hbm():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def ncu_reduction_sectors(kernel):
+def _profile_record(name):
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def ncu_reduction_sectors(kernel, workload):
     """Reduction sectors that `kernel` sends from L1 to the crossbar per
-    Siddon segment, recorded in profiles/, or None."""
-    path = os.path.join(ROOT, "profiles", "reduction_sectors.json")
-    try:
-        with open(path) as f:
-            rec = json.load(f).get(kernel)
-    except (OSError, ValueError):
+    Siddon segment on `workload`, recorded in profiles/, or None.  The
+    ratio was captured on a subset of the workload's images and holds per
+    segment for any subset; another workload's geometry changes it."""
+    rec = _profile_record("reduction_sectors.json").get(kernel)
+    if not rec or rec.get("workload") != workload:
         return None
-    return None if rec is None else rec.get(
-        "l1_to_crossbar_reduction_sectors_per_segment")
+    return rec.get("l1_to_crossbar_reduction_sectors_per_segment")
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` recorded in profiles/, or None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
-        with open(path) as f:
-            return json.load(f).get(kernel)
-    except (OSError, ValueError):
+def ncu_traffic(kernel, workload, n_img):
+    """DRAM bytes per launch of `kernel` recorded in profiles/ for this
+    workload at this image count, or None (the bytes are those of one full
+    launch, which another image count or workload does not repeat)."""
+    rec = _profile_record("traffic.json")
+    if rec.get("workload") != workload or rec.get("images") != n_img:
         return None
+    return rec.get("bytes_per_launch", {}).get(kernel)
 
 
 # ----------------------------------------------------------- oracle legs
@@ -417,7 +423,7 @@ def run_gpu(args, rank, local_rank, world):
     roofline = {"bound": "hbm", "kernel": kname[dom],
                 "achieved": kern[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kern[dom]["achieved_gbs"] / peak,
-                "traffic": ncu_traffic(kname[dom]),
+                "traffic": ncu_traffic(kname[dom], args.workload, n_img),
                 "peak_source": peak_src + " HBM copy bandwidth",
                 "bytes_model": "4 B/segment + 37 B/live ray + 1 B/pixel"}
     if dom == "adjoint":
@@ -432,7 +438,8 @@ def run_gpu(args, rank, local_rank, world):
     # most one 32-byte reduction sector per cycle to the crossbar; sectors
     # per segment from the committed capture, time from this run, clock the
     # median sampled during the timed region
-    red = ncu_reduction_sectors(kname[dom]) if dom == "adjoint" else None
+    red = (ncu_reduction_sectors(kname[dom], args.workload)
+           if dom == "adjoint" else None)
     if red is not None and clk.get("sm_mhz"):
         per_launch_s = kern["adjoint"]["ms_per_projection"] / 1e3
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
