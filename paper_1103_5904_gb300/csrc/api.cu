@@ -199,7 +199,10 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     const tomo_plane_rules rules = rules_for(ctx, c, g);
     const uint64_t hh = fnv1a(h, &rules, sizeof(rules));
     tomo_status st;
-    if ((st = ensure(ctx, ctx->layout_used, sizeof(unsigned)))) return st;
+    if ((st = ensure(ctx, ctx->layout_used, sizeof(unsigned))) ||
+        (st = ensure(ctx, ctx->per_ray_fwd,
+                     sizeof(unsigned) * (1 + (size_t)g->n_img))))
+        return st;
     if (ctx->ray_cache && ctx->key_valid && ctx->key == h) {
         if (ctx->hint_key == hh) {
             CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
@@ -208,11 +211,15 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
         // same rays, other walk rules: only the per-image hints change
         CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->setup_done, 0));
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->per_ray_fwd.p, 0, sizeof(unsigned), s));
         ctx->fwd_plane_possible = false;
+        ctx->fwd_plane_all = true;
         ctx->plane_possible = false;
         for (int32_t i = 0; i < g->n_img; ++i) {
+            const bool f = plane_forward_estimate(ptg[i], c, rules);
             ctx->plane_possible |= plane_estimate(ptg[i], c, rules);
-            ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c, rules);
+            ctx->fwd_plane_possible |= f;
+            ctx->fwd_plane_all &= f;
         }
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
@@ -220,7 +227,8 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                              (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
                              (ImgParam *)ctx->params.p,
                              make_double3(c->dx, c->dy, c->dz),
-                             (unsigned *)ctx->layout_used.p, rules, s));
+                             (unsigned *)ctx->layout_used.p,
+                             (unsigned *)ctx->per_ray_fwd.p, rules, s));
         CUDA_TRY(ctx, cudaEventRecord(ctx->setup_done, s));
         ctx->hint_key = hh;
         return TOMO_OK;
@@ -238,11 +246,15 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ptg.p, ptg, sizeof(tomo_pointing) * n_img,
                                   cudaMemcpyHostToDevice, s));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->layout_used.p, 0, sizeof(unsigned), s));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->per_ray_fwd.p, 0, sizeof(unsigned), s));
     ctx->fwd_plane_possible = false;
+    ctx->fwd_plane_all = true;
     ctx->plane_possible = false;
     for (size_t i = 0; i < n_img; ++i) {
+        const bool f = plane_forward_estimate(ptg[i], c, rules);
         ctx->plane_possible |= plane_estimate(ptg[i], c, rules);
-        ctx->fwd_plane_possible |= plane_forward_estimate(ptg[i], c, rules);
+        ctx->fwd_plane_possible |= f;
+        ctx->fwd_plane_all &= f;
     }
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_frames((const tomo_pointing *)ctx->ptg.p, g->n_img, g->nu,
@@ -250,7 +262,8 @@ tomo_status prepare_rays(tomo_ctx *ctx, const tomo_cube_geom *c,
                          (double *)ctx->tan_u.p, (double *)ctx->tan_v.p,
                          (ImgParam *)ctx->params.p,
                          make_double3(c->dx, c->dy, c->dz),
-                         (unsigned *)ctx->layout_used.p, rules, s));
+                         (unsigned *)ctx->layout_used.p,
+                         (unsigned *)ctx->per_ray_fwd.p, rules, s));
     LAUNCH(ctx, TOMO_K_SETUP, s,
            launch_ray_setup((const Frame *)ctx->frames.p,
                             (const double *)ctx->tan_u.p,
@@ -399,6 +412,14 @@ bool use_time_pairs(const tomo_ctx *ctx, const tomo_cube_geom *c,
     return n_frames > 1 && (ctx->channels & 1) && plane_supported(c, 8);
 }
 
+// The per-ray forward's image list when the host estimate says every image
+// may take the plane forward (the list is then short or empty), else NULL:
+// images certain to need the per-ray walk keep its one-CTA-per-tile grid.
+const unsigned *per_ray_list(const tomo_ctx *ctx)
+{
+    return ctx->fwd_plane_all ? (const unsigned *)ctx->per_ray_fwd.p : nullptr;
+}
+
 tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                         int32_t n_frames, const uint8_t *mask, float *out,
                         const tomo_cube_geom *c, const tomo_image_geom *g,
@@ -427,7 +448,8 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
             LAUNCH(ctx, TOMO_K_FORWARD, s,
                    launch_forward(rays, prm, cube_dev, dtype, fstride, true,
                                   mask, out, g->n_img, g->nu, g->nv, c->nx,
-                                  c->nx * c->ny, t, done, s, true));
+                                  c->nx * c->ny, t, done, s, true,
+                                  per_ray_list(ctx), ctx->num_sms));
         LAUNCH(ctx, TOMO_K_FORWARD, s,
                launch_forward_plane_pair(
                    rays, prm, pc, cube_dev, dtype, fstride, mask, out,
@@ -449,7 +471,7 @@ tomo_status forward_one(tomo_ctx *ctx, const void *cube_dev, tomo_dtype dtype,
                    launch_forward(rays, prm, cube_dev, dtype, fstride,
                                   n_frames > 1, mask, out, g->n_img, g->nu,
                                   g->nv, c->nx, c->nx * c->ny, t, done, s,
-                                  true));
+                                  true, per_ray_list(ctx), ctx->num_sms));
         LAUNCH(ctx, TOMO_K_FORWARD, s,
                launch_forward_plane(
                    rays, prm, pc, dtype, fstride, n_frames > 1, mask, out,
@@ -785,6 +807,7 @@ void tomo_destroy(tomo_ctx *ctx)
                        &ctx->params, &ctx->rays, &ctx->b, &ctx->r, &ctx->p,
                        &ctx->q, &ctx->t, &ctx->p16, &ctx->S, &ctx->partials,
                        &ctx->counter, &ctx->count64, &ctx->layout_used,
+                       &ctx->per_ray_fwd,
                        &ctx->lay1, &ctx->lay2, &ctx->mcube, &ctx->rho2,
                        &ctx->thf, &ctx->th1, &ctx->th2, &ctx->thimg,
                        &ctx->pr[0], &ctx->pr[1], &ctx->pr[2] };

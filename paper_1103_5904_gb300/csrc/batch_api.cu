@@ -249,7 +249,7 @@ tomo_status prepare_batch(tomo_ctx *ctx, int32_t n, const tomo_problem *probs,
                launch_frames((const tomo_pointing *)P->ptg.p + P->img_off[i],
                              p.img.n_img, p.img.nu, p.img.nv, 1, fr, tu, tv, pr,
                              make_double3(p.cube.dx, p.cube.dy, p.cube.dz),
-                             (unsigned *)P->lay_used.p + i,
+                             (unsigned *)P->lay_used.p + i, nullptr,
                              rules_for(ctx, &p.cube, &p.img), s));
         LAUNCH(ctx, TOMO_K_SETUP, s,
                launch_ray_setup(fr, tu, tv, cube_dev(&p.cube), p.img.n_img,

@@ -64,9 +64,15 @@ struct tomo_ctx {
     tomo::host::DevBuf ptg, frames, tan_u, tan_v, params, rays;
     // bit L set: some image of the cached geometry walks in layout L
     tomo::host::DevBuf layout_used;
+    // { count, image indices }: the images of the cached geometry whose hint
+    // leaves them to the per-ray forward
+    tomo::host::DevBuf per_ray_fwd;
     // some image of the cached geometry may select the plane forward (a
     // host-side upper bound of the device's per-image pixel-pitch test)
     bool fwd_plane_possible = true;
+    // every image of the cached geometry may select the plane forward (the
+    // same estimate): the per-ray forward then runs in its listed form
+    bool fwd_plane_all = false;
     // some image of the cached geometry may have a valid plane hint (the
     // same kind of estimate; when false the per-ray transpose runs)
     bool plane_possible = true;

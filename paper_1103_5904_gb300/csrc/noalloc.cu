@@ -105,7 +105,7 @@ tomo_project_noalloc(const tomo_cube_geom *cube, int32_t n_frames,
         launch_frames(ptg, img->n_img, img->nu, img->nv, n_frames, frames,
                       tan_u, tan_v, params,
                       make_double3(cube->dx, cube->dy, cube->dz), nullptr,
-                      default_plane_rules(), s) != cudaSuccess ||
+                      nullptr, default_plane_rules(), s) != cudaSuccess ||
         launch_ray_setup(frames, tan_u, tan_v, tomo::host::cube_dev(cube),
                          img->n_img,
                          img->nu, img->nv, rays, s) != cudaSuccess ||

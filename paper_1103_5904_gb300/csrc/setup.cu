@@ -72,7 +72,7 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
                          int32_t nv, int32_t n_frames, Frame *frames,
                          double *tan_u, double *tan_v, ImgParam *params,
                          double3 vox, unsigned *layout_used,
-                         tomo_plane_rules rules)
+                         unsigned *per_ray_fwd, tomo_plane_rules rules)
 {
     const int img = blockIdx.x;
     const tomo_pointing p = ptg[img];
@@ -108,6 +108,8 @@ __global__ void k_frames(const tomo_pointing *__restrict__ ptg, int32_t nu,
             atomicOr(layout_used, (1u << L) |
                                       ((q.pad & kPlaneFwdBit) ? 1u << (8 + L) : 0u));
         }
+        if (per_ray_fwd && !(q.pad & kPlaneFwdBit))
+            per_ray_fwd[1 + atomicAdd(per_ray_fwd, 1u)] = (unsigned)img;
         if (n_frames > 1) {
             int k = (int)floor(p.time);
             if (k > n_frames - 2) k = n_frames - 2;
@@ -284,12 +286,13 @@ cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
                           ImgParam *params, double3 vox,
-                          unsigned *layout_used, const tomo_plane_rules &rules,
-                          cudaStream_t s)
+                          unsigned *layout_used, unsigned *per_ray_fwd,
+                          const tomo_plane_rules &rules, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
     k_frames<<<n_img, 128, 0, s>>>(ptg_dev, nu, nv, n_frames, frames, tan_u,
-                                   tan_v, params, vox, layout_used, rules);
+                                   tan_v, params, vox, layout_used,
+                                   per_ray_fwd, rules);
     return cudaGetLastError();
 }
 

@@ -20,19 +20,14 @@ namespace tomo {
 
 namespace {
 
+// One pixel of the forward projection: the masked, gained line integral.
 template <typename CubeT, bool kTime>
-__global__ void __launch_bounds__(512)
-k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
-          const CubeT *__restrict__ cube, int64_t frame_stride,
-          const uint8_t *__restrict__ mask, float *__restrict__ out, int nu,
-          int nv, int nx, int nxny, Tiling tl, const double *__restrict__ done,
-          bool skip_plane_images)
+__device__ __forceinline__ void forward_pixel(
+    const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
+    const CubeT *__restrict__ cube, int64_t frame_stride,
+    const uint8_t *__restrict__ mask, float *__restrict__ out, int nu, int nv,
+    int nx, int nxny, int img, int iu, int iv)
 {
-    if (done != nullptr && *done != 0.0) return;
-    const int img = blockIdx.z;
-    if (skip_plane_images && (prm[img].pad & kPlaneFwdBit)) return;
-    int iu, iv;
-    if (!pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv)) return;
     const int64_t id = ((int64_t)img * nv + iv) * nu + iu;
     float y = 0.0f;
     if (mask == nullptr || mask[id] == 0) {
@@ -58,6 +53,54 @@ k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
         }
     }
     out[id] = y;
+}
+
+// One CTA per pixel tile of one image; with skip_plane_images the CTAs of
+// images whose hint selects the plane forward return at once.
+template <typename CubeT, bool kTime>
+__global__ void __launch_bounds__(512)
+k_forward(const RayRec *__restrict__ rays, const ImgParam *__restrict__ prm,
+          const CubeT *__restrict__ cube, int64_t frame_stride,
+          const uint8_t *__restrict__ mask, float *__restrict__ out, int nu,
+          int nv, int nx, int nxny, Tiling tl, const double *__restrict__ done,
+          bool skip_plane_images)
+{
+    if (done != nullptr && *done != 0.0) return;
+    if (skip_plane_images && (prm[blockIdx.z].pad & kPlaneFwdBit)) return;
+    int iu, iv;
+    if (!pixel_of_thread(tl, blockIdx.x, blockIdx.y, nu, nv, iu, iv)) return;
+    forward_pixel<CubeT, kTime>(rays, prm, cube, frame_stride, mask, out, nu,
+                                nv, nx, nxny, blockIdx.z, iu, iv);
+}
+
+// The images listed in listed = { count, image indices ... }: a grid of
+// about one wave of CTAs deals the (listed image, tile) units out in turn.
+// With an empty list (every image taken by the plane-synchronous forward)
+// the launch costs one wave of CTAs that read the count and return, not one
+// CTA per tile of every image.
+template <typename CubeT, bool kTime>
+__global__ void __launch_bounds__(512)
+k_forward_listed(const RayRec *__restrict__ rays,
+                 const ImgParam *__restrict__ prm,
+                 const CubeT *__restrict__ cube, int64_t frame_stride,
+                 const uint8_t *__restrict__ mask, float *__restrict__ out,
+                 int nu, int nv, int nx, int nxny, Tiling tl,
+                 const double *__restrict__ done,
+                 const unsigned *__restrict__ listed, unsigned tiles_u,
+                 unsigned tiles)
+{
+    if (done != nullptr && *done != 0.0) return;
+    // units + gridDim.x < 2^32: the launcher checks it
+    const unsigned units = listed[0] * tiles;
+    for (unsigned w = blockIdx.x; w < units; w += gridDim.x) {
+        const int img = (int)listed[1 + w / tiles];
+        const unsigned t = w % tiles;
+        int iu, iv;
+        if (pixel_of_thread(tl, (int)(t % tiles_u), (int)(t / tiles_u), nu,
+                            nv, iu, iv))
+            forward_pixel<CubeT, kTime>(rays, prm, cube, frame_stride, mask,
+                                        out, nu, nv, nx, nxny, img, iu, iv);
+    }
 }
 
 template <bool kTime>
@@ -122,6 +165,38 @@ dim3 grid_of(int nu, int nv, int n_img, Tiling t)
                 (unsigned)((nv + t.tile_v - 1) / t.tile_v), (unsigned)n_img);
 }
 
+template <typename CubeT, bool kTime>
+cudaError_t forward_kernel(const RayRec *rays, const ImgParam *prm,
+                           const CubeT *cube, int64_t frame_stride,
+                           const uint8_t *mask, float *out, int32_t n_img,
+                           int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
+                           Tiling t, const double *done, cudaStream_t s,
+                           bool skip, const unsigned *listed, int num_sms)
+{
+    const dim3 grid = grid_of(nu, nv, n_img, t);
+    const int block = t.tile_u * t.tile_v;
+    if (!skip || listed == nullptr) {
+        k_forward<CubeT, kTime><<<grid, block, 0, s>>>(
+            rays, prm, cube, frame_stride, mask, out, nu, nv, nx, nxny, t, done,
+            skip);
+        return cudaGetLastError();
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_forward_listed<CubeT, kTime>, block, 0);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (int64_t)grid.x * grid.y;
+    const int64_t units = tiles * n_img;
+    int64_t ctas = (int64_t)(per_sm > 0 ? per_sm : 1) * (num_sms > 0 ? num_sms : 1);
+    if (ctas > units) ctas = units;
+    // the unit counter w < units steps by ctas without wrapping
+    if (units + ctas >= ((int64_t)1 << 32)) return cudaErrorInvalidValue;
+    k_forward_listed<CubeT, kTime><<<(unsigned)ctas, block, 0, s>>>(
+        rays, prm, cube, frame_stride, mask, out, nu, nv, nx, nxny, t, done,
+        listed, grid.x, (unsigned)tiles);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
@@ -130,30 +205,31 @@ cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
                            const uint8_t *mask, float *out, int32_t n_img,
                            int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
                            Tiling t, const double *done, cudaStream_t s,
-                           bool skip_plane_images)
+                           bool skip_plane_images, const unsigned *listed,
+                           int num_sms)
 {
     if (n_img <= 0) return cudaSuccess;
-    const dim3 grid = grid_of(nu, nv, n_img, t);
-    const int block = t.tile_u * t.tile_v;
     const bool sk = skip_plane_images;
     if (dtype == TOMO_BF16) {
         const uint16_t *c = static_cast<const uint16_t *>(cube);
-        if (time_interp)
-            k_forward<uint16_t, true><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
-        else
-            k_forward<uint16_t, false><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
-    } else {
-        const float *c = static_cast<const float *>(cube);
-        if (time_interp)
-            k_forward<float, true><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
-        else
-            k_forward<float, false><<<grid, block, 0, s>>>(
-                rays, prm, c, frame_stride, mask, out, nu, nv, nx, nxny, t, done, sk);
+        return time_interp
+                   ? forward_kernel<uint16_t, true>(rays, prm, c, frame_stride,
+                                                    mask, out, n_img, nu, nv,
+                                                    nx, nxny, t, done, s, sk,
+                                                    listed, num_sms)
+                   : forward_kernel<uint16_t, false>(rays, prm, c, frame_stride,
+                                                     mask, out, n_img, nu, nv,
+                                                     nx, nxny, t, done, s, sk,
+                                                     listed, num_sms);
     }
-    return cudaGetLastError();
+    const float *c = static_cast<const float *>(cube);
+    return time_interp
+               ? forward_kernel<float, true>(rays, prm, c, frame_stride, mask,
+                                             out, n_img, nu, nv, nx, nxny, t,
+                                             done, s, sk, listed, num_sms)
+               : forward_kernel<float, false>(rays, prm, c, frame_stride, mask,
+                                              out, n_img, nu, nv, nx, nxny, t,
+                                              done, s, sk, listed, num_sms);
 }
 
 cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,

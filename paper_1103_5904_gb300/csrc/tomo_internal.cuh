@@ -135,12 +135,16 @@ constexpr int kMaxReduceBlocks = 2048;
 // vox: voxel size per axis (for the plane-walk hint's pixel-pitch test);
 // layout_used (may be NULL): bit L is or-ed in for every image whose plane
 // hint is valid and names layout L, bit 8 + L if its hint also selects the
-// plane forward
+// plane forward.  per_ray_fwd (may be NULL; 1 + n_img words, word 0 zeroed
+// by the caller): the images whose hint leaves them to the per-ray forward
+// are appended, per_ray_fwd[0] = their count, then their indices in no
+// fixed order.
 cudaError_t launch_frames(const tomo_pointing *ptg_dev, int32_t n_img,
                           int32_t nu, int32_t nv, int32_t n_frames,
                           Frame *frames, double *tan_u, double *tan_v,
                           ImgParam *params, double3 vox, unsigned *layout_used,
-                          const tomo_plane_rules &rules, cudaStream_t s);
+                          unsigned *per_ray_fwd, const tomo_plane_rules &rules,
+                          cudaStream_t s);
 cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
                              const double *tan_v, CubeDev cube, int32_t n_img,
                              int32_t nu, int32_t nv, RayRec *rays,
@@ -148,14 +152,20 @@ cudaError_t launch_ray_setup(const Frame *frames, const double *tan_u,
 
 // ---- siddon.cu
 // skip_plane_images: leave the images whose hint has kPlaneFwdBit to the
-// plane-synchronous forward (launched with only_marked)
+// plane-synchronous forward (launched with only_marked).  With listed (a
+// per_ray_fwd list built by launch_frames) the skipping launch takes about
+// one wave of CTAs (num_sms x resident CTAs per SM) that deal out the
+// listed images' tiles instead of one CTA per tile of every image: far
+// cheaper when the list is short or empty, at a few more registers per
+// thread.  A pixel gets the same value from every form.
 cudaError_t launch_forward(const RayRec *rays, const ImgParam *prm,
                            const void *cube, tomo_dtype dtype,
                            int64_t frame_stride, bool time_interp,
                            const uint8_t *mask, float *out, int32_t n_img,
                            int32_t nu, int32_t nv, int32_t nx, int32_t nxny,
                            Tiling t, const double *done, cudaStream_t s,
-                           bool skip_plane_images = false);
+                           bool skip_plane_images = false,
+                           const unsigned *listed = nullptr, int num_sms = 0);
 cudaError_t launch_adjoint(const RayRec *rays, const ImgParam *prm,
                            const float *images, const uint8_t *mask,
                            float *cube, int64_t frame_stride,
