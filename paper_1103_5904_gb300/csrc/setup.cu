@@ -162,10 +162,19 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
                             int32_t nu, int32_t nv, RayRec *rays)
 {
     const int img = blockIdx.y;
+    const Frame &f = frames[img];
+    // o - lo and o - hi, constants of the image: once per block
+    __shared__ double s_olo[3], s_ohi[3];
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            s_olo[a] = f.o[a] - c.lo[a];
+            s_ohi[a] = f.o[a] - c.hi[a];
+        }
+    }
+    __syncthreads();
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= (int64_t)nu * nv) return;
     const int iu = (int)(pix % nu), iv = (int)(pix / nu);
-    const Frame &f = frames[img];
     const double tu = tan_u[(int64_t)img * nu + iu];
     const double tv = tan_v[(int64_t)img * nv + iv];
     double u[3];
@@ -193,8 +202,9 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
             const long long ko = d_key(f.o[a]);
             if (ko < d_key(c.lo[a]) || ko >= d_key(c.hi[a])) hit = false;
         } else {
-            const double a0 = (c.lo[a] - f.o[a]) * ru[a];
-            const double a1 = (c.hi[a] - f.o[a]) * ru[a];
+            // (lo - o) ru, with lo - o = -(o - lo) exactly
+            const double a0 = -(s_olo[a] * ru[a]);
+            const double a1 = -(s_ohi[a] * ru[a]);
             const double near = neg[a] ? a1 : a0, far = neg[a] ? a0 : a1;
             const long long kn = d_key(near), kf = d_key(far);
             if (kn > kmin) {
@@ -244,8 +254,8 @@ __global__ void k_ray_setup(const Frame *__restrict__ frames,
         int idx[3];
         float t0f[3], dtf[3];
         for (int a = 0; a < 3; ++a) {
-            const double pa = f.o[a] + amin * u[a];
-            const double g = (pa - c.lo[a]) * c.inv_d[a];  // voxel coordinate
+            // voxel coordinate of the entry point o + amin u
+            const double g = fma(amin, u[a], s_olo[a]) * c.inv_d[a];
             // half-open voxels: floor(g), or ceil(g) - 1 walking down
             int ia = neg[a] ? __double2int_ru(g) - 1 : __double2int_rd(g);
             ia = ia < 0 ? 0 : (ia > n[a] - 1 ? n[a] - 1 : ia);
