@@ -177,6 +177,36 @@ def test_axis_aligned_column_sums():
             g["dz"] * x[:, j, i].sum(), rel=1e-13)
 
 
+def test_rays_in_the_boundary_faces():
+    """Half-open voxels [lo + i d, lo + (i + 1) d): a ray lying in a lower
+    face of the cube runs inside the first layer of voxels and integrates
+    that layer's row; the same ray in the upper face lies in no voxel and
+    integrates nothing.  Rays along x in the faces z = z0 and z = z0 + nz dz,
+    along y in x = x0 and x = x0 + nx dx, along z in y = y0 and y = y0 + ny dy
+    (the coordinates chosen exactly representable)."""
+    rng = np.random.default_rng(11)
+    g = _geom((7, 5, 4), (-1.0, -0.5, 0.25), (0.25, 0.5, 0.125))
+    x = rng.random((4, 5, 7))
+    flat = x.reshape(-1)
+    hi = [g["x0"] + 7 * g["dx"], g["y0"] + 5 * g["dy"], g["z0"] + 4 * g["dz"]]
+    j, k, i = 2, 1, 3
+    yc = g["y0"] + (j + 0.5) * g["dy"]
+    zc = g["z0"] + (k + 0.5) * g["dz"]
+    xc = g["x0"] + (i + 0.5) * g["dx"]
+    cases = [
+        ([-5.0, yc, g["z0"]], [1.0, 0, 0], g["dx"] * x[0, j, :].sum()),
+        ([-5.0, yc, hi[2]], [1.0, 0, 0], 0.0),
+        ([g["x0"], 9.0, zc], [0, -1.0, 0], g["dy"] * x[k, :, 0].sum()),
+        ([hi[0], 9.0, zc], [0, -1.0, 0], 0.0),
+        ([xc, g["y0"], -3.0], [0, 0, 1.0], g["dz"] * x[:, 0, i].sum()),
+        ([xc, hi[1], -3.0], [0, 0, 1.0], 0.0),
+    ]
+    for o, u, want in cases:
+        idx, ln, _, _ = siddon.segments(g, o, u)
+        got = float(np.sum(ln * flat[idx])) if len(idx) else 0.0
+        assert got == pytest.approx(want, rel=1e-13, abs=0.0), (o, u)
+
+
 def test_fine_sampling_converges():
     """Midpoint sampling with step h stays within (S + 2) h max|x| of the
     Siddon integral (S = number of segments), and the error shrinks with h."""
