@@ -1,22 +1,26 @@
-"""Planted mistakes in the FP64 projector oracle (`oracle/siddon_oracle.c`).
+"""Planted mistakes in the FP64 oracle: the C projector
+(`oracle/siddon_oracle.c`) and the prior and CG (`oracle/solver.py`).
 
-Each mutant is a copy of the oracle's C source with one plausible error (a
-wrong sign, a swapped operand, a wrong index, a dropped bound or term),
-compiled on the CPU into a library of its own.  The oracle's pins
-(`test_oracle_pins.py`) then run against it in a child process, and at
-least one must fail.  An unmodified copy run the same way passes every pin,
-so the failures come from the planted mistakes and not from the harness.
-Mutants that cannot change a result (scaling lengths by |u| when u is a
-unit vector, say) are not planted."""
+Each mutant is a copy of one source with one plausible error (a wrong sign,
+a swapped operand, a wrong index, a dropped bound, factor or term): a C copy
+is compiled on the CPU into a library of its own, a Python copy is loaded
+as the oracle's solver module.  The oracle's pins (`test_oracle_pins.py`)
+then run against it in a child process, and at least one must fail.  An
+unmodified copy run the same way passes every pin, so the failures come
+from the planted mistakes and not from the harness.  Mutants that cannot
+change a result (scaling lengths by |u| when u is a unit vector, say) are
+not planted."""
 
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "siddon_oracle.c")
+SOLVER = os.path.join(ROOT, "oracle", "solver.py")
 
 # (what the mistake is, text in the source, text it is replaced by); each
 # text occurs exactly once
@@ -80,21 +84,70 @@ MUTANTS = [
      "double o[3], u[3];\n            if (orc_ray("),
 ]
 
-# Run in a child process: point the oracle at the given library, then call
-# every pin with each of its parameter sets until one raises.  Prints
-# "READY" once the pins are imported, then "FAIL <pin>" or "PASS".
+# The same for the solver module (Python): (what, text, replacement).
+SOLVER_MUTANTS = [
+    ("difference transpose with the wrong sign",
+     "out[tuple(sl_lo)] -= g", "out[tuple(sl_lo)] += g"),
+    ("temporal difference transpose with the wrong sign",
+     "out[:-1] -= g", "out[:-1] += g"),
+    ("outer map mask dropped from the prior term",
+     "self.lam * self.K(\n            self.R(DtD_frames",
+     "self.lam * (\n            self.R(DtD_frames"),
+    ("prior weight applied on one side only",
+     "self.R(DtD_frames(self.R(self.K(v))))", "DtD_frames(self.R(self.K(v)))"),
+    ("temporal prior dropped from the normal operator",
+     "out = out + self.lam_t * self.K(DtD_time(self.K(v)))", "out = out"),
+    ("map mask not applied to the transpose",
+     "return self.K(siddon.backproject(", "return (siddon.backproject("),
+    ("map mask not applied to P",
+     "return siddon.project(self.geom, self.K(x), self.pointing",
+     "return siddon.project(self.geom, x, self.pointing"),
+    ("pixel mask inverted", "np.where(self.mask == 0, y, 0.0)",
+     "np.where(self.mask != 0, y, 0.0)"),
+    ("lambda missing from J",
+     "j = float(np.sum(r * r)) + self.lam * spatial",
+     "j = float(np.sum(r * r)) + spatial"),
+    ("temporal prior missing from J",
+     "j += self.lam_t * float(np.sum(Dt_time(kx) ** 2))",
+     "j += 0.0 * float(np.sum(Dt_time(kx) ** 2))"),
+    ("CG step length from q.q", "alpha = rr / float(np.sum(p * q))",
+     "alpha = rr / float(np.sum(q * q))"),
+    ("CG residual updated with the wrong sign", "r = r - alpha * q",
+     "r = r + alpha * q"),
+    ("CG beta inverted", "beta = rr_new / rr", "beta = rr / rr_new"),
+    ("CG warm start ignored",
+     "r = b - problem.normal(x) if x0 is not None else b.copy()",
+     "r = b.copy()"),
+]
+
+# Run in a child process: point the oracle at the given C library ("c") or
+# load the given file as its solver module ("py"), then call every pin with
+# each of its parameter sets until one raises.  Prints "READY" once the
+# pins are imported, then "FAIL <pin>" or "PASS".
 RUNNER = r"""
-import inspect, itertools, os, sys
-sys.path.insert(0, sys.argv[2])
+import importlib.util, inspect, os, sys
+mode, path, root = sys.argv[1:4]
+sys.path.insert(0, root)
+import oracle
 import oracle.siddon as siddon
-siddon._build.build = lambda force=False: sys.argv[1]
-siddon._lib = None
+if mode == "c":
+    siddon._build.build = lambda force=False: path
+    siddon._lib = None
+else:
+    spec = importlib.util.spec_from_file_location("oracle.solver", path)
+    mod = importlib.util.module_from_spec(spec)
+    sys.modules["oracle.solver"] = mod
+    spec.loader.exec_module(mod)
+    oracle.solver = mod
 import tests.test_oracle_pins as pins
-golden = os.path.join(sys.argv[2], "tests", "golden")
+assert (pins.solver is oracle.solver) and (mode == "c" or pins.solver.__file__ == path)
+golden = os.path.join(root, "tests", "golden")
 skip = ("test_thomson_voxel_factors_pin_catches_planted_mistakes",)
 calls = []
-for name, fn in inspect.getmembers(pins, inspect.isfunction):
-    if not name.startswith("test_") or name in skip:
+fns = sorted(inspect.getmembers(pins, inspect.isfunction),
+             key=lambda nf: nf[1].__code__.co_firstlineno)  # the file's order
+for name, fn in fns:
+    if not name.startswith("test_") or name in skip or fn.__module__ != pins.__name__:
         continue
     sets = [{}]
     for m in getattr(fn, "pytestmark", []):
@@ -134,28 +187,78 @@ def _compile(source, out_dir):
     return so_path
 
 
-def _run_pins(so_path):
-    env = dict(os.environ, OMP_NUM_THREADS="4")
-    r = subprocess.run([sys.executable, "-c", RUNNER, so_path, ROOT],
-                       cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
-    lines = r.stdout.split()
-    assert r.returncode == 0 and "READY" in lines, r.stdout + r.stderr
+def _solver_copy(source, out_dir):
+    path = os.path.join(out_dir, "solver_variant.py")
+    with open(path, "w") as f:
+        f.write(source)
+    return path
+
+
+def _run_pins(path, mode):
+    """The last line the child prints ("PASS" or "FAIL <pin> <error>"), or
+    "ERROR ..." when the harness itself failed."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", RUNNER, mode, path, ROOT],
+                           cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=900)
+    except subprocess.TimeoutExpired:
+        return "ERROR timeout"
+    if r.returncode != 0 or "READY" not in r.stdout.split():
+        return "ERROR exit %d: %s" % (r.returncode, (r.stdout + r.stderr)[-2000:])
     return r.stdout.strip().splitlines()[-1]
 
 
-def _source():
-    with open(SRC) as f:
+def _source(path=SRC):
+    with open(path) as f:
         return f.read()
 
 
-def test_unmodified_copy_passes_every_pin(tmp_path):
-    assert _run_pins(_compile(_source(), str(tmp_path))) == "PASS"
+def _variants():
+    """(key, mode, source) of the two unmodified copies and every mutant."""
+    out = [("c", "c", _source()), ("py", "py", _source(SOLVER))]
+    for what, old, new in MUTANTS:
+        out.append(("c:" + what, "c", _source().replace(old, new)))
+    for what, old, new in SOLVER_MUTANTS:
+        out.append(("py:" + what, "py", _source(SOLVER).replace(old, new)))
+    return out
 
 
-@pytest.mark.parametrize("what,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(what, old, new, tmp_path):
-    src = _source()
-    assert src.count(old) == 1, what
-    result = _run_pins(_compile(src.replace(old, new), str(tmp_path)))
-    assert result.startswith("FAIL"), "%s: no pin fails" % what
+@pytest.fixture(scope="module")
+def results(tmp_path_factory):
+    """Every variant built and run against the pins, the children in
+    parallel (they are independent processes)."""
+    jobs = []
+    for i, (key, mode, src) in enumerate(_variants()):
+        d = str(tmp_path_factory.mktemp("variant%02d" % i))
+        path = _compile(src, d) if mode == "c" else _solver_copy(src, d)
+        jobs.append((key, path, mode))
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {key: ex.submit(_run_pins, path, mode)
+                for key, path, mode in jobs}
+        return {key: f.result() for key, f in futs.items()}
+
+
+def test_each_mistake_is_planted_once():
+    for what, old, _ in MUTANTS:
+        assert _source().count(old) == 1, what
+    for what, old, _ in SOLVER_MUTANTS:
+        assert _source(SOLVER).count(old) == 1, what
+
+
+def test_unmodified_copies_pass_every_pin(results):
+    assert results["c"] == "PASS", results["c"]
+    assert results["py"] == "PASS", results["py"]
+
+
+@pytest.mark.parametrize("what", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(results, what):
+    got = results["c:" + what]
+    assert got.startswith("FAIL"), "%s: %s" % (what, got)
+
+
+@pytest.mark.parametrize("what", [m[0] for m in SOLVER_MUTANTS])
+def test_planted_solver_mistake_fails_a_pin(results, what):
+    got = results["py:" + what]
+    assert got.startswith("FAIL"), "%s: %s" % (what, got)

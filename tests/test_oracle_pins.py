@@ -574,6 +574,13 @@ def test_map_mask_projection_special_cases():
     pb, _ = _map_mask_problem(80)
     x_all, rep = solver.cg(pb, 5, x0=np.ones((4, 4, 5)))
     assert not np.any(x_all)
+    # the solver's operator reads excluded voxels as 0 (R14) whatever they
+    # hold: its P of x equals the masked projection pinned above, and the
+    # criterion of x equals that of K x
+    pm = solver.Problem(g, ptg, 10, 6, y, mask, lam=0.3, map_mask=mm)
+    np.testing.assert_allclose(pm.P(x), got, rtol=1e-13, atol=1e-15)
+    assert pm.J(x) == pytest.approx(pm.J(np.where(mm == 0, x, 0.0)),
+                                    rel=1e-13)
 
 
 def test_height_weighted_prior_solves_the_dense_system():
