@@ -1,10 +1,11 @@
 """Planted mistakes in the FP64 oracle: the C projector
-(`oracle/siddon_oracle.c`) and the prior and CG (`oracle/solver.py`).
+(`oracle/siddon_oracle.c`), the prior and CG (`oracle/solver.py`) and the
+Thomson operators (`oracle/thomson.py`).
 
 Each mutant is a copy of one source with one plausible error (a wrong sign,
 a swapped operand, a wrong index, a dropped bound, factor or term): a C copy
 is compiled on the CPU into a library of its own, a Python copy is loaded
-as the oracle's solver module.  The oracle's pins (`test_oracle_pins.py`)
+in place of the oracle's module.  The oracle's pins (`test_oracle_pins.py`)
 then run against it in a child process, and at least one must fail.  An
 unmodified copy run the same way passes every pin, so the failures come
 from the planted mistakes and not from the harness.  Mutants that cannot
@@ -21,6 +22,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "siddon_oracle.c")
 SOLVER = os.path.join(ROOT, "oracle", "solver.py")
+THOMSON = os.path.join(ROOT, "oracle", "thomson.py")
 
 # (what the mistake is, text in the source, text it is replaced by); each
 # text occurs exactly once
@@ -120,13 +122,33 @@ SOLVER_MUTANTS = [
      "r = b.copy()"),
 ]
 
+# The same for the Thomson module (Python): (what, text, replacement).
+THOMSON_MUTANTS = [
+    ("pB without the impact-parameter factor", "return o * pm", "return pm"),
+    ("B with the sign of its pB part flipped",
+     "map_mask=map_mask) - o * pm", "map_mask=map_mask) + o * pm"),
+    ("pB transpose without the impact-parameter factor",
+     "pto = siddon.backproject(geom, o * y,", "pto = siddon.backproject(geom, y,"),
+    ("B transpose with m in place of m'",
+     "return mp * siddon.backproject(", "return m * siddon.backproject("),
+    ("C1 with sin for sin^2", "C1 = c * s * s", "C1 = c * s"),
+    ("C3 with the cube term's sign flipped",
+     "C3 = 4.0 / 3.0 - c - c ** 3 / 3.0", "C3 = 4.0 / 3.0 - c + c ** 3 / 3.0"),
+    ("limb-darkening weights swapped in m",
+     "((1.0 - u) * C1 + u * C2)", "(u * C1 + (1.0 - u) * C2)"),
+    ("voxel factors at the voxels' lower corners",
+     '(np.arange(geom["n" + a]) + 0.5) * geom["d" + a]',
+     'np.arange(geom["n" + a]) * geom["d" + a]'),
+    ("scattering kept inside the Sun", "out = r > 1.0", "out = r > 0.0"),
+]
+
 # Run in a child process: point the oracle at the given C library ("c") or
-# load the given file as its solver module ("py"), then call every pin with
-# each of its parameter sets until one raises.  Prints "READY" once the
-# pins are imported, then "FAIL <pin>" or "PASS".
+# load the given file in place of the named oracle module ("py"), then call
+# every pin with each of its parameter sets until one raises.  Prints
+# "READY" once the pins are imported, then "FAIL <pin>" or "PASS".
 RUNNER = r"""
 import importlib.util, inspect, os, sys
-mode, path, root = sys.argv[1:4]
+mode, path, root, name = sys.argv[1:5]
 sys.path.insert(0, root)
 import oracle
 import oracle.siddon as siddon
@@ -134,13 +156,17 @@ if mode == "c":
     siddon._build.build = lambda force=False: path
     siddon._lib = None
 else:
-    spec = importlib.util.spec_from_file_location("oracle.solver", path)
+    spec = importlib.util.spec_from_file_location("oracle." + name, path)
     mod = importlib.util.module_from_spec(spec)
-    sys.modules["oracle.solver"] = mod
+    sys.modules["oracle." + name] = mod
     spec.loader.exec_module(mod)
-    oracle.solver = mod
+    setattr(oracle, name, mod)
+    if name == "thomson":  # the solver's operators use it too
+        oracle.solver.thomson = mod
 import tests.test_oracle_pins as pins
-assert (pins.solver is oracle.solver) and (mode == "c" or pins.solver.__file__ == path)
+if mode == "py":
+    assert getattr(oracle, name).__file__ == path
+    assert name != "solver" or pins.solver.__file__ == path
 golden = os.path.join(root, "tests", "golden")
 skip = ("test_thomson_voxel_factors_pin_catches_planted_mistakes",)
 calls = []
@@ -187,19 +213,20 @@ def _compile(source, out_dir):
     return so_path
 
 
-def _solver_copy(source, out_dir):
-    path = os.path.join(out_dir, "solver_variant.py")
+def _module_copy(source, out_dir):
+    path = os.path.join(out_dir, "module_variant.py")
     with open(path, "w") as f:
         f.write(source)
     return path
 
 
-def _run_pins(path, mode):
+def _run_pins(path, mode, name):
     """The last line the child prints ("PASS" or "FAIL <pin> <error>"), or
     "ERROR ..." when the harness itself failed."""
     env = dict(os.environ, OMP_NUM_THREADS="1")
     try:
-        r = subprocess.run([sys.executable, "-c", RUNNER, mode, path, ROOT],
+        r = subprocess.run([sys.executable, "-c", RUNNER, mode, path, ROOT,
+                            name],
                            cwd=ROOT, env=env, capture_output=True, text=True,
                            timeout=900)
     except subprocess.TimeoutExpired:
@@ -214,13 +241,21 @@ def _source(path=SRC):
         return f.read()
 
 
+# (key prefix, mode, module name, source file, mutants)
+FAMILIES = [("c", "c", "siddon", SRC, MUTANTS),
+            ("solver", "py", "solver", SOLVER, SOLVER_MUTANTS),
+            ("thomson", "py", "thomson", THOMSON, THOMSON_MUTANTS)]
+
+
 def _variants():
-    """(key, mode, source) of the two unmodified copies and every mutant."""
-    out = [("c", "c", _source()), ("py", "py", _source(SOLVER))]
-    for what, old, new in MUTANTS:
-        out.append(("c:" + what, "c", _source().replace(old, new)))
-    for what, old, new in SOLVER_MUTANTS:
-        out.append(("py:" + what, "py", _source(SOLVER).replace(old, new)))
+    """(key, mode, module name, source) of each family's unmodified copy
+    (key = the prefix) and of every mutant (key = prefix:what)."""
+    out = []
+    for prefix, mode, name, src_path, mutants in FAMILIES:
+        src = _source(src_path)
+        out.append((prefix, mode, name, src))
+        for what, old, new in mutants:
+            out.append((prefix + ":" + what, mode, name, src.replace(old, new)))
     return out
 
 
@@ -229,36 +264,31 @@ def results(tmp_path_factory):
     """Every variant built and run against the pins, the children in
     parallel (they are independent processes)."""
     jobs = []
-    for i, (key, mode, src) in enumerate(_variants()):
+    for i, (key, mode, name, src) in enumerate(_variants()):
         d = str(tmp_path_factory.mktemp("variant%02d" % i))
-        path = _compile(src, d) if mode == "c" else _solver_copy(src, d)
-        jobs.append((key, path, mode))
+        path = _compile(src, d) if mode == "c" else _module_copy(src, d)
+        jobs.append((key, path, mode, name))
     workers = max(1, min(8, os.cpu_count() or 1))
     with ThreadPoolExecutor(max_workers=workers) as ex:
-        futs = {key: ex.submit(_run_pins, path, mode)
-                for key, path, mode in jobs}
+        futs = {key: ex.submit(_run_pins, path, mode, name)
+                for key, path, mode, name in jobs}
         return {key: f.result() for key, f in futs.items()}
 
 
 def test_each_mistake_is_planted_once():
-    for what, old, _ in MUTANTS:
-        assert _source().count(old) == 1, what
-    for what, old, _ in SOLVER_MUTANTS:
-        assert _source(SOLVER).count(old) == 1, what
+    for prefix, _, _, src_path, mutants in FAMILIES:
+        src = _source(src_path)
+        for what, old, _ in mutants:
+            assert src.count(old) == 1, (prefix, what)
 
 
-def test_unmodified_copies_pass_every_pin(results):
-    assert results["c"] == "PASS", results["c"]
-    assert results["py"] == "PASS", results["py"]
+@pytest.mark.parametrize("prefix", [f[0] for f in FAMILIES])
+def test_unmodified_copy_passes_every_pin(results, prefix):
+    assert results[prefix] == "PASS", results[prefix]
 
 
-@pytest.mark.parametrize("what", [m[0] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(results, what):
-    got = results["c:" + what]
-    assert got.startswith("FAIL"), "%s: %s" % (what, got)
-
-
-@pytest.mark.parametrize("what", [m[0] for m in SOLVER_MUTANTS])
-def test_planted_solver_mistake_fails_a_pin(results, what):
-    got = results["py:" + what]
-    assert got.startswith("FAIL"), "%s: %s" % (what, got)
+@pytest.mark.parametrize("key", [f[0] + ":" + m[0] for f in FAMILIES
+                                 for m in f[4]])
+def test_planted_mistake_fails_a_pin(results, key):
+    got = results[key]
+    assert got.startswith("FAIL"), "%s: %s" % (key, got)
