@@ -25,7 +25,7 @@ SOLVER = os.path.join(ROOT, "oracle", "solver.py")
 THOMSON = os.path.join(ROOT, "oracle", "thomson.py")
 
 # (what the mistake is, text in the source, text it is replaced by); each
-# text occurs exactly once
+# text occurs exactly once, and no mutant can index outside its arrays
 MUTANTS = [
     ("roll turns the other way",
      "f1[a] = cr * e1[a] + sr * e2[a];", "f1[a] = cr * e1[a] - sr * e2[a];"),
@@ -80,6 +80,29 @@ MUTANTS = [
      "if (crossing_weights) yk = fabs(yk);", ""),
     ("impact parameter taken as the observer distance",
      "cross3(o, u, c);", "c[0] = o[0]; c[1] = o[1]; c[2] = o[2];"),
+    ("longitude measured from the y axis",
+     "o[0] = d * cos(lat) * cos(lon);\n    o[1] = d * cos(lat) * sin(lon);",
+     "o[0] = d * cos(lat) * sin(lon);\n    o[1] = d * cos(lat) * cos(lon);"),
+    ("first image axis reversed", "cross3(w, zhat, e1);", "cross3(zhat, w, e1);"),
+    ("second image axis reversed", "cross3(e1, w, e2);", "cross3(w, e1, e2);"),
+    ("first image axis not normalised", "for (int a = 0; a < 3; ++a) e1[a] /= n1;",
+     ""),
+    ("direction not normalised", "u[a] = dir[a] / nd;", "u[a] = dir[a];"),
+    ("interpolation weight measured from the next frame",
+     "*w = tau - kk;", "*w = kk + 1 - tau;"),
+    ("gain dropped in P", "out[r] = p[C_GAIN] * acc;", "out[r] = acc;"),
+    ("impact parameter without its z term",
+     "c[0] * c[0] + c[1] * c[1] + c[2] * c[2];", "c[0] * c[0] + c[1] * c[1];"),
+    ("voxel index with x mirrored",
+     "idx[s] = ((int64_t)i[2] * c->n[1] + i[1]) * c->n[0] + i[0];",
+     "idx[s] = ((int64_t)i[2] * c->n[1] + i[1]) * c->n[0] + "
+     "(c->n[0] - 1 - i[0]);"),
+    ("voxel coordinate divided by dx on every axis",
+     "double x = (o[a] + mid * u[a] - c->lo[a]) / c->d[a];",
+     "double x = (o[a] + mid * u[a] - c->lo[a]) / c->d[0];"),
+    ("plane crossings with the observer's sign flipped",
+     "double al = (c->lo[a] + k * c->d[a] - o[a]) / u[a];",
+     "double al = (c->lo[a] + k * c->d[a] + o[a]) / u[a];"),
     ("segment count includes masked rays",
      "if (mask && mask[id]) continue;\n            double o[3], u[3];\n"
      "            if (orc_ray(",
